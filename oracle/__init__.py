@@ -1,0 +1,216 @@
+"""CPU oracle for the NMC inhomogeneous Metropolis sweep (ctypes wrapper over nmc_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the bench's
+CPU-baseline / reference leg. The product path (the CUDA library and its binding) never
+imports this package, and this package never imports the product.
+
+The definitions it implements are stated at the top of nmc_oracle.c. Every function here is
+a thin argument marshaller; all arithmetic is in the C file.
+
+Parity status: every function is pinned by tests/test_oracle_pins.py (brute-force
+enumeration, recomputation, closed forms, a chi-square against the exact Boltzmann law and an
+independent Philox implementation); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nmc_oracle.c")
+_LIB = os.path.join(_HERE, "libnmc_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles nmc_oracle.c with gcc (plain -O2, no fast-math) into libnmc_oracle.so."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC,
+                               "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = C.CDLL(_LIB)
+            P = C.c_void_p
+            i32, i64, u32, u64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
+            lib.orc_philox4x32_10.argtypes = [P, P, P]
+            lib.orc_threshold_table.argtypes = [P, C.c_int]
+            lib.orc_threshold_table.restype = C.c_int
+            lib.orc_quantize_beta.argtypes = [C.c_float]
+            lib.orc_quantize_beta.restype = u32
+            lib.orc_uphill_threshold.argtypes = [u32, i64]
+            lib.orc_uphill_threshold.restype = u32
+            lib.orc_ksat_energy.argtypes = [i32, i32, i32, P, P]
+            lib.orc_ksat_energy.restype = i64
+            lib.orc_ksat_delta.argtypes = [i32, i32, i32, P, P, i32]
+            lib.orc_ksat_delta.restype = i64
+            lib.orc_ksat_colour.argtypes = [i32, i32, i32, P, P]
+            lib.orc_ksat_colour.restype = i32
+            lib.orc_ksat_anneal.argtypes = [i32, i32, i32, P, i32, P, i32, P, i32, i32, u64, P, P,
+                                            P, i32, P, P, P, P]
+            lib.orc_ksat_anneal.restype = C.c_int
+            lib.orc_qap_cost.argtypes = [i32, P, P, P]
+            lib.orc_qap_cost.restype = i64
+            lib.orc_qap_swap_delta.argtypes = [i32, P, P, P, i32, i32]
+            lib.orc_qap_swap_delta.restype = i64
+            lib.orc_qap_anneal.argtypes = [i32, P, P, i32, P, i32, P, i32, i32, u64, P, P, P,
+                                           i32, P, P, P, P]
+            lib.orc_qap_anneal.restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+TAG_KSAT_INIT = 0x4B494E49
+TAG_KSAT_SWEEP = 0x4B535750
+TAG_QAP_INIT = 0x51494E49
+TAG_QAP_STEP = 0x51535450
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """One Philox4x32-10 block: ctr 4 x uint32, key 2 x uint32 -> 4 x uint32."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def threshold_table(cap: int = 8192):
+    """(table uint32[L], L): Tab[j] = min(2^32-1, floor(2^32 exp(-j/256))), L = first zero."""
+    lib = _load()
+    t = np.zeros(cap, dtype=np.uint32)
+    n = lib.orc_threshold_table(_p(t), cap)
+    if n < 0:
+        raise RuntimeError("threshold table capacity too small")
+    return t[:n].copy(), n
+
+
+def quantize_beta(beta: float) -> int:
+    return int(_load().orc_quantize_beta(float(beta)))
+
+
+def uphill_threshold(bq: int, dE: int) -> int:
+    return int(_load().orc_uphill_threshold(int(bq), int(dE)))
+
+
+def _cnf(lits):
+    lits = np.ascontiguousarray(lits, dtype=np.int32)
+    if lits.ndim != 2:
+        raise ValueError("lits must be [M, kmax]")
+    return lits, lits.shape[0], lits.shape[1]
+
+
+def ksat_energy(lits, n_vars: int, x) -> int:
+    lits, m, k = _cnf(lits)
+    x = _c(x, np.uint8)
+    return int(_load().orc_ksat_energy(n_vars, m, k, _p(lits), _p(x)))
+
+
+def ksat_delta(lits, n_vars: int, x, v: int) -> int:
+    lits, m, k = _cnf(lits)
+    x = _c(x, np.uint8)
+    return int(_load().orc_ksat_delta(n_vars, m, k, _p(lits), _p(x), int(v)))
+
+
+def ksat_colour(lits, n_vars: int):
+    """(colour int32[N], n_colours) of the greedy ascending-id colouring."""
+    lits, m, k = _cnf(lits)
+    col = np.zeros(n_vars, dtype=np.int32)
+    nc = _load().orc_ksat_colour(n_vars, m, k, _p(lits), _p(col))
+    return col, int(nc)
+
+
+def ksat_anneal(lits, n_vars, beta, t0, t1, seed, replicas=None, replica_ids=None, init=None,
+                init_best=None, init_best_energy=None, n_threads=None):
+    """Runs sweeps t0..t1-1. Returns dict(states uint8[R,N], energies int64[R],
+    best_energies int64[R], best_states uint8[R,N]).
+
+    replica_ids selects which replica indices (Philox streams) to run; default 0..replicas-1.
+    """
+    lits, m, k = _cnf(lits)
+    beta = np.ascontiguousarray(beta, dtype=np.float32)
+    if beta.ndim != 2 or beta.shape[0] != n_vars:
+        raise ValueError("beta must be [N, n_steps]")
+    ids = None if replica_ids is None else np.ascontiguousarray(replica_ids, dtype=np.int32)
+    nr = len(ids) if ids is not None else int(replicas)
+    init = _c(init, np.uint8)
+    init_best = _c(init_best, np.uint8)
+    init_best_energy = _c(init_best_energy, np.int64)
+    if n_threads is None:
+        n_threads = min(nr, os.cpu_count() or 1)
+    out_s = np.zeros((nr, n_vars), dtype=np.uint8)
+    out_b = np.zeros((nr, n_vars), dtype=np.uint8)
+    e = np.zeros(nr, dtype=np.int64)
+    be = np.zeros(nr, dtype=np.int64)
+    rc = _load().orc_ksat_anneal(n_vars, m, k, _p(lits), beta.shape[1], _p(beta), nr, _p(ids),
+                                 int(t0), int(t1), int(seed) & (2**64 - 1), _p(init),
+                                 _p(init_best), _p(init_best_energy), int(n_threads), _p(out_s),
+                                 _p(e), _p(be), _p(out_b))
+    if rc != 0:
+        raise ValueError("orc_ksat_anneal rejected its arguments")
+    return dict(states=out_s, energies=e, best_energies=be, best_states=out_b)
+
+
+def qap_cost(F, D, p) -> int:
+    F = _c(F, np.int32)
+    D = _c(D, np.int32)
+    p = _c(p, np.int16)
+    return int(_load().orc_qap_cost(F.shape[0], _p(F), _p(D), _p(p)))
+
+
+def qap_swap_delta(F, D, p, r, s) -> int:
+    F = _c(F, np.int32)
+    D = _c(D, np.int32)
+    p = _c(p, np.int16)
+    return int(_load().orc_qap_swap_delta(F.shape[0], _p(F), _p(D), _p(p), int(r), int(s)))
+
+
+def qap_anneal(F, D, beta, t0, t1, seed, replicas=None, replica_ids=None, init=None,
+               init_best=None, init_best_energy=None, n_threads=None):
+    """Runs QAP steps t0..t1-1 (n swap attempts each). Returns dict(perms int16[R,n],
+    energies, best_energies, best_perms)."""
+    F = _c(F, np.int32)
+    D = _c(D, np.int32)
+    n = F.shape[0]
+    beta = np.ascontiguousarray(beta, dtype=np.float32)
+    if beta.ndim != 2 or beta.shape[0] != n:
+        raise ValueError("beta must be [n, n_steps]")
+    ids = None if replica_ids is None else np.ascontiguousarray(replica_ids, dtype=np.int32)
+    nr = len(ids) if ids is not None else int(replicas)
+    init = _c(init, np.int16)
+    init_best = _c(init_best, np.int16)
+    init_best_energy = _c(init_best_energy, np.int64)
+    if n_threads is None:
+        n_threads = min(nr, os.cpu_count() or 1)
+    out_p = np.zeros((nr, n), dtype=np.int16)
+    out_b = np.zeros((nr, n), dtype=np.int16)
+    e = np.zeros(nr, dtype=np.int64)
+    be = np.zeros(nr, dtype=np.int64)
+    rc = _load().orc_qap_anneal(n, _p(F), _p(D), beta.shape[1], _p(beta), nr, _p(ids), int(t0),
+                                int(t1), int(seed) & (2**64 - 1), _p(init), _p(init_best),
+                                _p(init_best_energy), int(n_threads), _p(out_p), _p(e), _p(be),
+                                _p(out_b))
+    if rc != 0:
+        raise ValueError("orc_qap_anneal rejected its arguments")
+    return dict(perms=out_p, energies=e, best_energies=be, best_perms=out_b)

@@ -1,0 +1,428 @@
+"""Pins the CPU oracle to facts other than itself (CPU only, no GPU).
+
+Each check is chosen so that a plausible mistake in the oracle fails it: brute-force
+enumeration of every assignment / permutation, recomputation of every energy change, the exact
+Boltzmann law as the stationary distribution of the homogeneous chain (chi-square), closed
+forms at beta = 0 and beta -> infinity, the Philox4x32-10 definition as implemented by an
+independent library (triton's interpreter), and the threshold table against 60-digit
+arithmetic (mpmath).
+"""
+import itertools
+import json
+import math
+import os
+import subprocess
+import sys
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import nmc_inputs as W
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+# ---------------------------------------------------------------- independent evaluators
+def energies_numpy(lits, X):
+    """#violated clauses for every row of X (S x N uint8), written independently of the
+    oracle: a clause is satisfied when any of its literals matches."""
+    lits = np.asarray(lits)
+    X = np.asarray(X, dtype=np.uint8)
+    used = lits != 0
+    var = np.abs(lits) - 1
+    want = (lits > 0).astype(np.uint8)
+    vals = X[:, np.where(used, var, 0)]  # S x M x k
+    sat = ((vals == want[None]) & used[None]).any(axis=2)
+    return (~sat).sum(axis=1).astype(np.int64)
+
+
+def all_states(n):
+    return ((np.arange(2 ** n)[:, None] >> np.arange(n)[None, :]) & 1).astype(np.uint8)
+
+
+def small_cnf(n, m, k, seed, pad_some=False):
+    rng = np.random.default_rng(seed)
+    rows = []
+    for _ in range(m):
+        kk = k if not pad_some else int(rng.integers(1, k + 1))
+        v = rng.choice(n, size=kk, replace=False) + 1
+        s = rng.choice([-1, 1], size=kk)
+        row = np.zeros(k, dtype=np.int32)
+        row[:kk] = v * s
+        rows.append(row)
+    return np.array(rows, dtype=np.int32)
+
+
+# ---------------------------------------------------------------- paper-printed sizes
+def test_paper_clause_count_convention():
+    path = os.path.join(ROOT, "tests", "golden", "paper_sizes.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for k, n, alpha, m, viol in rows:
+        assert W.n_clauses(int(n), float(alpha)) == int(m)
+        assert W.random_ksat(int(n), float(alpha), int(k), 7).shape == (int(m), int(k))
+        # ratio 1e-4 of the clauses, rounded to the nearest violation count
+        assert round(1e-4 * int(m)) == int(viol)
+
+
+# ---------------------------------------------------------------- Philox4x32-10
+_TRITON_SCRIPT = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+@triton.jit
+def k(cp, outp, seed, BLOCK: tl.constexpr):
+    o = tl.arange(0, BLOCK)
+    c0 = tl.load(cp + o * 4 + 0); c1 = tl.load(cp + o * 4 + 1)
+    c2 = tl.load(cp + o * 4 + 2); c3 = tl.load(cp + o * 4 + 3)
+    a, b, c, d = tl.philox(seed, c0, c1, c2, c3)
+    tl.store(outp + o * 4 + 0, a); tl.store(outp + o * 4 + 1, b)
+    tl.store(outp + o * 4 + 2, c); tl.store(outp + o * 4 + 3, d)
+req = json.loads(sys.stdin.read())
+res = []
+for seed, ctrs in req:
+    c = torch.tensor(np.array(ctrs, dtype=np.uint32).view(np.int32))
+    out = torch.zeros_like(c)
+    k[(1,)](c, out, seed, BLOCK=c.shape[0])
+    res.append(out.numpy().view(np.uint32).tolist())
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_independent_implementation():
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(5)
+    req = []
+    seeds = [0, 1, 0xFFFFFFFF, 0x123456789ABCDEF, 2**64 - 1, int(rng.integers(0, 2**63))]
+    for s in seeds:
+        ctrs = rng.integers(0, 2**32, size=(8, 4), dtype=np.uint64)
+        ctrs[0] = 0
+        ctrs[1] = 0xFFFFFFFF
+        req.append([s, ctrs.tolist()])
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    out = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=json.dumps(req),
+                         capture_output=True, text=True, env=env, timeout=600)
+    if out.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + out.stderr[-300:])
+    ref = json.loads(out.stdout.strip().splitlines()[-1])
+    for (s, ctrs), r in zip(req, ref):
+        key = [s & 0xFFFFFFFF, (s >> 32) & 0xFFFFFFFF]
+        for c, rr in zip(ctrs, np.array(r, dtype=np.uint64).reshape(-1, 4)):
+            got = O.philox4x32_10(c, key)
+            assert got.tolist() == rr.tolist(), (s, c)
+
+
+def test_philox_is_a_bijection_of_the_counter_and_looks_uniform():
+    # distinct counters give distinct blocks; bits are balanced
+    key = [7, 9]
+    outs = np.array([O.philox4x32_10([i, 0, 0, 0], key) for i in range(4096)])
+    assert len({tuple(o) for o in outs}) == 4096
+    bits = np.unpackbits(outs.view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 0.01
+
+
+# ---------------------------------------------------------------- thresholds, quantisation
+def test_threshold_table_against_high_precision():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    tab, L = O.threshold_table()
+    assert tab[0] == 2**32 - 1
+    # first zero entry: 2^32 exp(-j/256) < 1  <=>  j > 256 * 32 ln 2
+    assert L == math.floor(256 * 32 * math.log(2)) + 1
+    for j in range(1, L + 3):
+        exact = int(mpmath.floor(mpmath.ldexp(mpmath.exp(-mpmath.mpf(j) / 256), 32)))
+        exact = min(exact, 2**32 - 1)
+        got = int(tab[j]) if j < L else 0
+        assert got == exact, j
+    assert np.all(np.diff(tab.astype(np.int64)) <= 0)
+
+
+def test_beta_quantisation_rounds_half_to_even():
+    cases = [0.0, 1.0, 0.5, 4.0, 6.0, 0.3, 0.01, 65535.0, 1e-9, 3.5 / 65536, 2.5 / 65536,
+             12345.678]
+    for b in cases:
+        b32 = float(np.float32(b))
+        exact = Fraction(b32) * 65536
+        assert O.quantize_beta(b32) == round(exact)  # Fraction rounds half to even
+
+
+def test_uphill_threshold_is_boltzmann_factor_on_the_grid():
+    # beta = m/256 and integer dE: beta*dE is on the table's grid, so the threshold is
+    # floor(2^32 exp(-beta dE)) up to the 2^32-1 cap
+    for m in [1, 7, 64, 255, 256, 300, 1024]:
+        bq = m * 256
+        for dE in [1, 2, 3, 5, 8, 20]:
+            x = m * dE / 256.0
+            want = math.floor(math.ldexp(math.exp(-x), 32)) if x < 22.18 else 0
+            got = O.uphill_threshold(bq, dE)
+            assert abs(got - min(want, 2**32 - 1)) <= 1, (m, dE)
+    # off-grid beta: the index truncates beta*dE down to a multiple of 1/256
+    rng = np.random.default_rng(3)
+    tab, L = O.threshold_table()
+    for _ in range(200):
+        bq = int(rng.integers(0, 2**20))
+        dE = int(rng.integers(1, 50))
+        j = (bq * dE) // 256
+        assert O.uphill_threshold(bq, dE) == (int(tab[j]) if j < L else 0)
+
+
+# ---------------------------------------------------------------- k-SAT energy and moves
+@pytest.mark.parametrize("n,m,k,pad", [(10, 42, 3, False), (12, 100, 4, False),
+                                       (9, 30, 4, True)])
+def test_energy_matches_enumeration(n, m, k, pad):
+    lits = small_cnf(n, m, k, seed=n * 100 + m, pad_some=pad)
+    X = all_states(n)
+    want = energies_numpy(lits, X)
+    got = np.array([O.ksat_energy(lits, n, x) for x in X])
+    assert np.array_equal(got, want)
+    assert want.min() >= 0
+
+
+def test_energy_of_generated_instance_matches_independent_count():
+    lits = W.random_ksat(300, 9.6, 4, 11)
+    rng = np.random.default_rng(1)
+    X = rng.integers(0, 2, size=(20, 300), dtype=np.uint8)
+    want = energies_numpy(lits, X)
+    got = np.array([O.ksat_energy(lits, 300, x) for x in X])
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("n,m,k,pad", [(15, 60, 3, False), (20, 190, 4, False),
+                                       (14, 70, 5, True)])
+def test_delta_matches_recomputation(n, m, k, pad):
+    lits = small_cnf(n, m, k, seed=7 * n + m, pad_some=pad)
+    rng = np.random.default_rng(n)
+    for _ in range(6):
+        x = rng.integers(0, 2, size=n, dtype=np.uint8)
+        e0 = energies_numpy(lits, x[None])[0]
+        for v in range(n):
+            y = x.copy()
+            y[v] ^= 1
+            e1 = energies_numpy(lits, y[None])[0]
+            assert O.ksat_delta(lits, n, x, v) == e1 - e0
+
+
+def _adjacency(lits, n):
+    adj = [set() for _ in range(n)]
+    for row in lits:
+        vs = [abs(int(l)) - 1 for l in row if l != 0]
+        for a in vs:
+            for b in vs:
+                if a != b:
+                    adj[a].add(b)
+    return adj
+
+
+@pytest.mark.parametrize("n,alpha,k", [(200, 9.6, 4), (500, 4.2, 3), (50, 2.0, 5)])
+def test_colouring_is_proper_and_greedy(n, alpha, k):
+    lits = W.random_ksat(n, alpha, k, 99 + n)
+    col, nc = O.ksat_colour(lits, n)
+    adj = _adjacency(lits, n)
+    assert col.min() == 0 and col.max() == nc - 1
+    for v in range(n):
+        assert all(col[u] != col[v] for u in adj[v])  # classes are independent sets
+        # greedy in ascending id: every smaller colour is held by a lower-id neighbour
+        lower = {int(col[u]) for u in adj[v] if u < v}
+        assert set(range(col[v])) <= lower
+
+
+# ---------------------------------------------------------------- closed forms of the chain
+def test_beta_zero_flips_every_variable_every_sweep():
+    n = 60
+    lits = W.random_ksat(n, 4.2, 3, 5)
+    beta = np.zeros((n, 9), dtype=np.float32)
+    r0 = O.ksat_anneal(lits, n, beta, 0, 0, seed=3, replicas=40)
+    for t1 in [1, 2, 5, 9]:
+        r = O.ksat_anneal(lits, n, beta, 0, t1, seed=3, replicas=40)
+        assert np.array_equal(r["states"], r0["states"] ^ np.uint8(t1 & 1))
+        assert np.array_equal(r["energies"], energies_numpy(lits, r["states"]))
+
+
+def test_infinite_beta_never_goes_uphill():
+    n = 120
+    lits = W.random_ksat(n, 9.6, 4, 8)
+    T = 12
+    beta = np.full((n, T), 65535.0, dtype=np.float32)
+    st = O.ksat_anneal(lits, n, beta, 0, 0, seed=4, replicas=16)
+    prev = st["energies"].copy()
+    best = st["best_energies"].copy()
+    bstates = st["best_states"].copy()
+    for t in range(T):
+        st = O.ksat_anneal(lits, n, beta, t, t + 1, seed=4, replicas=16, init=st["states"],
+                           init_best=bstates, init_best_energy=best)
+        assert np.all(st["energies"] <= prev)
+        prev = st["energies"].copy()
+        best, bstates = st["best_energies"], st["best_states"]
+    assert np.array_equal(best, prev)  # a descent's best is its last state
+
+
+def test_invariants_segments_and_replica_subsets():
+    wl = W.workload_ksat_small(60)
+    lits, n, beta = wl["lits"], wl["n_vars"], wl["beta"]
+    full = O.ksat_anneal(lits, n, beta, 0, 60, seed=1, replicas=24)
+    assert np.all(full["energies"] >= 0)
+    assert np.array_equal(full["energies"], energies_numpy(lits, full["states"]))
+    assert np.array_equal(full["best_energies"], energies_numpy(lits, full["best_states"]))
+    assert np.all(full["best_energies"] <= full["energies"])
+    init = O.ksat_anneal(lits, n, beta, 0, 0, seed=1, replicas=24)
+    assert np.all(full["best_energies"] <= init["energies"])
+    # segment invariance: [0,25) then [25,60) from the resident state and best
+    a = O.ksat_anneal(lits, n, beta, 0, 25, seed=1, replicas=24)
+    b = O.ksat_anneal(lits, n, beta, 25, 60, seed=1, replicas=24, init=a["states"],
+                      init_best=a["best_states"], init_best_energy=a["best_energies"])
+    for key in ["states", "energies", "best_energies", "best_states"]:
+        assert np.array_equal(b[key], full[key]), key
+    # best is the minimum over sweep ends, earliest kept
+    st, mins = init, init["energies"].copy()
+    for t in range(60):
+        st = O.ksat_anneal(lits, n, beta, t, t + 1, seed=1, replicas=24, init=st["states"],
+                           init_best=st["best_states"], init_best_energy=st["best_energies"])
+        mins = np.minimum(mins, st["energies"])
+    assert np.array_equal(mins, full["best_energies"])
+    # a replica's trajectory does not depend on which other replicas run
+    ids = np.array([23, 0, 7], dtype=np.int32)
+    sub = O.ksat_anneal(lits, n, beta, 0, 60, seed=1, replica_ids=ids)
+    assert np.array_equal(sub["states"], full["states"][ids])
+    assert np.array_equal(sub["best_energies"], full["best_energies"][ids])
+    # the thread split does not matter
+    one = O.ksat_anneal(lits, n, beta, 0, 60, seed=1, replicas=24, n_threads=1)
+    assert np.array_equal(one["states"], full["states"])
+
+
+def _chi2_pvalue(counts, probs):
+    from scipy import stats
+    counts = np.asarray(counts, dtype=np.float64)
+    exp = np.asarray(probs) * counts.sum()
+    order = np.argsort(exp)
+    # pool the smallest expected cells until each pooled cell expects >= 5
+    obs_p, exp_p, co, ce = [], [], 0.0, 0.0
+    for i in order:
+        co += counts[i]
+        ce += exp[i]
+        if ce >= 5:
+            obs_p.append(co)
+            exp_p.append(ce)
+            co, ce = 0.0, 0.0
+    if ce > 0:
+        obs_p[-1] += co
+        exp_p[-1] += ce
+    return stats.chisquare(obs_p, exp_p).pvalue
+
+
+@pytest.mark.parametrize("beta_num", [128, 256, 512])
+def test_homogeneous_chain_samples_boltzmann(beta_num):
+    """At a fixed homogeneous beta every single-site Metropolis kernel, and so the
+    colour-ordered sweep, leaves exp(-beta E) invariant. beta = beta_num/256 sits on the
+    threshold grid, so the integer rule is exact up to 2^-32."""
+    n = 7
+    lits = small_cnf(n, 24, 3, seed=beta_num)
+    beta_v = beta_num / 256.0
+    T = 25
+    beta = np.full((n, T), beta_v, dtype=np.float32)
+    R = 24000
+    r = O.ksat_anneal(lits, n, beta, 0, T, seed=77 + beta_num, replicas=R)
+    idx = (r["states"].astype(np.int64) << np.arange(n)).sum(axis=1)
+    counts = np.bincount(idx, minlength=2 ** n)
+    E = energies_numpy(lits, all_states(n))
+    w = np.exp(-beta_v * E)
+    p = _chi2_pvalue(counts, w / w.sum())
+    assert p > 1e-4, p
+    # a flipped sign of the energy change would sample exp(+beta E): clearly rejected
+    w_bad = np.exp(+beta_v * E)
+    assert _chi2_pvalue(counts, w_bad / w_bad.sum()) < 1e-6
+
+
+# ---------------------------------------------------------------- QAP
+def _qap_cost_numpy(F, D, p):
+    p = np.asarray(p)
+    return int((F * D[np.ix_(p, p)]).sum())
+
+
+@pytest.mark.parametrize("n", [3, 5, 7])
+def test_qap_cost_matches_enumeration(n):
+    F, D = W.random_qap(n, 40 + n)
+    costs = []
+    for perm in itertools.permutations(range(n)):
+        p = np.array(perm, dtype=np.int16)
+        c = O.qap_cost(F, D, p)
+        assert c == _qap_cost_numpy(F, D, p)
+        costs.append(c)
+    assert min(costs) >= 0
+
+
+def test_qap_swap_delta_matches_recomputation():
+    for n in [2, 3, 6, 17]:
+        F, D = W.random_qap(n, 60 + n)
+        rng = np.random.default_rng(n)
+        for _ in range(4):
+            p = rng.permutation(n).astype(np.int16)
+            c0 = _qap_cost_numpy(F, D, p)
+            for r in range(n):
+                for s in range(n):
+                    if r == s:
+                        continue
+                    q = p.copy()
+                    q[r], q[s] = q[s], q[r]
+                    assert O.qap_swap_delta(F, D, p, r, s) == _qap_cost_numpy(F, D, q) - c0
+
+
+def test_qap_chain_invariants_and_segments():
+    n = 11
+    F, D = W.random_qap(n, 3)
+    beta = W.beta_scaled_linear(n, 40, 0.01, 1.0, 0.5, 1.5, 4)
+    full = O.qap_anneal(F, D, beta, 0, 40, seed=9, replicas=20)
+    for j in range(20):
+        assert sorted(full["perms"][j].tolist()) == list(range(n))
+        assert full["energies"][j] == _qap_cost_numpy(F, D, full["perms"][j])
+        assert full["best_energies"][j] == _qap_cost_numpy(F, D, full["best_perms"][j])
+    assert np.all(full["best_energies"] <= full["energies"])
+    a = O.qap_anneal(F, D, beta, 0, 13, seed=9, replicas=20)
+    b = O.qap_anneal(F, D, beta, 13, 40, seed=9, replicas=20, init=a["perms"],
+                     init_best=a["best_perms"], init_best_energy=a["best_energies"])
+    for k1, k2 in [("perms", "perms"), ("energies", "energies"),
+                   ("best_energies", "best_energies"), ("best_perms", "best_perms")]:
+        assert np.array_equal(b[k1], full[k2])
+    ids = np.array([19, 4], dtype=np.int32)
+    sub = O.qap_anneal(F, D, beta, 0, 40, seed=9, replica_ids=ids)
+    assert np.array_equal(sub["perms"], full["perms"][ids])
+
+
+def test_qap_infinite_beta_never_goes_uphill():
+    n = 20
+    F, D = W.random_qap(n, 5)
+    T = 10
+    beta = np.full((n, T), 65535.0, dtype=np.float32)
+    st = O.qap_anneal(F, D, beta, 0, 0, seed=2, replicas=8)
+    prev = st["energies"].copy()
+    for t in range(T):
+        st = O.qap_anneal(F, D, beta, t, t + 1, seed=2, replicas=8, init=st["perms"],
+                          init_best=st["best_perms"], init_best_energy=st["best_energies"])
+        assert np.all(st["energies"] <= prev)
+        prev = st["energies"].copy()
+
+
+def test_qap_homogeneous_chain_samples_boltzmann():
+    n = 4
+    rng = np.random.default_rng(8)
+    F = rng.integers(0, 4, size=(n, n))
+    F = np.triu(F, 1)
+    F = (F + F.T).astype(np.int32)
+    D = rng.integers(0, 4, size=(n, n))
+    D = np.triu(D, 1)
+    D = (D + D.T).astype(np.int32)
+    beta_v = 64 / 256.0
+    T = 20
+    beta = np.full((n, T), beta_v, dtype=np.float32)
+    R = 24000
+    r = O.qap_anneal(F, D, beta, 0, T, seed=31, replicas=R)
+    perms = list(itertools.permutations(range(n)))
+    index = {p: i for i, p in enumerate(perms)}
+    counts = np.zeros(len(perms))
+    for row in r["perms"]:
+        counts[index[tuple(int(v) for v in row)]] += 1
+    E = np.array([_qap_cost_numpy(F, D, np.array(p)) for p in perms])
+    w = np.exp(-beta_v * (E - E.min()))
+    assert _chi2_pvalue(counts, w / w.sum()) > 1e-4
+    w_bad = np.exp(+beta_v * (E - E.min()))
+    assert _chi2_pvalue(counts, w_bad / w_bad.sum()) < 1e-6
