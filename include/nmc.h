@@ -1,0 +1,166 @@
+/*
+ * nmc.h -- C ABI of the GB300 engine for the inhomogeneous Metropolis sweep of Nonequilibrium
+ * Monte Carlo (NMC; Mohseni et al., arXiv:2111.13628).
+ *
+ * The engine runs the sampling stage of NMC (Algorithm 1, "nonlocal exploration", "local
+ * exploitation" and "unlearning" steps): single-variable Metropolis updates with a separate
+ * inverse temperature beta_v[t] for every variable v at every sweep t (Sec. "Nonequilibrium
+ * inhomogeneous sampling over subgraphs"), over many independent replicas of a random k-SAT
+ * formula (energy = number of violated clauses, Sec. "4-SAT Problems Near Computational Phase
+ * Transitions") or of a Koopmans-Beckmann QAP (swap moves on a permutation, Sec. "Quadratic
+ * Assignment Problems"). A homogeneous profile is the unlearning phase; a short schedule is one
+ * of the learning stage's exploratory runs.
+ *
+ * Dynamics (fixed here so that every result is reproducible bit for bit):
+ *   - sweep order: greedy colouring of the variable-interaction graph in ascending variable
+ *     id; one sweep visits colours in ascending order, every colour class (an independent
+ *     set) updated against the state left by the earlier colours;
+ *   - random numbers: Philox4x32-10 keyed by the 64-bit seed; replica r's attempt on variable
+ *     v at sweep t uses word r&3 of the block for counter (v, t, r>>2, 0x4B535750);
+ *   - acceptance: dE <= 0 always; otherwise with bq = round_half_even(beta * 2^16) and
+ *     j = (bq * dE) >> 8, accept iff u < floor(2^32 exp(-j/256)) (capped at 2^32-1);
+ *   - best-so-far: the initial state, then replaced after any sweep that ends strictly lower.
+ * The QAP chain is defined in nmc_load_qap.
+ *
+ * Conventions: every function returns NMC_OK (0) or a negative NMC_E* code and never aborts;
+ * nmc_last_error() describes the last failure on that context. Host pointers are read during
+ * the call only (the caller keeps ownership); results go to caller-owned buffers. Device
+ * state (instances, schedules, replica sets) is owned by the context and stays resident
+ * until it is released or the context is destroyed. Work is issued on the context's stream;
+ * calls that return host data synchronise that stream. A context is not thread-safe: use one
+ * per host thread, or serialise calls.
+ */
+#ifndef NMC_H_
+#define NMC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NMC_OK 0
+#define NMC_EINVAL (-1)   /* bad argument: ids, sizes, literals, beta outside [0, 65535] */
+#define NMC_ENOMEM (-2)   /* device allocation failed */
+#define NMC_ECUDA (-3)    /* a CUDA call failed (message from the runtime) */
+#define NMC_ETIMEOUT (-4) /* a bounded device-side wait expired; the result is not valid */
+#define NMC_ESTATE (-5)   /* call out of order (no schedule, schedule too short, wrong kind) */
+
+#define NMC_KIND_KSAT 1
+#define NMC_KIND_QAP 2
+
+typedef struct nmc_ctx nmc_ctx;
+
+/* Outputs of a replica set, all caller-owned (host or device, as the call states); any field
+ * may be NULL to skip it. k-SAT states are uint8 [R][N] (0/1, original variable order); QAP
+ * states are int16 [R][n] with p[facility] = location. Energies are int64 [R]. */
+typedef struct nmc_result {
+  void *states;
+  int64_t *energies;
+  int64_t *best_energies;
+  void *best_states;
+} nmc_result;
+
+/* Creates a context on CUDA device `device`. `cuda_stream` is a cudaStream_t to issue work on
+ * (NULL: the context creates and owns a non-blocking stream). */
+int nmc_create(nmc_ctx **out, int device, void *cuda_stream);
+/* Synchronises and frees everything the context owns. NULL is ignored. */
+void nmc_destroy(nmc_ctx *ctx);
+/* Message for the last failed call on ctx (static string when ctx is NULL). */
+const char *nmc_last_error(nmc_ctx *ctx);
+/* Waits for all work issued on the context's stream. */
+int nmc_sync(nmc_ctx *ctx);
+
+/*
+ * Loads a CNF formula (the factor graph of Sec. "k-local factor-graph"; clauses a, variables
+ * i, literals in DIMACS form). lits: n_clauses * k_max int32, clause a in row a, literal
+ * +(v+1) / -(v+1) for x_v / not x_v, 0 for an unused slot. Requirements (else NMC_EINVAL):
+ * 1 <= n_vars < 2^28, 0 <= n_clauses < 2^31, 1 <= k_max <= 8, every |literal| <= n_vars,
+ * at least one literal per clause, no variable twice in one clause, every variable in at most
+ * 1023 clauses. Builds, on the host, the colouring and the occurrence lists, and uploads them.
+ * *inst_out receives the instance id.
+ */
+int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max,
+                  const int32_t *lits, int32_t *inst_out);
+
+/*
+ * Loads a Koopmans-Beckmann QAP (Sec. "Quadratic Assignment Problems", without the placement
+ * term): cost C(p) = sum_ij F[i][j] D[p(i)][p(j)]. F (flows) and D (distances) are n*n int32,
+ * row-major, symmetric, zero diagonal, entries in [0, 255]; 1 <= n <= 256 (else NMC_EINVAL).
+ * One schedule step is n swap attempts; attempt a of step t of replica r draws the Philox block
+ * for counter (a, t, r, 0x51535450): facility r_ = (u0 n) >> 32, s' = (u1 (n-1)) >> 32,
+ * s = s' + (s' >= r_), and u2 decides an uphill swap at bq = (bq_r_[t] + bq_s[t]) >> 1.
+ */
+int nmc_load_qap(nmc_ctx *ctx, int32_t n, const int32_t *F, const int32_t *D, int32_t *inst_out);
+
+/* Releases an instance, its schedule and nothing else (replica sets of it must be released
+ * first, else NMC_ESTATE). */
+int nmc_unload(nmc_ctx *ctx, int32_t inst);
+
+/* Number of colours and, if colour_out != NULL, the colour of every variable (int32 [N]) of a
+ * k-SAT instance. */
+int nmc_ksat_colouring(nmc_ctx *ctx, int32_t inst, int32_t *colour_out, int32_t *n_colours);
+
+/*
+ * Sets the inverse-temperature profile beta[unit][step] of an instance (units = variables or
+ * facilities): n_units * n_steps float32, row-major (row = one unit's schedule), host memory.
+ * Every value must be finite and in [0, 65535] (checked on the device; else NMC_EINVAL). The
+ * profile is quantised to Q16 and stored step-major on the device. Replaces any earlier one.
+ */
+int nmc_set_schedule(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const float *beta);
+/* As nmc_set_schedule, with beta in device memory (read on the context's stream). */
+int nmc_set_schedule_device(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const float *beta_dev);
+
+/*
+ * Creates a resident replica set of `replicas` chains (1..4096) of an instance, seeded by
+ * `seed`. init_states (host, nullable): k-SAT uint8 [R][N] 0/1, QAP int16 [R][n] permutations;
+ * NULL draws the initial states from Philox (k-SAT: bit 0 of word r&3 for counter
+ * (v, 0, r>>2, 0x4B494E49); QAP: Fisher-Yates from the identity, position q (n-1 down to 1)
+ * exchanged with (u (q+1)) >> 32 for u word 0 of counter (q, 0, r, 0x51494E49)). Computes the
+ * energies; best-so-far = initial. *rs_out receives the replica-set id.
+ */
+int nmc_replicas_create(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t seed,
+                        const void *init_states, int32_t *rs_out);
+/* Re-initialises an existing replica set in place (no allocation): new seed, new initial
+ * states (init_states as in nmc_replicas_create), energies recomputed, best-so-far reset. */
+int nmc_replicas_reset(nmc_ctx *ctx, int32_t rs, uint64_t seed, const void *init_states);
+/* Frees a replica set. */
+int nmc_replicas_destroy(nmc_ctx *ctx, int32_t rs);
+/*
+ * Runs sweeps (k-SAT) or steps (QAP) t0..t1-1 of the schedule on the resident replica set,
+ * asynchronously on the context's stream. t is absolute, so [t0,t1) then [t1,t2) equals
+ * [t0,t2) bit for bit. Requires 0 <= t0 <= t1 <= n_steps of the current schedule
+ * (NMC_ESTATE otherwise). A device-side wait that expires is reported as NMC_ETIMEOUT by the
+ * next synchronising call on this replica set.
+ */
+int nmc_replicas_run(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1);
+/* Copies the replica set's current states, energies, best energies and best states to host
+ * buffers (synchronises). */
+int nmc_replicas_read(nmc_ctx *ctx, int32_t rs, const nmc_result *out);
+/* As nmc_replicas_read, into device buffers, asynchronously on the context's stream. */
+int nmc_replicas_read_device(nmc_ctx *ctx, int32_t rs, const nmc_result *out_dev);
+
+/*
+ * One-shot anneal through host memory: creates a replica set, runs [t0, t1), copies the
+ * results to the host buffers in *out and frees the set. Arguments as above.
+ */
+int nmc_anneal(nmc_ctx *ctx, int32_t inst, int32_t replicas, int32_t t0, int32_t t1,
+               uint64_t seed, const void *init_states, const nmc_result *out);
+
+/* Self-test of the bounded device wait: launches one CTA that waits at the grid barrier the
+ * sweep kernel uses, for a second arrival that never comes, with the given limit in
+ * milliseconds (1..10000). Returns NMC_ETIMEOUT when the wait expired and was reported as
+ * the sweep would report it, NMC_OK if it did not expire (a defect), or an error code. The
+ * context stays usable afterwards. */
+int nmc_selftest_wait_timeout(nmc_ctx *ctx, int32_t timeout_ms);
+
+/* The library's acceptance-threshold table: writes min(cap, L) entries
+ * floor(2^32 exp(-j/256)) (entry 0 capped at 2^32-1) and returns L, the index of the first
+ * zero entry. */
+int32_t nmc_threshold_table(uint32_t *out, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMC_H_ */

@@ -1,0 +1,273 @@
+"""GB300 engine for the inhomogeneous Metropolis sweep of Nonequilibrium Monte Carlo.
+
+Thin ctypes binding over libnmc.so, whose C ABI is declared in include/nmc.h. Every step of
+the sweep runs in the library's CUDA kernels; this module only marshals arguments. PyTorch is
+used, where the caller wants it, for device buffers and streams (tensors are passed to the
+library as raw device pointers). There is no CPU fallback: if the library cannot be built or
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+NMC_OK = 0
+NMC_EINVAL = -1
+NMC_ENOMEM = -2
+NMC_ECUDA = -3
+NMC_ETIMEOUT = -4
+NMC_ESTATE = -5
+KIND_KSAT = 1
+KIND_QAP = 2
+
+_ERRNAMES = {NMC_EINVAL: "EINVAL", NMC_ENOMEM: "ENOMEM", NMC_ECUDA: "ECUDA",
+             NMC_ETIMEOUT: "ETIMEOUT", NMC_ESTATE: "ESTATE"}
+
+
+class NmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nmc {_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Result(C.Structure):
+    _fields_ = [("states", C.c_void_p), ("energies", C.c_void_p),
+                ("best_energies", C.c_void_p), ("best_states", C.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# Exported C-ABI symbols (every function declared in include/nmc.h).
+SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_ksat",
+           "nmc_load_qap", "nmc_unload", "nmc_ksat_colouring", "nmc_set_schedule",
+           "nmc_set_schedule_device", "nmc_replicas_create", "nmc_replicas_reset", "nmc_replicas_destroy",
+           "nmc_replicas_run", "nmc_replicas_read", "nmc_replicas_read_device", "nmc_anneal",
+           "nmc_threshold_table", "nmc_selftest_wait_timeout"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libnmc.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and _build.stale():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libnmc.so is not built; run __graft_entry__.build()")
+        lib = C.CDLL(_build.LIB)
+        P, i32, u64 = C.c_void_p, C.c_int32, C.c_uint64
+        sig = {
+            "nmc_create": ([P, C.c_int, P], C.c_int),
+            "nmc_destroy": ([P], None),
+            "nmc_last_error": ([P], C.c_char_p),
+            "nmc_sync": ([P], C.c_int),
+            "nmc_load_ksat": ([P, i32, i32, i32, P, P], C.c_int),
+            "nmc_load_qap": ([P, i32, P, P, P], C.c_int),
+            "nmc_unload": ([P, i32], C.c_int),
+            "nmc_ksat_colouring": ([P, i32, P, P], C.c_int),
+            "nmc_set_schedule": ([P, i32, i32, P], C.c_int),
+            "nmc_set_schedule_device": ([P, i32, i32, P], C.c_int),
+            "nmc_replicas_create": ([P, i32, i32, u64, P, P], C.c_int),
+            "nmc_replicas_reset": ([P, i32, u64, P], C.c_int),
+            "nmc_replicas_destroy": ([P, i32], C.c_int),
+            "nmc_replicas_run": ([P, i32, i32, i32], C.c_int),
+            "nmc_replicas_read": ([P, i32, P], C.c_int),
+            "nmc_replicas_read_device": ([P, i32, P], C.c_int),
+            "nmc_anneal": ([P, i32, i32, i32, i32, u64, P, P], C.c_int),
+            "nmc_threshold_table": ([P, i32], i32),
+            "nmc_selftest_wait_timeout": ([P, i32], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def threshold_table(cap: int = 8192):
+    """(table uint32[L], L) as built by the library."""
+    lib = load()
+    out = np.zeros(cap, dtype=np.uint32)
+    n = lib.nmc_threshold_table(_ptr(out), cap)
+    return out[:n].copy(), int(n)
+
+
+class Context:
+    """One nmc_ctx: a device, a stream, and the instances / replica sets resident on it."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = load()
+        self._kinds = {}
+        self._units = {}
+        self._rs = {}
+        h = C.c_void_p()
+        s = None
+        if stream is not None:
+            s = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        rc = self._lib.nmc_create(C.byref(h), int(device), s)
+        if rc != NMC_OK:
+            raise NmcError(rc, "nmc_create failed")
+        self._h = h
+
+    # -- plumbing
+    def _check(self, rc):
+        if rc != NMC_OK:
+            raise NmcError(rc, self._lib.nmc_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nmc_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def selftest_wait_timeout(self, timeout_ms: int) -> int:
+        """Return code of nmc_selftest_wait_timeout (NMC_ETIMEOUT when the wait expired)."""
+        return int(self._lib.nmc_selftest_wait_timeout(self._h, int(timeout_ms)))
+
+    def sync(self):
+        self._check(self._lib.nmc_sync(self._h))
+
+    # -- instances
+    def load_ksat(self, lits, n_vars: int) -> int:
+        lits = np.ascontiguousarray(lits, dtype=np.int32)
+        if lits.ndim != 2:
+            raise ValueError("lits must be [n_clauses, k_max]")
+        inst = C.c_int32()
+        self._check(self._lib.nmc_load_ksat(self._h, int(n_vars), lits.shape[0], lits.shape[1],
+                                            _ptr(lits), C.byref(inst)))
+        self._kinds[inst.value] = KIND_KSAT
+        self._units[inst.value] = int(n_vars)
+        return inst.value
+
+    def load_qap(self, F, D) -> int:
+        F = np.ascontiguousarray(F, dtype=np.int32)
+        D = np.ascontiguousarray(D, dtype=np.int32)
+        if F.ndim != 2 or F.shape[0] != F.shape[1] or D.shape != F.shape:
+            raise ValueError("F and D must be n x n")
+        inst = C.c_int32()
+        self._check(self._lib.nmc_load_qap(self._h, F.shape[0], _ptr(F), _ptr(D), C.byref(inst)))
+        self._kinds[inst.value] = KIND_QAP
+        self._units[inst.value] = F.shape[0]
+        return inst.value
+
+    def unload(self, inst: int):
+        self._check(self._lib.nmc_unload(self._h, int(inst)))
+
+    def ksat_colouring(self, inst: int):
+        n = self._units[inst]
+        col = np.zeros(n, dtype=np.int32)
+        nc = C.c_int32()
+        self._check(self._lib.nmc_ksat_colouring(self._h, int(inst), _ptr(col), C.byref(nc)))
+        return col, nc.value
+
+    def set_schedule(self, inst: int, beta):
+        """beta: [n_units, n_steps] float32, numpy (host) or a CUDA torch tensor (device)."""
+        if hasattr(beta, "is_cuda") and beta.is_cuda:
+            if beta.dtype.__str__() != "torch.float32" or not beta.is_contiguous():
+                raise ValueError("device beta must be a contiguous float32 tensor")
+            self._check(self._lib.nmc_set_schedule_device(self._h, int(inst), beta.shape[1],
+                                                          _ptr(beta)))
+            return
+        if hasattr(beta, "numpy"):
+            beta = beta.numpy()
+        beta = np.ascontiguousarray(beta, dtype=np.float32)
+        if beta.ndim != 2 or beta.shape[0] != self._units[inst]:
+            raise ValueError("beta must be [n_units, n_steps]")
+        self._check(self._lib.nmc_set_schedule(self._h, int(inst), beta.shape[1], _ptr(beta)))
+
+    # -- replica sets
+    def replicas_create(self, inst: int, replicas: int, seed: int, init=None) -> int:
+        if init is not None:
+            dt = np.uint8 if self._kinds[inst] == KIND_KSAT else np.int16
+            init = np.ascontiguousarray(init, dtype=dt)
+            if init.shape != (replicas, self._units[inst]):
+                raise ValueError("init must be [replicas, n_units]")
+        rs = C.c_int32()
+        self._check(self._lib.nmc_replicas_create(self._h, int(inst), int(replicas),
+                                                  int(seed) & (2**64 - 1), _ptr(init),
+                                                  C.byref(rs)))
+        self._rs[rs.value] = (inst, int(replicas))
+        return rs.value
+
+    def replicas_reset(self, rs: int, seed: int, init=None):
+        inst, R = self._rs[rs]
+        if init is not None:
+            dt = np.uint8 if self._kinds[inst] == KIND_KSAT else np.int16
+            init = np.ascontiguousarray(init, dtype=dt)
+            if init.shape != (R, self._units[inst]):
+                raise ValueError("init must be [replicas, n_units]")
+        self._check(self._lib.nmc_replicas_reset(self._h, int(rs), int(seed) & (2**64 - 1),
+                                                 _ptr(init)))
+
+    def replicas_destroy(self, rs: int):
+        self._check(self._lib.nmc_replicas_destroy(self._h, int(rs)))
+        self._rs.pop(rs, None)
+
+    def replicas_run(self, rs: int, t0: int, t1: int):
+        self._check(self._lib.nmc_replicas_run(self._h, int(rs), int(t0), int(t1)))
+
+    def _alloc_out(self, inst, R, host=True):
+        n = self._units[inst]
+        dt = np.uint8 if self._kinds[inst] == KIND_KSAT else np.int16
+        return dict(states=np.zeros((R, n), dtype=dt), energies=np.zeros(R, dtype=np.int64),
+                    best_energies=np.zeros(R, dtype=np.int64),
+                    best_states=np.zeros((R, n), dtype=dt))
+
+    def replicas_read(self, rs: int) -> dict:
+        inst, R = self._rs[rs]
+        out = self._alloc_out(inst, R)
+        res = Result(_ptr(out["states"]), _ptr(out["energies"]), _ptr(out["best_energies"]),
+                     _ptr(out["best_states"]))
+        self._check(self._lib.nmc_replicas_read(self._h, int(rs), C.byref(res)))
+        return out
+
+    def replicas_read_device(self, rs: int, states=None, energies=None, best_energies=None,
+                             best_states=None):
+        """Writes into caller-owned CUDA tensors (any may be None), asynchronously."""
+        res = Result(_ptr(states), _ptr(energies), _ptr(best_energies), _ptr(best_states))
+        self._check(self._lib.nmc_replicas_read_device(self._h, int(rs), C.byref(res)))
+
+    def anneal(self, inst: int, replicas: int, t0: int, t1: int, seed: int, init=None,
+               out=None) -> dict:
+        """One-shot anneal through host buffers (nmc_anneal)."""
+        if init is not None:
+            dt = np.uint8 if self._kinds[inst] == KIND_KSAT else np.int16
+            init = np.ascontiguousarray(init, dtype=dt)
+        if out is None:
+            out = self._alloc_out(inst, replicas)
+        res = Result(_ptr(out.get("states")), _ptr(out.get("energies")),
+                     _ptr(out.get("best_energies")), _ptr(out.get("best_states")))
+        self._check(self._lib.nmc_anneal(self._h, int(inst), int(replicas), int(t0), int(t1),
+                                         int(seed) & (2**64 - 1), _ptr(init), C.byref(res)))
+        return out

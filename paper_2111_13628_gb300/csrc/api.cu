@@ -1,0 +1,754 @@
+// Host side of the C ABI declared in include/nmc.h: argument checks, the instance build
+// (greedy colouring, renumbering, occurrence lists), device residency of instances, schedules
+// and replica sets, and the dispatch to the kernels in ksat.cu and qap.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "nmc.h"
+#include "nmc_internal.h"
+
+using namespace nmc;
+
+namespace {
+
+struct Instance {
+  int kind = 0;
+  int32_t n_units = 0;
+  KsatDevice ks{};
+  QapDevice qp{};
+  std::vector<int32_t> colour;  // k-SAT: colour of every original variable
+  uint32_t *bq = nullptr;       // [n_steps][n_units] Q16, step-major (new ids for k-SAT)
+  int32_t n_steps = 0;
+  int users = 0;  // live replica sets
+};
+
+struct ReplicaSet {
+  int32_t inst = -1;
+  int32_t R = 0;
+  uint64_t seed = 0;
+  KsatReplicas ks{};
+  QapReplicas qp{};
+};
+
+const char *kStaticNoCtx = "nmc: no context";
+
+// Acceptance thresholds Tab[j] = min(2^32-1, floor(2^32 exp(-j/256))), computed in IEEE
+// double with the host C library's exp; returns the index of the first zero entry.
+int32_t build_table(uint32_t *out, int32_t cap) {
+  int32_t len = -1;
+  for (int32_t j = 0; j < cap; ++j) {
+    const double scaled = std::ldexp(std::exp(-static_cast<double>(j) / 256.0), 32);
+    const uint32_t t = scaled >= 4294967295.0 ? 0xFFFFFFFFu : static_cast<uint32_t>(std::floor(scaled));
+    if (t == 0u) {
+      len = j;
+      for (int32_t q = j; q < cap; ++q) out[q] = 0u;
+      break;
+    }
+    out[j] = t;
+  }
+  return len;
+}
+
+}  // namespace
+
+struct nmc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::map<int32_t, Instance> insts;
+  std::map<int32_t, ReplicaSet> sets;
+  int32_t next_inst = 1, next_set = 1;
+  uint32_t *tab = nullptr;
+  int32_t tab_len = 0;
+  int32_t *flag = nullptr;  // device scratch flag for schedule validation
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int fail(nmc_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(nmc_ctx *c, cudaError_t e, const char *what) {
+  cudaGetLastError();
+  const int code = (e == cudaErrorMemoryAllocation) ? NMC_ENOMEM : NMC_ECUDA;
+  return fail(c, code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define NMC_CUDA(call, what)                     \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * count);
+}
+
+template <typename T>
+void dev_free(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_instance(Instance &I) {
+  dev_free(I.ks.occ);
+  dev_free(I.ks.occ_ptr);
+  dev_free(I.ks.col_ptr);
+  dev_free(I.ks.orig);
+  dev_free(I.ks.newid);
+  dev_free(I.ks.clits);
+  dev_free(I.qp.F);
+  dev_free(I.qp.D);
+  dev_free(I.bq);
+}
+
+void free_set(ReplicaSet &S) {
+  dev_free(S.ks.S);
+  dev_free(S.ks.best);
+  dev_free(S.ks.energy);
+  dev_free(S.ks.best_energy);
+  dev_free(S.ks.imp);
+  dev_free(S.ks.bar);
+  dev_free(S.qp.perm);
+  dev_free(S.qp.best_perm);
+  dev_free(S.qp.energy);
+  dev_free(S.qp.best_energy);
+}
+
+Instance *find_inst(nmc_ctx *ctx, int32_t id) {
+  auto it = ctx->insts.find(id);
+  return it == ctx->insts.end() ? nullptr : &it->second;
+}
+
+ReplicaSet *find_set(nmc_ctx *ctx, int32_t id) {
+  auto it = ctx->sets.find(id);
+  return it == ctx->sets.end() ? nullptr : &it->second;
+}
+
+// Checks the sticky timeout word of a k-SAT replica set after its stream was synchronised.
+int check_timeout(nmc_ctx *ctx, ReplicaSet &S) {
+  if (!S.ks.bar) return NMC_OK;
+  int sticky = 0;
+  NMC_CUDA(cudaMemcpy(&sticky, &S.ks.bar->sticky, sizeof(int), cudaMemcpyDeviceToHost),
+           "read barrier status");
+  if (sticky) {
+    const int zero = 0;
+    cudaMemcpy(&S.ks.bar->sticky, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    return fail(ctx, NMC_ETIMEOUT, "a grid barrier wait expired; the sweep stopped early");
+  }
+  return NMC_OK;
+}
+
+// Host-side check of caller-given initial states.
+int check_init(nmc_ctx *ctx, const Instance &I, int32_t replicas, const void *init_states) {
+  if (!init_states) return NMC_OK;
+  if (I.kind == NMC_KIND_KSAT) {
+    const uint8_t *p = static_cast<const uint8_t *>(init_states);
+    for (size_t i = 0; i < static_cast<size_t>(replicas) * I.ks.n; ++i)
+      if (p[i] > 1) return fail(ctx, NMC_EINVAL, "k-SAT initial states must be 0/1");
+    return NMC_OK;
+  }
+  const int32_t n = I.qp.n;
+  const int16_t *p = static_cast<const int16_t *>(init_states);
+  std::vector<int> seen(n);
+  for (int32_t r = 0; r < replicas; ++r) {
+    std::fill(seen.begin(), seen.end(), 0);
+    for (int32_t k = 0; k < n; ++k) {
+      const int16_t x = p[static_cast<size_t>(r) * n + k];
+      if (x < 0 || x >= n || seen[x]++)
+        return fail(ctx, NMC_EINVAL, "QAP initial states must be permutations");
+    }
+  }
+  return NMC_OK;
+}
+
+// Initial states (Philox or given), energies and best-so-far of an allocated replica set.
+int init_replicas(nmc_ctx *ctx, const Instance &I, ReplicaSet &S, const void *init_states) {
+  cudaError_t e = cudaSuccess;
+  void *init_dev = nullptr;
+  const size_t n = static_cast<size_t>(I.n_units);
+  const size_t bytes = static_cast<size_t>(S.R) * n * (I.kind == NMC_KIND_KSAT ? 1 : 2);
+  if (init_states) {
+    if ((e = cudaMallocAsync(&init_dev, bytes, ctx->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(init_dev, init_states, bytes, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "upload initial states");
+  }
+  if (I.kind == NMC_KIND_KSAT) {
+    e = cudaMemsetAsync(S.ks.imp, 0, sizeof(uint32_t) * S.ks.W, ctx->stream);
+    if (e == cudaSuccess)
+      e = ksat_init_states(I.ks, S.ks, S.seed, static_cast<const uint8_t *>(init_dev), ctx->stream);
+    if (e == cudaSuccess) e = ksat_energies(I.ks, S.ks, ctx->stream);
+  } else {
+    e = qap_init_states(I.qp, S.qp, S.seed, static_cast<const int16_t *>(init_dev), ctx->stream);
+  }
+  if (init_dev) cudaFreeAsync(init_dev, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "initialise replicas");
+  return NMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nmc_create(nmc_ctx **out, int device, void *cuda_stream) {
+  if (!out) return NMC_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return NMC_EINVAL;
+  }
+  nmc_ctx *ctx = new nmc_ctx();
+  ctx->device = device;
+  DeviceGuard g(device);
+  if (!g.ok) {
+    delete ctx;
+    return NMC_ECUDA;
+  }
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return NMC_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  std::vector<uint32_t> tab(kTabCap);
+  ctx->tab_len = build_table(tab.data(), kTabCap);
+  if (cudaMalloc(&ctx->tab, sizeof(uint32_t) * kTabCap) != cudaSuccess ||
+      cudaMemcpy(ctx->tab, tab.data(), sizeof(uint32_t) * kTabCap, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMalloc(&ctx->flag, sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    nmc_destroy(ctx);
+    return NMC_ENOMEM;
+  }
+  *out = ctx;
+  return NMC_OK;
+}
+
+void nmc_destroy(nmc_ctx *ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto &kv : ctx->sets) free_set(kv.second);
+  for (auto &kv : ctx->insts) free_instance(kv.second);
+  dev_free(ctx->tab);
+  dev_free(ctx->flag);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  cudaGetLastError();
+  delete ctx;
+}
+
+const char *nmc_last_error(nmc_ctx *ctx) { return ctx ? ctx->err.c_str() : kStaticNoCtx; }
+
+int nmc_sync(nmc_ctx *ctx) {
+  if (!ctx) return NMC_EINVAL;
+  DeviceGuard g(ctx->device);
+  NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  for (auto &kv : ctx->sets) {
+    const int rc = check_timeout(ctx, kv.second);
+    if (rc != NMC_OK) return rc;
+  }
+  return NMC_OK;
+}
+
+int nmc_selftest_wait_timeout(nmc_ctx *ctx, int32_t timeout_ms) {
+  if (!ctx) return NMC_EINVAL;
+  if (timeout_ms < 1 || timeout_ms > 10000) return fail(ctx, NMC_EINVAL, "timeout_ms out of range");
+  DeviceGuard g(ctx->device);
+  GridBarrier *gb = nullptr;
+  NMC_CUDA(cudaMalloc(&gb, sizeof(GridBarrier)), "allocate barrier");
+  cudaError_t e = cudaMemset(gb, 0, sizeof(GridBarrier));
+  if (e == cudaSuccess) e = wait_selftest(gb, 1000000ull * (unsigned long long)timeout_ms, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  GridBarrier host{};
+  if (e == cudaSuccess) e = cudaMemcpy(&host, gb, sizeof(GridBarrier), cudaMemcpyDeviceToHost);
+  cudaFree(gb);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "wait self-test");
+  if (host.sticky && host.error) return fail(ctx, NMC_ETIMEOUT, "bounded wait expired as designed");
+  return NMC_OK;
+}
+
+int32_t nmc_threshold_table(uint32_t *out, int32_t cap) {
+  std::vector<uint32_t> tab(kTabCap);
+  const int32_t len = build_table(tab.data(), kTabCap);
+  if (out)
+    for (int32_t j = 0; j < cap; ++j) out[j] = j < kTabCap ? tab[j] : 0u;
+  return len;
+}
+
+int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max,
+                  const int32_t *lits, int32_t *inst_out) {
+  if (!ctx) return NMC_EINVAL;
+  if (!inst_out) return fail(ctx, NMC_EINVAL, "inst_out is NULL");
+  if (n_vars < 1 || n_vars >= (1 << 28)) return fail(ctx, NMC_EINVAL, "n_vars out of range");
+  if (n_clauses < 0) return fail(ctx, NMC_EINVAL, "n_clauses < 0");
+  if (k_max < 1 || k_max > 8) return fail(ctx, NMC_EINVAL, "k_max must be in [1, 8]");
+  if (n_clauses > 0 && !lits) return fail(ctx, NMC_EINVAL, "lits is NULL");
+  const int32_t n = n_vars, m = n_clauses, K = k_max;
+  // -- checks and variable -> clause incidence (clauses in ascending order)
+  std::vector<int32_t> deg(n + 1, 0);
+  for (int64_t a = 0; a < m; ++a) {
+    int used = 0;
+    for (int q = 0; q < K; ++q) {
+      const int32_t l = lits[a * K + q];
+      if (l == 0) continue;
+      if (l < -n || l > n) return fail(ctx, NMC_EINVAL, "literal out of range in clause " + std::to_string(a));
+      const int32_t v = (l > 0 ? l : -l) - 1;
+      for (int q2 = 0; q2 < q; ++q2) {
+        const int32_t l2 = lits[a * K + q2];
+        if (l2 != 0 && ((l2 > 0 ? l2 : -l2) - 1) == v)
+          return fail(ctx, NMC_EINVAL, "variable repeated in clause " + std::to_string(a));
+      }
+      ++used;
+      ++deg[v];
+    }
+    if (used == 0) return fail(ctx, NMC_EINVAL, "empty clause " + std::to_string(a));
+  }
+  int32_t dmax = 0;
+  for (int32_t v = 0; v < n; ++v) dmax = deg[v] > dmax ? deg[v] : dmax;
+  if (dmax > kMaxDegree)
+    return fail(ctx, NMC_EINVAL, "a variable occurs in more than 1023 clauses");
+  std::vector<int32_t> vptr(n + 1, 0);
+  for (int32_t v = 0; v < n; ++v) vptr[v + 1] = vptr[v] + deg[v];
+  std::vector<int32_t> vcl(vptr[n] > 0 ? vptr[n] : 1);
+  {
+    std::vector<int32_t> fill(vptr.begin(), vptr.end() - 1);
+    for (int64_t a = 0; a < m; ++a)
+      for (int q = 0; q < K; ++q) {
+        const int32_t l = lits[a * K + q];
+        if (l != 0) vcl[fill[(l > 0 ? l : -l) - 1]++] = static_cast<int32_t>(a);
+      }
+  }
+  // -- greedy colouring in ascending id: smallest colour absent among coloured neighbours
+  std::vector<int32_t> colour(n, -1);
+  std::vector<int32_t> stamp(static_cast<size_t>(dmax) * (K > 1 ? K - 1 : 1) + 2, -1);
+  int32_t n_colours = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    for (int32_t e = vptr[v]; e < vptr[v + 1]; ++e) {
+      const int64_t a = vcl[e];
+      for (int q = 0; q < K; ++q) {
+        const int32_t l = lits[a * K + q];
+        if (l == 0) continue;
+        const int32_t u = (l > 0 ? l : -l) - 1;
+        const int32_t cu = colour[u];
+        if (u != v && cu >= 0 && cu < static_cast<int32_t>(stamp.size())) stamp[cu] = v;
+      }
+    }
+    int32_t c = 0;
+    while (c < static_cast<int32_t>(stamp.size()) && stamp[c] == v) ++c;
+    colour[v] = c;
+    if (c + 1 > n_colours) n_colours = c + 1;
+  }
+  // -- renumber: colour-major, original id minor
+  std::vector<int32_t> col_ptr(n_colours + 1, 0);
+  for (int32_t v = 0; v < n; ++v) ++col_ptr[colour[v] + 1];
+  for (int32_t c = 0; c < n_colours; ++c) col_ptr[c + 1] += col_ptr[c];
+  std::vector<int32_t> orig(n), newid(n);
+  {
+    std::vector<int32_t> fill(col_ptr.begin(), col_ptr.end() - 1);
+    for (int32_t v = 0; v < n; ++v) {
+      const int32_t p = fill[colour[v]]++;
+      orig[p] = v;
+      newid[v] = p;
+    }
+  }
+  // -- occurrence lists in new ids, each padded to a multiple of 4 occurrences
+  const int kq = K <= 4 ? 1 : 2;
+  const int slots = 4 * kq;
+  const int32_t lit_false = 2 * n, lit_true = 2 * n + 1;
+  std::vector<int32_t> occ_ptr(n + 1, 0);
+  for (int32_t v = 0; v < n; ++v) occ_ptr[v + 1] = occ_ptr[v] + ((deg[orig[v]] + 3) & ~3);
+  const int64_t n_occ = occ_ptr[n];
+  std::vector<int32_t> occ(static_cast<size_t>(n_occ > 0 ? n_occ : 1) * slots, lit_false);
+  for (int32_t v = 0; v < n; ++v) {
+    const int32_t ov = orig[v];
+    int64_t o = occ_ptr[v];
+    for (int32_t e = vptr[ov]; e < vptr[ov + 1]; ++e, ++o) {
+      const int64_t a = vcl[e];
+      int32_t *slot = &occ[static_cast<size_t>(o) * slots];
+      int s = 1;
+      for (int q = 0; q < K; ++q) {
+        const int32_t l = lits[a * K + q];
+        if (l == 0) continue;
+        const int32_t u = (l > 0 ? l : -l) - 1;
+        const int32_t neg = l < 0 ? 1 : 0;
+        if (u == ov)
+          slot[0] = neg ? -1 : 0;
+        else
+          slot[s++] = 2 * newid[u] + neg;
+      }
+    }
+    for (; o < occ_ptr[v + 1]; ++o) {  // padding: a satisfied pseudo-clause (no effect)
+      int32_t *slot = &occ[static_cast<size_t>(o) * slots];
+      slot[0] = 0;
+      slot[1] = lit_true;
+    }
+  }
+  std::vector<int32_t> clits(static_cast<size_t>(m > 0 ? m : 1) * K, lit_false);
+  for (int64_t a = 0; a < m; ++a)
+    for (int q = 0; q < K; ++q) {
+      const int32_t l = lits[a * K + q];
+      if (l == 0) continue;
+      const int32_t u = (l > 0 ? l : -l) - 1;
+      clits[a * K + q] = 2 * newid[u] + (l < 0 ? 1 : 0);
+    }
+  int nb = 2;
+  while ((1 << nb) <= dmax) ++nb;
+  // -- upload
+  DeviceGuard g(ctx->device);
+  Instance I;
+  I.kind = NMC_KIND_KSAT;
+  I.n_units = n;
+  I.ks.n = n;
+  I.ks.m = m;
+  I.ks.kmax = K;
+  I.ks.n_colours = n_colours;
+  I.ks.kq = kq;
+  I.ks.nb = nb;
+  I.ks.n_occ = static_cast<int32_t>(n_occ);
+  I.colour = colour;
+  cudaError_t e = cudaSuccess;
+  if ((e = dev_alloc(&I.ks.occ, occ.size() / 4)) != cudaSuccess ||
+      (e = dev_alloc(&I.ks.occ_ptr, n + 1)) != cudaSuccess ||
+      (e = dev_alloc(&I.ks.col_ptr, n_colours + 1)) != cudaSuccess ||
+      (e = dev_alloc(&I.ks.orig, n)) != cudaSuccess ||
+      (e = dev_alloc(&I.ks.newid, n)) != cudaSuccess ||
+      (e = dev_alloc(&I.ks.clits, clits.size())) != cudaSuccess ||
+      (e = cudaMemcpy(I.ks.occ, occ.data(), sizeof(int32_t) * occ.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(I.ks.occ_ptr, occ_ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(I.ks.col_ptr, col_ptr.data(), sizeof(int32_t) * (n_colours + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(I.ks.orig, orig.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(I.ks.newid, newid.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(I.ks.clits, clits.data(), sizeof(int32_t) * clits.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    free_instance(I);
+    return cuda_fail(ctx, e, "upload k-SAT instance");
+  }
+  const int32_t id = ctx->next_inst++;
+  ctx->insts[id] = I;
+  *inst_out = id;
+  return NMC_OK;
+}
+
+int nmc_load_qap(nmc_ctx *ctx, int32_t n, const int32_t *F, const int32_t *D, int32_t *inst_out) {
+  if (!ctx) return NMC_EINVAL;
+  if (!inst_out || !F || !D) return fail(ctx, NMC_EINVAL, "NULL argument");
+  if (n < 1 || n > kMaxQapN) return fail(ctx, NMC_EINVAL, "QAP size must be in [1, 256]");
+  std::vector<uint8_t> f(static_cast<size_t>(n) * n), d(static_cast<size_t>(n) * n);
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t j = 0; j < n; ++j) {
+      const int32_t fij = F[i * n + j], dij = D[i * n + j];
+      if (fij < 0 || fij > 255 || dij < 0 || dij > 255)
+        return fail(ctx, NMC_EINVAL, "QAP entries must be in [0, 255]");
+      if (fij != F[j * n + i] || dij != D[j * n + i])
+        return fail(ctx, NMC_EINVAL, "F and D must be symmetric");
+      if (i == j && (fij != 0 || dij != 0))
+        return fail(ctx, NMC_EINVAL, "F and D must have a zero diagonal");
+      f[i * n + j] = static_cast<uint8_t>(fij);
+      d[i * n + j] = static_cast<uint8_t>(dij);
+    }
+  DeviceGuard g(ctx->device);
+  Instance I;
+  I.kind = NMC_KIND_QAP;
+  I.n_units = n;
+  I.qp.n = n;
+  cudaError_t e = cudaSuccess;
+  if ((e = dev_alloc(&I.qp.F, f.size())) != cudaSuccess ||
+      (e = dev_alloc(&I.qp.D, d.size())) != cudaSuccess ||
+      (e = cudaMemcpy(I.qp.F, f.data(), f.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(I.qp.D, d.data(), d.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    free_instance(I);
+    return cuda_fail(ctx, e, "upload QAP instance");
+  }
+  const int32_t id = ctx->next_inst++;
+  ctx->insts[id] = I;
+  *inst_out = id;
+  return NMC_OK;
+}
+
+int nmc_unload(nmc_ctx *ctx, int32_t inst) {
+  if (!ctx) return NMC_EINVAL;
+  Instance *I = find_inst(ctx, inst);
+  if (!I) return fail(ctx, NMC_EINVAL, "unknown instance");
+  if (I->users > 0) return fail(ctx, NMC_ESTATE, "instance still has replica sets");
+  DeviceGuard g(ctx->device);
+  NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  free_instance(*I);
+  ctx->insts.erase(inst);
+  return NMC_OK;
+}
+
+int nmc_ksat_colouring(nmc_ctx *ctx, int32_t inst, int32_t *colour_out, int32_t *n_colours) {
+  if (!ctx) return NMC_EINVAL;
+  Instance *I = find_inst(ctx, inst);
+  if (!I || I->kind != NMC_KIND_KSAT) return fail(ctx, NMC_EINVAL, "not a k-SAT instance");
+  if (colour_out) std::memcpy(colour_out, I->colour.data(), sizeof(int32_t) * I->colour.size());
+  if (n_colours) *n_colours = I->ks.n_colours;
+  return NMC_OK;
+}
+
+static int set_schedule_impl(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const float *beta,
+                             bool on_device) {
+  if (!ctx) return NMC_EINVAL;
+  Instance *I = find_inst(ctx, inst);
+  if (!I) return fail(ctx, NMC_EINVAL, "unknown instance");
+  if (n_steps < 1 || !beta) return fail(ctx, NMC_EINVAL, "need n_steps >= 1 and a beta array");
+  DeviceGuard g(ctx->device);
+  const size_t count = static_cast<size_t>(I->n_units) * static_cast<size_t>(n_steps);
+  float *src = nullptr;
+  if (on_device) {
+    src = const_cast<float *>(beta);
+  } else {
+    NMC_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&src), sizeof(float) * count, ctx->stream),
+             "allocate schedule staging");
+    NMC_CUDA(cudaMemcpyAsync(src, beta, sizeof(float) * count, cudaMemcpyHostToDevice, ctx->stream),
+             "copy schedule");
+  }
+  uint32_t *bq = nullptr;
+  cudaError_t e = cudaMalloc(&bq, sizeof(uint32_t) * count);
+  if (e != cudaSuccess) {
+    if (!on_device) cudaFreeAsync(src, ctx->stream);
+    return cuda_fail(ctx, e, "allocate schedule");
+  }
+  int32_t bad = 0;
+  e = cudaMemsetAsync(ctx->flag, 0, sizeof(int32_t), ctx->stream);
+  if (e == cudaSuccess)
+    e = quantize_schedule(src, I->n_units, n_steps, I->kind == NMC_KIND_KSAT ? I->ks.orig : nullptr,
+                          bq, ctx->flag, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&bad, ctx->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (!on_device) cudaFreeAsync(src, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    cudaFree(bq);
+    return cuda_fail(ctx, e, "quantise schedule");
+  }
+  if (bad) {
+    cudaFree(bq);
+    return fail(ctx, NMC_EINVAL, "beta must be finite and in [0, 65535]");
+  }
+  dev_free(I->bq);
+  I->bq = bq;
+  I->n_steps = n_steps;
+  return NMC_OK;
+}
+
+int nmc_set_schedule(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const float *beta) {
+  return set_schedule_impl(ctx, inst, n_steps, beta, false);
+}
+
+int nmc_set_schedule_device(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const float *beta_dev) {
+  return set_schedule_impl(ctx, inst, n_steps, beta_dev, true);
+}
+
+int nmc_replicas_create(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t seed,
+                        const void *init_states, int32_t *rs_out) {
+  if (!ctx) return NMC_EINVAL;
+  if (!rs_out) return fail(ctx, NMC_EINVAL, "rs_out is NULL");
+  Instance *I = find_inst(ctx, inst);
+  if (!I) return fail(ctx, NMC_EINVAL, "unknown instance");
+  if (replicas < 1 || replicas > kMaxReplicas)
+    return fail(ctx, NMC_EINVAL, "replicas must be in [1, 4096]");
+  {
+    const int rc = check_init(ctx, *I, replicas, init_states);
+    if (rc != NMC_OK) return rc;
+  }
+  DeviceGuard g(ctx->device);
+  ReplicaSet S;
+  S.inst = inst;
+  S.R = replicas;
+  S.seed = seed;
+  cudaError_t e = cudaSuccess;
+  if (I->kind == NMC_KIND_KSAT) {
+    const int32_t n = I->ks.n;
+    const int32_t W = (replicas + 31) / 32;
+    S.ks.R = replicas;
+    S.ks.W = W;
+    if ((e = dev_alloc(&S.ks.S, static_cast<size_t>(2 * n + 2) * W)) != cudaSuccess ||
+        (e = dev_alloc(&S.ks.best, static_cast<size_t>(n) * W)) != cudaSuccess ||
+        (e = dev_alloc(&S.ks.energy, 32 * W)) != cudaSuccess ||
+        (e = dev_alloc(&S.ks.best_energy, 32 * W)) != cudaSuccess ||
+        (e = dev_alloc(&S.ks.imp, W)) != cudaSuccess ||
+        (e = dev_alloc(&S.ks.bar, 1)) != cudaSuccess ||
+        (e = cudaMemsetAsync(S.ks.imp, 0, sizeof(uint32_t) * W, ctx->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(S.ks.bar, 0, sizeof(GridBarrier), ctx->stream)) != cudaSuccess) {
+      free_set(S);
+      return cuda_fail(ctx, e, "allocate replica set");
+    }
+    const int rc = init_replicas(ctx, *I, S, init_states);
+    if (rc != NMC_OK) {
+      free_set(S);
+      return rc;
+    }
+  } else {
+    const int32_t n = I->qp.n;
+    S.qp.R = replicas;
+    const size_t cnt = static_cast<size_t>(replicas) * n;
+    if ((e = dev_alloc(&S.qp.perm, cnt)) != cudaSuccess ||
+        (e = dev_alloc(&S.qp.best_perm, cnt)) != cudaSuccess ||
+        (e = dev_alloc(&S.qp.energy, replicas)) != cudaSuccess ||
+        (e = dev_alloc(&S.qp.best_energy, replicas)) != cudaSuccess) {
+      free_set(S);
+      return cuda_fail(ctx, e, "allocate replica set");
+    }
+    const int rc = init_replicas(ctx, *I, S, init_states);
+    if (rc != NMC_OK) {
+      free_set(S);
+      return rc;
+    }
+  }
+  const int32_t id = ctx->next_set++;
+  ctx->sets[id] = S;
+  I->users++;
+  *rs_out = id;
+  return NMC_OK;
+}
+
+int nmc_replicas_reset(nmc_ctx *ctx, int32_t rs, uint64_t seed, const void *init_states) {
+  if (!ctx) return NMC_EINVAL;
+  ReplicaSet *S = find_set(ctx, rs);
+  if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
+  Instance *I = find_inst(ctx, S->inst);
+  if (!I) return fail(ctx, NMC_ESTATE, "instance was unloaded");
+  const int rc = check_init(ctx, *I, S->R, init_states);
+  if (rc != NMC_OK) return rc;
+  DeviceGuard g(ctx->device);
+  S->seed = seed;
+  return init_replicas(ctx, *I, *S, init_states);
+}
+
+int nmc_replicas_destroy(nmc_ctx *ctx, int32_t rs) {
+  if (!ctx) return NMC_EINVAL;
+  ReplicaSet *S = find_set(ctx, rs);
+  if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
+  DeviceGuard g(ctx->device);
+  NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  Instance *I = find_inst(ctx, S->inst);
+  if (I) I->users--;
+  free_set(*S);
+  ctx->sets.erase(rs);
+  return NMC_OK;
+}
+
+int nmc_replicas_run(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1) {
+  if (!ctx) return NMC_EINVAL;
+  ReplicaSet *S = find_set(ctx, rs);
+  if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
+  Instance *I = find_inst(ctx, S->inst);
+  if (!I) return fail(ctx, NMC_ESTATE, "instance was unloaded");
+  if (t0 < 0 || t1 < t0) return fail(ctx, NMC_EINVAL, "need 0 <= t0 <= t1");
+  if (t1 > t0 && (!I->bq || t1 > I->n_steps))
+    return fail(ctx, NMC_ESTATE, "schedule missing or shorter than t1");
+  if (t1 == t0) return NMC_OK;
+  DeviceGuard g(ctx->device);
+  cudaError_t e;
+  if (I->kind == NMC_KIND_KSAT)
+    e = ksat_sweeps(I->ks, S->ks, I->bq, ctx->tab, ctx->tab_len, t0, t1, S->seed, ctx->device,
+                    ctx->stream);
+  else
+    e = qap_steps(I->qp, S->qp, I->bq, ctx->tab, ctx->tab_len, t0, t1, S->seed, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "launch sweep");
+  return NMC_OK;
+}
+
+static int read_impl(nmc_ctx *ctx, int32_t rs, const nmc_result *out, bool to_host) {
+  if (!ctx) return NMC_EINVAL;
+  if (!out) return fail(ctx, NMC_EINVAL, "out is NULL");
+  ReplicaSet *S = find_set(ctx, rs);
+  if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
+  Instance *I = find_inst(ctx, S->inst);
+  if (!I) return fail(ctx, NMC_ESTATE, "instance was unloaded");
+  DeviceGuard g(ctx->device);
+  const size_t R = static_cast<size_t>(S->R), n = static_cast<size_t>(I->n_units);
+  const size_t elem = I->kind == NMC_KIND_KSAT ? 1 : 2;
+  const size_t state_bytes = R * n * elem;
+  void *st = out->states, *bst = out->best_states;
+  int64_t *en = out->energies, *ben = out->best_energies;
+  char *stage = nullptr;
+  if (to_host) {
+    // staging sections start on 256-byte boundaries (the int64 energies need 8-byte alignment)
+    const size_t sec_s = (state_bytes + 255) & ~static_cast<size_t>(255);
+    const size_t sec_e = (R * sizeof(int64_t) + 255) & ~static_cast<size_t>(255);
+    const size_t total = 2 * sec_s + 2 * sec_e;
+    NMC_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&stage), total, ctx->stream), "allocate readback");
+    st = out->states ? stage : nullptr;
+    bst = out->best_states ? stage + sec_s : nullptr;
+    en = out->energies ? reinterpret_cast<int64_t *>(stage + 2 * sec_s) : nullptr;
+    ben = out->best_energies ? reinterpret_cast<int64_t *>(stage + 2 * sec_s + sec_e) : nullptr;
+  }
+  cudaError_t e;
+  if (I->kind == NMC_KIND_KSAT)
+    e = ksat_unpack(I->ks, S->ks, static_cast<uint8_t *>(st), static_cast<uint8_t *>(bst), en, ben,
+                    ctx->stream);
+  else
+    e = qap_unpack(I->qp, S->qp, static_cast<int16_t *>(st), static_cast<int16_t *>(bst), en, ben,
+                   ctx->stream);
+  if (e == cudaSuccess && to_host) {
+    if (out->states && e == cudaSuccess)
+      e = cudaMemcpyAsync(out->states, st, state_bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (out->best_states && e == cudaSuccess)
+      e = cudaMemcpyAsync(out->best_states, bst, state_bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (out->energies && e == cudaSuccess)
+      e = cudaMemcpyAsync(out->energies, en, R * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream);
+    if (out->best_energies && e == cudaSuccess)
+      e = cudaMemcpyAsync(out->best_energies, ben, R * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream);
+  }
+  if (stage) cudaFreeAsync(stage, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "read replicas");
+  if (to_host) {
+    NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    return check_timeout(ctx, *S);
+  }
+  return NMC_OK;
+}
+
+int nmc_replicas_read(nmc_ctx *ctx, int32_t rs, const nmc_result *out) {
+  return read_impl(ctx, rs, out, true);
+}
+
+int nmc_replicas_read_device(nmc_ctx *ctx, int32_t rs, const nmc_result *out_dev) {
+  return read_impl(ctx, rs, out_dev, false);
+}
+
+int nmc_anneal(nmc_ctx *ctx, int32_t inst, int32_t replicas, int32_t t0, int32_t t1,
+               uint64_t seed, const void *init_states, const nmc_result *out) {
+  if (!ctx) return NMC_EINVAL;
+  int32_t rs = 0;
+  int rc = nmc_replicas_create(ctx, inst, replicas, seed, init_states, &rs);
+  if (rc != NMC_OK) return rc;
+  rc = nmc_replicas_run(ctx, rs, t0, t1);
+  if (rc == NMC_OK && out) rc = nmc_replicas_read(ctx, rs, out);
+  const std::string keep = ctx->err;
+  const int rc2 = nmc_replicas_destroy(ctx, rs);
+  if (rc != NMC_OK) {
+    ctx->err = keep;
+    return rc;
+  }
+  return rc2;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Internal declarations shared by the translation units of libnmc (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nmc {
+
+// Philox counter tags (word 3 of the counter) that separate the streams of the chain.
+constexpr uint32_t kTagKsatInit = 0x4B494E49u;
+constexpr uint32_t kTagKsatSweep = 0x4B535750u;
+constexpr uint32_t kTagQapInit = 0x51494E49u;
+constexpr uint32_t kTagQapStep = 0x51535450u;
+
+constexpr int kTabCap = 8192;    // capacity of the acceptance-threshold table
+constexpr int kMaxReplicas = 4096;
+constexpr int kMaxDegree = 1023; // occurrences of one variable (10-bit sliced counters)
+constexpr int kMaxQapN = 256;
+
+// Barrier shared by all CTAs of a cooperative launch. Reset before every launch.
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+  int error;   // 1 = a wait expired (the launch stopped early); reset with the barrier
+  int sticky;  // also set on expiry, kept across launches until the host reads it
+};
+// Bytes of GridBarrier cleared before every launch (count, gen, error; not sticky).
+constexpr size_t kBarrierResetBytes = 3 * sizeof(unsigned int);
+
+// Device-resident k-SAT instance after the host build (variables renumbered so that every
+// colour class is a contiguous id range; "new" ids below).
+struct KsatDevice {
+  int32_t n, m, kmax, n_colours, kq;  // kq = int4 words per occurrence (1: k<=4, 2: k<=8)
+  int32_t nb;                         // bits of the sliced counters (covers the max degree)
+  int32_t n_occ;                      // occurrences incl. padding (multiple of 4 per variable)
+  int4 *occ;                          // n_occ * kq: {own sign mask, other literal ids...}
+  int32_t *occ_ptr;                   // n+1
+  int32_t *col_ptr;                   // n_colours+1 (device copy)
+  int32_t *orig;                      // n: new id -> original id
+  int32_t *newid;                     // n: original id -> new id
+  int32_t *clits;                     // m * kmax literal ids (2*new+neg), pad = 2n (false)
+};
+
+// Replica state of one k-SAT replica set: W = ceil(R/32) words per literal row.
+struct KsatReplicas {
+  int32_t R, W;
+  uint32_t *S;        // (2n+2) * W: row 2v = x_v bits, row 2v+1 = not x_v, rows 2n/2n+1 dummy
+  uint32_t *best;     // n * W
+  int32_t *energy;    // 32W
+  int32_t *best_energy;
+  uint32_t *imp;      // W: replicas whose best improved at the last sweep end (pending copy)
+  GridBarrier *bar;
+};
+
+struct QapDevice {
+  int32_t n;
+  uint8_t *F, *D;  // n*n, entries 0..255
+};
+
+struct QapReplicas {
+  int32_t R;
+  int16_t *perm;       // R * n
+  int16_t *best_perm;  // R * n
+  int64_t *energy, *best_energy;
+};
+
+// ---- k-SAT launchers (ksat.cu); all asynchronous on `st` -------------------------------
+cudaError_t ksat_init_states(const KsatDevice &I, KsatReplicas &Rp, uint64_t seed,
+                             const uint8_t *init_dev, cudaStream_t st);
+cudaError_t ksat_energies(const KsatDevice &I, KsatReplicas &Rp, cudaStream_t st);
+cudaError_t ksat_sweeps(const KsatDevice &I, KsatReplicas &Rp, const uint32_t *bq,
+                        const uint32_t *tab, int32_t tab_len, int32_t t0, int32_t t1,
+                        uint64_t seed, int device, cudaStream_t st);
+cudaError_t ksat_unpack(const KsatDevice &I, const KsatReplicas &Rp, uint8_t *states,
+                        uint8_t *best_states, int64_t *energies, int64_t *best_energies,
+                        cudaStream_t st);
+cudaError_t wait_selftest(GridBarrier *gb, unsigned long long limit_ns, cudaStream_t st);
+cudaError_t quantize_schedule(const float *beta, int32_t n_units, int32_t n_steps,
+                              const int32_t *orig, uint32_t *bq, int32_t *bad,
+                              cudaStream_t st);
+
+// ---- QAP launchers (qap.cu) ------------------------------------------------------------
+cudaError_t qap_init_states(const QapDevice &I, QapReplicas &Rp, uint64_t seed,
+                            const int16_t *init_dev, cudaStream_t st);
+cudaError_t qap_steps(const QapDevice &I, QapReplicas &Rp, const uint32_t *bq,
+                      const uint32_t *tab, int32_t tab_len, int32_t t0, int32_t t1,
+                      uint64_t seed, cudaStream_t st);
+cudaError_t qap_unpack(const QapDevice &I, const QapReplicas &Rp, int16_t *perms,
+                       int16_t *best_perms, int64_t *energies, int64_t *best_energies,
+                       cudaStream_t st);
+
+}  // namespace nmc

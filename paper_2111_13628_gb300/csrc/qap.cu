@@ -1,0 +1,300 @@
+// QAP kernels: Metropolis over permutations with pairwise swap moves (Koopmans-Beckmann cost,
+// Sec. "Quadratic Assignment Problems"; per-facility inverse temperature as in the sampling
+// stage of Algorithm 1).
+//
+// One warp runs one replica; lane l owns the locations p[k] of facilities k = l + 32 i in
+// registers. F and D (entries 0..255, stored as bytes) of the CTA's instance sit in shared
+// memory, shared by the 32 replicas (warps) of the CTA. The swap change
+//   dC(r,s) = 2 sum_{k != r,s} (F_rk - F_sk)(D_{p(s)p(k)} - D_{p(r)p(k)})
+// is an O(n) dot product split over the lanes and summed with shuffles. The Philox blocks of
+// 32 consecutive attempts are drawn in parallel, one per lane, and broadcast in turn.
+#include "nmc_internal.h"
+#include "philox.cuh"
+
+namespace nmc {
+
+namespace {
+
+constexpr int kQapWarps = 32;
+
+template <int NPL>
+__device__ __forceinline__ int pick(const int (&p)[NPL], int i) {
+  int v = p[0];
+#pragma unroll
+  for (int q = 1; q < NPL; ++q)
+    if (q == i) v = p[q];
+  return v;
+}
+
+template <int NPL>
+__device__ __forceinline__ void put(int (&p)[NPL], int i, int v) {
+#pragma unroll
+  for (int q = 0; q < NPL; ++q)
+    if (q == i) p[q] = v;
+}
+
+// Cost of the permutation held in registers: sum_i sum_j F_ij D_{p(i)p(j)}.
+template <int NPL>
+__device__ long long warp_cost(const uint8_t *Fs, const uint8_t *Ds, const uint8_t *ps, int n,
+                               int lane) {
+  long long acc = 0;
+  for (int i = lane; i < n; i += 32) {
+    const int pi = ps[i];
+    for (int j = 0; j < n; ++j) acc += (long long)Fs[i * n + j] * (long long)Ds[pi * n + ps[j]];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  return acc;
+}
+
+struct QapArgs {
+  const uint8_t *F, *D;
+  int16_t *perm, *best_perm;
+  long long *energy, *best_energy;
+  const uint32_t *bq;
+  const uint32_t *tab;
+  int32_t tab_len, n, R, t0, t1;
+  uint32_t k0, k1;
+  int init_mode;  // 0: run steps; 1: draw initial states (Fisher-Yates); 2: states given
+};
+
+template <int NPL>
+__global__ void __launch_bounds__(kQapWarps * 32) qap_kernel(QapArgs a) {
+  extern __shared__ uint32_t smem[];
+  const int n = a.n;
+  uint32_t *tab_s = smem;
+  uint8_t *Fs = (uint8_t *)(smem + ((a.tab_len + 31) & ~31));
+  uint8_t *Ds = Fs + ((n * n + 15) & ~15);
+  uint8_t *pw_all = Ds + ((n * n + 15) & ~15);  // one n-byte row per warp (permutation copy)
+  for (int i = threadIdx.x; i < a.tab_len; i += blockDim.x) tab_s[i] = a.tab[i];
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    Fs[i] = a.F[i];
+    Ds[i] = a.D[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.x * kQapWarps + warp;
+  if (r >= a.R) return;
+  uint8_t *pw = pw_all + warp * ((n + 15) & ~15);
+  int16_t *gp = a.perm + (size_t)r * n;
+
+  if (a.init_mode == 1) {
+    // Fisher-Yates from the identity: position q = n-1..1 exchanged with (u (q+1)) >> 32.
+    for (int k = lane; k < n; k += 32) pw[k] = (uint8_t)k;
+    __syncwarp();
+    for (int q0 = n - 1; q0 >= 1; q0 -= 32) {
+      const int q = q0 - lane;
+      uint32_t u = 0u;
+      if (q >= 1)
+        u = philox4x32_10(make_uint4((uint32_t)q, 0u, (uint32_t)r, kTagQapInit), a.k0, a.k1).x;
+      const int cnt = q0 >= 32 ? 32 : q0;
+      for (int j = 0; j < cnt; ++j) {
+        const uint32_t uj = __shfl_sync(0xFFFFFFFFu, u, j);
+        const int qq = q0 - j;
+        const int kk = (int)(((unsigned long long)uj * (unsigned)(qq + 1)) >> 32);
+        if (lane == 0) {
+          const uint8_t tmp = pw[qq];
+          pw[qq] = pw[kk];
+          pw[kk] = tmp;
+        }
+        __syncwarp();
+      }
+    }
+  } else {
+    for (int k = lane; k < n; k += 32) pw[k] = (uint8_t)gp[k];
+    __syncwarp();
+  }
+  if (a.init_mode != 0) {
+    const long long c = warp_cost<NPL>(Fs, Ds, pw, n, lane);
+    for (int k = lane; k < n; k += 32) {
+      gp[k] = (int16_t)pw[k];
+      a.best_perm[(size_t)r * n + k] = (int16_t)pw[k];
+    }
+    if (lane == 0) {
+      a.energy[r] = c;
+      a.best_energy[r] = c;
+    }
+    return;
+  }
+
+  int p[NPL];
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) {
+    const int k = lane + 32 * i;
+    p[i] = k < n ? pw[k] : 0;
+  }
+  long long e = a.energy[r];
+  long long be = a.best_energy[r];
+  const int nm1 = n - 1;
+  for (int t = a.t0; t < a.t1; ++t) {
+    if (n >= 2) {
+      const uint32_t *bqt = a.bq + (size_t)t * n;
+      for (int a0 = 0; a0 < n; a0 += 32) {
+        // lane j draws attempt a0+j
+        const int at = a0 + lane;
+        int fr = 0, fs = 0;
+        uint32_t u2 = 0u, bqs = 0u;
+        if (at < n) {
+          const uint4 u =
+              philox4x32_10(make_uint4((uint32_t)at, (uint32_t)t, (uint32_t)r, kTagQapStep), a.k0, a.k1);
+          fr = (int)(((unsigned long long)u.x * (unsigned)n) >> 32);
+          fs = (int)(((unsigned long long)u.y * (unsigned)nm1) >> 32);
+          fs += fs >= fr;
+          u2 = u.z;
+          bqs = (uint32_t)(((unsigned long long)__ldg(bqt + fr) + __ldg(bqt + fs)) >> 1);
+        }
+        const int cnt = (n - a0) < 32 ? (n - a0) : 32;
+        for (int j = 0; j < cnt; ++j) {
+          const int rr = __shfl_sync(0xFFFFFFFFu, fr, j);
+          const int ss = __shfl_sync(0xFFFFFFFFu, fs, j);
+          const int pr = __shfl_sync(0xFFFFFFFFu, pick<NPL>(p, rr >> 5), rr & 31);
+          const int ps = __shfl_sync(0xFFFFFFFFu, pick<NPL>(p, ss >> 5), ss & 31);
+          const uint8_t *Fr = Fs + rr * n, *Fsr = Fs + ss * n;
+          const uint8_t *Dr = Ds + pr * n, *Dsr = Ds + ps * n;
+          int acc = 0;
+#pragma unroll
+          for (int i = 0; i < NPL; ++i) {
+            const int k = lane + 32 * i;
+            if (k < n && k != rr && k != ss) {
+              const int pk = p[i];
+              acc += ((int)Fr[k] - (int)Fsr[k]) * ((int)Dsr[pk] - (int)Dr[pk]);
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+          const long long d = 2LL * acc;
+          bool ok = d <= 0;
+          if (!ok) {
+            const uint32_t bj = __shfl_sync(0xFFFFFFFFu, bqs, j);
+            const uint32_t uj = __shfl_sync(0xFFFFFFFFu, u2, j);
+            const unsigned long long idx = ((unsigned long long)bj * (unsigned long long)d) >> 8;
+            ok = idx < (unsigned long long)a.tab_len && uj < tab_s[idx];
+          }
+          if (ok) {
+            if (lane == (rr & 31)) put<NPL>(p, rr >> 5, ps);
+            if (lane == (ss & 31)) put<NPL>(p, ss >> 5, pr);
+            e += d;
+          }
+        }
+      }
+    }
+    if (e < be) {
+      be = e;
+#pragma unroll
+      for (int i = 0; i < NPL; ++i) {
+        const int k = lane + 32 * i;
+        if (k < n) a.best_perm[(size_t)r * n + k] = (int16_t)p[i];
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) {
+    const int k = lane + 32 * i;
+    if (k < n) gp[k] = (int16_t)p[i];
+  }
+  if (lane == 0) {
+    a.energy[r] = e;
+    a.best_energy[r] = be;
+  }
+}
+
+template <int NPL>
+cudaError_t launch_qap(const QapArgs &a, cudaStream_t st) {
+  const int n = a.n;
+  const size_t smem = sizeof(uint32_t) * ((a.tab_len + 31) & ~31) + 2 * (size_t)((n * n + 15) & ~15) +
+                      (size_t)kQapWarps * ((n + 15) & ~15);
+  auto kern = qap_kernel<NPL>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int blocks = (a.R + kQapWarps - 1) / kQapWarps;
+  kern<<<blocks, kQapWarps * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch_qap(const QapArgs &a, cudaStream_t st) {
+  if (a.n <= 32) return launch_qap<1>(a, st);
+  if (a.n <= 64) return launch_qap<2>(a, st);
+  if (a.n <= 128) return launch_qap<4>(a, st);
+  return launch_qap<8>(a, st);
+}
+
+__global__ void qap_unpack_kernel(const int16_t *perm, const int16_t *best_perm,
+                                  const long long *energy, const long long *best_energy,
+                                  int32_t n, int32_t R, int16_t *p_out, int16_t *bp_out,
+                                  int64_t *e_out, int64_t *be_out) {
+  const long long total = (long long)R * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (p_out) p_out[i] = perm[i];
+    if (bp_out) bp_out[i] = best_perm[i];
+    if (i < R) {
+      if (e_out) e_out[i] = energy[i];
+      if (be_out) be_out[i] = best_energy[i];
+    }
+  }
+}
+
+QapArgs make_args(const QapDevice &I, QapReplicas &Rp, uint64_t seed) {
+  QapArgs a;
+  a.F = (const uint8_t *)I.F;
+  a.D = (const uint8_t *)I.D;
+  a.perm = Rp.perm;
+  a.best_perm = Rp.best_perm;
+  a.energy = (long long *)Rp.energy;
+  a.best_energy = (long long *)Rp.best_energy;
+  a.bq = nullptr;
+  a.tab = nullptr;
+  a.tab_len = 0;
+  a.n = I.n;
+  a.R = Rp.R;
+  a.t0 = a.t1 = 0;
+  a.k0 = (uint32_t)seed;
+  a.k1 = (uint32_t)(seed >> 32);
+  a.init_mode = 0;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t qap_init_states(const QapDevice &I, QapReplicas &Rp, uint64_t seed,
+                            const int16_t *init_dev, cudaStream_t st) {
+  QapArgs a = make_args(I, Rp, seed);
+  if (init_dev) {
+    cudaError_t err = cudaMemcpyAsync(Rp.perm, init_dev, sizeof(int16_t) * (size_t)Rp.R * I.n,
+                                      cudaMemcpyDeviceToDevice, st);
+    if (err != cudaSuccess) return err;
+    a.init_mode = 2;
+  } else {
+    a.init_mode = 1;
+  }
+  return dispatch_qap(a, st);
+}
+
+cudaError_t qap_steps(const QapDevice &I, QapReplicas &Rp, const uint32_t *bq,
+                      const uint32_t *tab, int32_t tab_len, int32_t t0, int32_t t1,
+                      uint64_t seed, cudaStream_t st) {
+  if (t1 <= t0) return cudaSuccess;
+  QapArgs a = make_args(I, Rp, seed);
+  a.bq = bq;
+  a.tab = tab;
+  a.tab_len = tab_len;
+  a.t0 = t0;
+  a.t1 = t1;
+  return dispatch_qap(a, st);
+}
+
+cudaError_t qap_unpack(const QapDevice &I, const QapReplicas &Rp, int16_t *perms,
+                       int16_t *best_perms, int64_t *energies, int64_t *best_energies,
+                       cudaStream_t st) {
+  const long long total = (long long)Rp.R * I.n;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  if (blocks < 1) blocks = 1;
+  qap_unpack_kernel<<<(int)blocks, 256, 0, st>>>(Rp.perm, Rp.best_perm,
+                                                 (const long long *)Rp.energy,
+                                                 (const long long *)Rp.best_energy, I.n, Rp.R,
+                                                 perms, best_perms, energies, best_energies);
+  return cudaGetLastError();
+}
+
+}  // namespace nmc

@@ -1,0 +1,59 @@
+"""The C-ABI library builds, loads and exports every function include/nmc.h declares (CPU).
+
+No compute call runs here; the threshold table is host code of the library and is compared
+with the oracle's own table (both built from floor(2^32 exp(-j/256)) independently).
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "nmc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nmc_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2111_13628_gb300 import _build
+    return ctypes.CDLL(_build.build())
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import paper_2111_13628_gb300 as nmc
+    declared = _declared()
+    assert declared, "no declarations parsed"
+    assert sorted(nmc.SYMBOLS) == declared
+    out = subprocess.run(["nm", "-D", "--defined-only", nmc.library_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (nmc_[a-z_]+)", out))
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    for s in declared:
+        assert hasattr(lib, s)
+
+
+def test_threshold_table_matches_oracle():
+    import paper_2111_13628_gb300 as nmc
+    t_lib, L_lib = nmc.threshold_table()
+    t_or, L_or = O.threshold_table()
+    assert L_lib == L_or
+    assert np.array_equal(t_lib, t_or)
+
+
+def test_create_without_device_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    import paper_2111_13628_gb300 as nmc
+    with pytest.raises(nmc.NmcError):
+        nmc.Context(0)
