@@ -19,6 +19,7 @@
 // waits are bounded (a few seconds); when one expires the kernel records an error and every
 // CTA returns.
 #include <cooperative_groups.h>
+#include <cstdlib>
 
 #include "nmc_internal.h"
 #include "philox.cuh"
@@ -290,6 +291,281 @@ __global__ void __launch_bounds__(kSweepThreads) ksat_sweep_kernel(SweepArgs a) 
   }
 }
 
+// ---- fast path: W a multiple of 32, counters of at most 7 bits ---------------------------
+//
+// A team of P consecutive warps takes one variable and one group of 32 words (lane = word):
+// the warps split the variable's occurrence list, stage their entries in shared memory with
+// one cooperative load, gather the neighbour literal words in batches of CH occurrences, and
+// exchange their partial bit-sliced counters through shared memory. Each warp then resolves
+// the acceptance of 32/P of the 32 replica bits of its lane's word. With P > 1 the latency
+// of one attempt is split P ways, which matters because one colour class is one wave.
+constexpr int kFastEntCap = 64;   // occurrences staged per warp per batch
+constexpr int kFastMaxTeams = 15; // named barriers 1..15
+
+__device__ __forceinline__ void team_bar(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+struct FastSmem {
+  uint32_t *tab;   // acceptance table
+  int *eacc;       // W*33 per-CTA energy sums
+  int4 *ent;       // per warp: kFastEntCap * KQ entries
+  uint32_t *thr;   // per warp: 128 thresholds by energy change 0..127
+  uint32_t *part;  // per team: P * 2*NB * 32 partial counters
+  uint32_t *flip;  // per team: P * 32 flip masks
+  int *acc;        // per warp: (32/P) x 32 lanes, energy change of this sweep per replica bit
+};
+
+template <int NB, int KQ, int P>
+__host__ __device__ constexpr size_t fast_smem_bytes(int tab_len, int W, int nwarps) {
+  return sizeof(uint32_t) * ((tab_len + 31) & ~31) + sizeof(int) * (size_t)W * 33 +
+         sizeof(int4) * (size_t)nwarps * kFastEntCap * KQ + sizeof(uint32_t) * (size_t)nwarps * 128 +
+         sizeof(uint32_t) * (size_t)(nwarps / P) * P * 2 * NB * 32 +
+         sizeof(uint32_t) * (size_t)(nwarps / P) * P * 32 + sizeof(int) * (size_t)nwarps * 32 * (32 / P) +
+         64;
+}
+
+template <int NB, int KQ, int P>
+__device__ __forceinline__ void fast_attempt(const SweepArgs &a, const FastSmem &sm, int v, int w,
+                                             int t, int warp, int team_in_cta, int p, int lane) {
+  const int W = a.W;
+  const uint32_t *Sw = a.S + w;
+  const int e0 = __ldg(a.occ_ptr + v), e1 = __ldg(a.occ_ptr + v + 1);
+  const uint32_t x = __ldcg(Sw + (size_t)(2 * v) * W);
+  const uint32_t bqv = __ldg(a.bq + (size_t)t * a.n + v);
+  // this warp's share of the occurrences, a multiple of 4
+  const int quads = (e1 - e0) >> 2;
+  const int per = (quads + P - 1) / P;
+  const int lo = e0 + 4 * min(quads, p * per);
+  const int hi = e0 + 4 * min(quads, (p + 1) * per);
+  uint32_t bc[NB], mc[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    bc[j] = 0u;
+    mc[j] = 0u;
+  }
+  int4 *ent = sm.ent + (size_t)warp * kFastEntCap * KQ;
+  for (int base = lo; base < hi; base += kFastEntCap) {
+    const int cnt = min(kFastEntCap, hi - base);
+    for (int i = lane; i < cnt * KQ; i += 32) ent[i] = __ldg(a.occ + (size_t)base * KQ + i);
+    __syncwarp();
+    for (int e = 0; e < cnt; e += 4) {
+      uint32_t bb[4], mm[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int4 q = ent[(e + j) * KQ];
+        uint32_t o = __ldcg(Sw + (size_t)q.y * W) | __ldcg(Sw + (size_t)q.z * W) |
+                     __ldcg(Sw + (size_t)q.w * W);
+        if (KQ == 2) {
+          const int4 q2 = ent[(e + j) * KQ + 1];
+          o |= __ldcg(Sw + (size_t)q2.x * W) | __ldcg(Sw + (size_t)q2.y * W) |
+               __ldcg(Sw + (size_t)q2.z * W) | __ldcg(Sw + (size_t)q2.w * W);
+        }
+        const uint32_t own = x ^ (uint32_t)q.x;
+        bb[j] = own & ~o;
+        mm[j] = ~(own | o);
+      }
+      csa_add4<NB>(bc, bb[0], bb[1], bb[2], bb[3]);
+      csa_add4<NB>(mc, mm[0], mm[1], mm[2], mm[3]);
+    }
+    __syncwarp();
+  }
+  const int bar_id = 1 + team_in_cta;
+  if (P > 1) {
+    uint32_t *part = sm.part + (size_t)team_in_cta * P * 2 * NB * 32;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      part[((p * 2 + 0) * NB + j) * 32 + lane] = bc[j];
+      part[((p * 2 + 1) * NB + j) * 32 + lane] = mc[j];
+    }
+    team_bar(bar_id, P * 32);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      bc[j] = 0u;
+      mc[j] = 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q) {  // sum the P partial counters (ripple-carry, bit-sliced)
+      uint32_t cb = 0u, cm = 0u;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const uint32_t pb = part[((q * 2 + 0) * NB + j) * 32 + lane];
+        const uint32_t pm = part[((q * 2 + 1) * NB + j) * 32 + lane];
+        const uint32_t sb = bc[j] ^ pb ^ cb;
+        cb = maj3(bc[j], pb, cb);
+        bc[j] = sb;
+        const uint32_t sm2 = mc[j] ^ pm ^ cm;
+        cm = maj3(mc[j], pm, cm);
+        mc[j] = sm2;
+      }
+    }
+  }
+  // D = B - U in NB+1 bit two's complement, bit-sliced
+  uint32_t d[NB + 1];
+  {
+    uint32_t br = 0u;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      d[j] = bc[j] ^ mc[j] ^ br;
+      br = maj3(~bc[j], mc[j], br);
+    }
+    d[NB] = br;
+  }
+  // thresholds by energy change for this variable's beta (shared by the warp's lanes)
+  uint32_t *thr = sm.thr + warp * 128;
+  for (int dv = lane; dv < (1 << NB); dv += 32) {
+    const unsigned long long idx = ((unsigned long long)bqv * (unsigned)dv) >> 8;
+    thr[dv] = (dv > 0 && idx < (unsigned long long)a.tab_len) ? sm.tab[idx] : 0u;
+  }
+  __syncwarp();
+  const uint32_t vo = (uint32_t)__ldg(a.orig + v);
+  uint32_t flip = 0u;
+  constexpr int GPW = 8 / P;  // Philox groups (4 replicas each) per warp
+#pragma unroll 1
+  for (int gi = 0; gi < GPW; ++gi) {
+    const int g = p * GPW + gi;
+    int de[4];
+    uint32_t th[4];
+    bool need = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = 4 * g + j;
+      int val = 0;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) val |= (int)((d[q] >> b) & 1u) << q;
+      val -= (int)((d[NB] >> b) & 1u) << NB;
+      de[j] = val;
+      th[j] = val > 0 ? thr[val] : 0u;
+      need |= th[j] != 0u;
+    }
+    uint4 u = make_uint4(0u, 0u, 0u, 0u);
+    if (need) u = philox4x32_10(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * w + g), kTagKsatSweep),
+                                a.k0, a.k1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool ok = de[j] <= 0 || uint4_word(u, j) < th[j];
+      if (ok) {
+        flip |= 1u << (4 * g + j);
+        if (de[j] != 0) sm.acc[(warp * (32 / P) + 4 * gi + j) * 32 + lane] += de[j];
+      }
+    }
+  }
+  if (P > 1) {
+    uint32_t *fl = sm.flip + (size_t)team_in_cta * P * 32;
+    fl[p * 32 + lane] = flip;
+    team_bar(bar_id, P * 32);
+    if (p != 0) return;
+    flip = 0u;
+#pragma unroll
+    for (int q = 0; q < P; ++q) flip |= fl[q * 32 + lane];
+  }
+  const uint32_t xn = x ^ flip;
+  __stcg(a.S + (size_t)(2 * v) * W + w, xn);
+  __stcg(a.S + (size_t)(2 * v + 1) * W + w, ~xn);
+  const uint32_t m = __ldcg(a.imp + w);
+  if (m) {
+    const size_t bi = (size_t)v * W + w;
+    __stcg(a.best + bi, (__ldcg(a.best + bi) & ~m) | (x & m));
+  }
+}
+
+template <int NB, int KQ, int P, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) ksat_sweep_fast_kernel(SweepArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int W = a.W;
+  const int nwarps = blockDim.x >> 5;
+  FastSmem sm;
+  {
+    char *p = (char *)smem;
+    sm.tab = (uint32_t *)p;
+    p += sizeof(uint32_t) * ((a.tab_len + 31) & ~31);
+    sm.eacc = (int *)p;
+    p += sizeof(int) * (size_t)W * 33;
+    p = (char *)(((size_t)p + 15) & ~(size_t)15);
+    sm.ent = (int4 *)p;
+    p += sizeof(int4) * (size_t)nwarps * kFastEntCap * KQ;
+    sm.thr = (uint32_t *)p;
+    p += sizeof(uint32_t) * (size_t)nwarps * 128;
+    sm.part = (uint32_t *)p;
+    p += sizeof(uint32_t) * (size_t)(nwarps / P) * P * 2 * NB * 32;
+    sm.flip = (uint32_t *)p;
+    p += sizeof(uint32_t) * (size_t)(nwarps / P) * P * 32;
+    sm.acc = (int *)p;
+  }
+  for (int i = threadIdx.x; i < a.tab_len; i += blockDim.x) sm.tab[i] = a.tab[i];
+  for (int i = threadIdx.x; i < W * 33; i += blockDim.x) sm.eacc[i] = 0;
+  for (int i = threadIdx.x; i < nwarps * 32 * (32 / P); i += blockDim.x) sm.acc[i] = 0;
+  __syncthreads();
+
+  const unsigned nblocks = gridDim.x;
+  unsigned gen = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int team_in_cta = warp / P, p = warp % P;
+  const int teams_per_cta = nwarps / P;
+  const int team = blockIdx.x * teams_per_cta + team_in_cta;
+  const int nteams = gridDim.x * teams_per_cta;
+  const int G = W >> 5;
+  const int g = team % G, vslot = team / G, vslots = nteams / G;
+  const bool active = team_in_cta < teams_per_cta && vslot < vslots;
+  const int w = g * 32 + lane;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nthreads = gridDim.x * blockDim.x;
+
+  for (int t = a.t0; t < a.t1; ++t) {
+    for (int c = 0; c < a.n_colours; ++c) {
+      if (active) {
+        const int v0 = __ldg(a.col_ptr + c), v1 = __ldg(a.col_ptr + c + 1);
+        for (int v = v0 + vslot; v < v1; v += vslots)
+          fast_attempt<NB, KQ, P>(a, sm, v, w, t, warp, team_in_cta, p, lane);
+      }
+      if (!grid_sync(a.bar, nblocks, gen, kSweepWaitLimitNs)) return;
+    }
+    if (active) {
+#pragma unroll
+      for (int b = 0; b < 32 / P; ++b) {
+        int *slot = &sm.acc[(warp * (32 / P) + b) * 32 + lane];
+        const int val = *slot;
+        if (val != 0) {
+          atomicAdd(&sm.eacc[w * 33 + p * (32 / P) + b], val);
+          *slot = 0;
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < W * 32; i += blockDim.x) {
+      const int s = (i >> 5) * 33 + (i & 31);
+      const int val = sm.eacc[s];
+      if (val != 0) {
+        atomicAdd(&a.energy[i], val);
+        sm.eacc[s] = 0;
+      }
+    }
+    if (!grid_sync(a.bar, nblocks, gen, kSweepWaitLimitNs)) return;
+    if (gtid < W * 32) {
+      const int e = __ldcg(a.energy + gtid);
+      const int be = __ldcg(a.best_energy + gtid);
+      const bool better = e < be;
+      if (better) __stcg(a.best_energy + gtid, e);
+      const unsigned mask = __ballot_sync(0xFFFFFFFFu, better);
+      if ((threadIdx.x & 31) == 0) __stcg(a.imp + (gtid >> 5), mask);
+    }
+    if (!grid_sync(a.bar, nblocks, gen, kSweepWaitLimitNs)) return;
+  }
+  if (a.t1 > a.t0) {
+    for (long long i = gtid; i < (long long)a.n * W; i += nthreads) {
+      const int ww = (int)(i % W);
+      const uint32_t m = __ldcg(a.imp + ww);
+      if (m) {
+        const long long v = i / W;
+        const uint32_t x = __ldcg(a.S + (size_t)(2 * v) * W + ww);
+        __stcg(a.best + i, (__ldcg(a.best + i) & ~m) | (x & m));
+      }
+    }
+    if (!grid_sync(a.bar, nblocks, gen, kSweepWaitLimitNs)) return;
+    for (int i = gtid; i < W; i += nthreads) __stcg(a.imp + i, 0u);
+  }
+}
+
 // One CTA waits for `expected` arrivals at the barrier; with expected > 1 nothing releases it
 // and the bounded wait must expire.
 __global__ void wait_selftest_kernel(GridBarrier *gb, unsigned expected,
@@ -425,6 +701,39 @@ cudaError_t launch_sweeps(const SweepArgs &a, int device, cudaStream_t st) {
                                      smem, st);
 }
 
+
+template <int NB, int KQ, int P, int THREADS>
+cudaError_t launch_fast(const SweepArgs &a, int device, cudaStream_t st) {
+  const int threads = THREADS;
+  const int nwarps = threads / 32;
+  const size_t smem = fast_smem_bytes<NB, KQ, P>(a.tab_len, a.W, nwarps);
+  auto kern = ksat_sweep_fast_kernel<NB, KQ, P, THREADS>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (err != cudaSuccess) return err;
+  int sms = 0;
+  err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  void *args[] = {(void *)&a};
+  return cudaLaunchCooperativeKernel((const void *)kern, dim3(sms * per_sm), dim3(threads), args,
+                                     smem, st);
+}
+
+// Fast-path shape: warps per variable (teams of P warps; at most 15 teams per CTA).
+int g_fast_p = 2;
+
+template <int NB, int KQ>
+cudaError_t dispatch_fast(const SweepArgs &a, int device, cudaStream_t st) {
+  switch (g_fast_p) {
+    case 1: return launch_fast<NB, KQ, 1, 512>(a, device, st);
+    case 4: return launch_fast<NB, KQ, 4, 1024>(a, device, st);
+    default: return launch_fast<NB, KQ, 2, 896>(a, device, st);
+  }
+}
+
 int grid_for(long long work, int threads) {
   long long b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -433,6 +742,8 @@ int grid_for(long long work, int threads) {
 }
 
 }  // namespace
+
+void set_sweep_shape(int warps_per_variable) { g_fast_p = warps_per_variable; }
 
 cudaError_t ksat_init_states(const KsatDevice &I, KsatReplicas &Rp, uint64_t seed,
                              const uint8_t *init_dev, cudaStream_t st) {
@@ -485,6 +796,11 @@ cudaError_t ksat_sweeps(const KsatDevice &I, KsatReplicas &Rp, const uint32_t *b
   a.t1 = t1;
   a.k0 = (uint32_t)seed;
   a.k1 = (uint32_t)(seed >> 32);
+  if (const char *env = getenv("NMC_SWEEP_WARPS")) g_fast_p = atoi(env);  // tuning override
+  if (Rp.W % 32 == 0 && I.nb <= 7 && g_fast_p > 0) {
+    if (I.kq == 1) return I.nb <= 5 ? dispatch_fast<5, 1>(a, device, st) : dispatch_fast<7, 1>(a, device, st);
+    return I.nb <= 5 ? dispatch_fast<5, 2>(a, device, st) : dispatch_fast<7, 2>(a, device, st);
+  }
   if (I.kq == 1) {
     if (I.nb <= 5) return launch_sweeps<5, 1>(a, device, st);
     if (I.nb <= 7) return launch_sweeps<7, 1>(a, device, st);

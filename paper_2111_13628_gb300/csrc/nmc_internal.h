@@ -74,6 +74,9 @@ cudaError_t ksat_sweeps(const KsatDevice &I, KsatReplicas &Rp, const uint32_t *b
 cudaError_t ksat_unpack(const KsatDevice &I, const KsatReplicas &Rp, uint8_t *states,
                         uint8_t *best_states, int64_t *energies, int64_t *best_energies,
                         cudaStream_t st);
+// Shape of the sweep kernel for W % 32 == 0: warps per variable (1, 2 or 4; 0 selects the
+// general kernel).
+void set_sweep_shape(int warps_per_variable);
 cudaError_t wait_selftest(GridBarrier *gb, unsigned long long limit_ns, cudaStream_t st);
 cudaError_t quantize_schedule(const float *beta, int32_t n_units, int32_t n_steps,
                               const int32_t *orig, uint32_t *bq, int32_t *bad,

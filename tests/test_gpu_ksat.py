@@ -203,3 +203,20 @@ def test_full_size_sampled_replicas(ctx):
         assert got["energies"][r] == O.ksat_energy(lits, n, got["states"][r])
         assert got["best_energies"][r] == O.ksat_energy(lits, n, got["best_states"][r])
     assert np.all(got["best_energies"] <= got["energies"])
+
+
+@pytest.mark.parametrize("warps", [0, 1, 2, 4])
+@pytest.mark.parametrize("n,alpha,k,R,T", [
+    (500, 9.6, 4, 1024, 20),    # one 32-word group
+    (300, 3.0, 6, 2048, 6),     # two word groups, two int4 per occurrence
+    (2000, 4.2, 3, 1024, 8),    # low degree: 5-bit counters
+])
+def test_sweep_shapes_agree(ctx, monkeypatch, warps, n, alpha, k, R, T):
+    """Every kernel shape (general kernel, teams of 1, 2 or 4 warps per variable) gives the
+    oracle's trajectories."""
+    monkeypatch.setenv("NMC_SWEEP_WARPS", str(warps))
+    lits = W.random_ksat(n, alpha, k, 700 + n)
+    beta = W.beta_inhomogeneous_linear(n, T, 0.3, 4.0, 0.3, 0.5, 800 + n)
+    got = _run(ctx, lits, n, beta, R, 0, T, seed=n)
+    want = O.ksat_anneal(lits, n, beta, 0, T, n, replicas=R)
+    _same(got, want)
