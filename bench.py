@@ -164,7 +164,10 @@ def run_ours(args, world, rank, local):
         ctx.replicas_reset(rs, seed_base + i)
         if ev is not None:
             ev[0].record(stream)
-        ctx.replicas_run(rs, 0, T)
+        if args.path == "batch":
+            ctx.batch_run([rs], 0, T)
+        else:
+            ctx.replicas_run(rs, 0, T)
         if ev is not None:
             ev[1].record(stream)
         ctx.replicas_read_device(rs, **out)
@@ -324,6 +327,9 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=8)
     ap.add_argument("--cpu-replicas", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--path", default="batch", choices=["batch", "grid"],
+                    help="batch: clustered shared-memory kernel (nmc_batch_run); grid: "
+                         "grid-barrier kernel (nmc_replicas_run)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -141,6 +141,19 @@ int nmc_replicas_read(nmc_ctx *ctx, int32_t rs, const nmc_result *out);
 int nmc_replicas_read_device(nmc_ctx *ctx, int32_t rs, const nmc_result *out_dev);
 
 /*
+ * Batched sweeps: runs sweeps t0[i]..t1[i]-1 of k-SAT replica sets rs[i] (i < n_sets), all in
+ * one persistent launch, asynchronously on the context's stream. Each set's result is bit for
+ * bit what nmc_replicas_run gives for it alone. Work is split into items of one word (32
+ * replicas) of one set; a CTA runs an item with the word vector in shared memory, so each
+ * instance needs n_vars <= the limit of nmc_batch_max_vars() and every variable in at most 127
+ * clauses (else NMC_EINVAL; use nmc_replicas_run for those). The same set may not appear twice.
+ */
+int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
+                  const int32_t *t1);
+/* Largest n_vars nmc_batch_run accepts on this context's device. */
+int32_t nmc_batch_max_vars(nmc_ctx *ctx);
+
+/*
  * One-shot anneal through host memory: creates a replica set, runs [t0, t1), copies the
  * results to the host buffers in *out and frees the set. Arguments as above.
  */

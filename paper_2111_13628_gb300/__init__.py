@@ -48,7 +48,8 @@ SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_
            "nmc_load_qap", "nmc_unload", "nmc_ksat_colouring", "nmc_set_schedule",
            "nmc_set_schedule_device", "nmc_replicas_create", "nmc_replicas_reset", "nmc_replicas_destroy",
            "nmc_replicas_run", "nmc_replicas_read", "nmc_replicas_read_device", "nmc_anneal",
-           "nmc_threshold_table", "nmc_selftest_wait_timeout"]
+           "nmc_threshold_table", "nmc_selftest_wait_timeout", "nmc_batch_run",
+           "nmc_batch_max_vars"]
 
 
 def library_path() -> str:
@@ -87,6 +88,8 @@ def load(build_if_missing: bool = True):
             "nmc_anneal": ([P, i32, i32, i32, i32, u64, P, P], C.c_int),
             "nmc_threshold_table": ([P, i32], i32),
             "nmc_selftest_wait_timeout": ([P, i32], C.c_int),
+            "nmc_batch_run": ([P, i32, P, P, P], C.c_int),
+            "nmc_batch_max_vars": ([P], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -219,6 +222,16 @@ class Context:
                                                   C.byref(rs)))
         self._rs[rs.value] = (inst, int(replicas))
         return rs.value
+
+    def batch_run(self, rs, t0, t1):
+        """Runs sweeps t0[i]..t1[i]-1 of k-SAT replica sets rs[i] in one batched launch."""
+        rs = np.ascontiguousarray(rs, dtype=np.int32)
+        t0 = np.ascontiguousarray(np.broadcast_to(t0, rs.shape), dtype=np.int32)
+        t1 = np.ascontiguousarray(np.broadcast_to(t1, rs.shape), dtype=np.int32)
+        self._check(self._lib.nmc_batch_run(self._h, rs.size, _ptr(rs), _ptr(t0), _ptr(t1)))
+
+    def batch_max_vars(self) -> int:
+        return int(self._lib.nmc_batch_max_vars(self._h))
 
     def replicas_reset(self, rs: int, seed: int, init=None):
         inst, R = self._rs[rs]

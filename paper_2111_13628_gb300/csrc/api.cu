@@ -1,8 +1,10 @@
 // Host side of the C ABI declared in include/nmc.h: argument checks, the instance build
 // (greedy colouring, renumbering, occurrence lists), device residency of instances, schedules
 // and replica sets, and the dispatch to the kernels in ksat.cu and qap.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -66,6 +68,9 @@ struct nmc_ctx {
   uint32_t *tab = nullptr;
   int32_t tab_len = 0;
   int32_t *flag = nullptr;  // device scratch flag for schedule validation
+  BatchItem *items = nullptr;  // batched-kernel work list (grown on demand)
+  size_t items_cap = 0;
+  int32_t *next_item = nullptr;  // two work counters (one per occurrence width)
 };
 
 namespace {
@@ -258,6 +263,8 @@ void nmc_destroy(nmc_ctx *ctx) {
   for (auto &kv : ctx->insts) free_instance(kv.second);
   dev_free(ctx->tab);
   dev_free(ctx->flag);
+  dev_free(ctx->items);
+  dev_free(ctx->next_item);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaGetLastError();
   delete ctx;
@@ -732,6 +739,104 @@ int nmc_replicas_read(nmc_ctx *ctx, int32_t rs, const nmc_result *out) {
 
 int nmc_replicas_read_device(nmc_ctx *ctx, int32_t rs, const nmc_result *out_dev) {
   return read_impl(ctx, rs, out_dev, false);
+}
+
+int32_t nmc_batch_max_vars(nmc_ctx *ctx) {
+  if (!ctx) return 0;
+  const size_t m = batch_max_vars(ctx->tab_len, ctx->device);
+  return m > 0x7FFFFFFF ? 0x7FFFFFFF : static_cast<int32_t>(m);
+}
+
+int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
+                  const int32_t *t1) {
+  if (!ctx) return NMC_EINVAL;
+  if (n_sets < 0 || (n_sets > 0 && (!rs || !t0 || !t1)))
+    return fail(ctx, NMC_EINVAL, "bad batch arrays");
+  DeviceGuard g(ctx->device);
+  const size_t max_vars = batch_max_vars(ctx->tab_len, ctx->device);
+  std::vector<BatchItem> by_kq[2];
+  int max_n[2] = {0, 0};
+  std::vector<long long> cost[2];
+  std::map<int32_t, int> seen;
+  for (int32_t i = 0; i < n_sets; ++i) {
+    ReplicaSet *S = find_set(ctx, rs[i]);
+    if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set in batch");
+    if (seen[rs[i]]++) return fail(ctx, NMC_EINVAL, "replica set repeated in batch");
+    Instance *I = find_inst(ctx, S->inst);
+    if (!I || I->kind != NMC_KIND_KSAT) return fail(ctx, NMC_EINVAL, "batch sets must be k-SAT");
+    if (t0[i] < 0 || t1[i] < t0[i]) return fail(ctx, NMC_EINVAL, "need 0 <= t0 <= t1");
+    if (t1[i] > t0[i] && (!I->bq || t1[i] > I->n_steps))
+      return fail(ctx, NMC_ESTATE, "schedule missing or shorter than t1");
+    if (I->ks.nb > 7) return fail(ctx, NMC_EINVAL, "batched sets need every variable in <= 127 clauses");
+    if (static_cast<size_t>(I->ks.n) > max_vars)
+      return fail(ctx, NMC_EINVAL, "instance too large for the batched kernel");
+    if (t1[i] == t0[i]) continue;
+    const int q = I->ks.kq == 1 ? 0 : 1;
+    for (int32_t w = 0; w < S->ks.W; ++w) {
+      BatchItem B;
+      B.occ = I->ks.occ;
+      B.occ_ptr = I->ks.occ_ptr;
+      B.col_ptr = I->ks.col_ptr;
+      B.orig = I->ks.orig;
+      B.bq = I->bq;
+      B.S = S->ks.S;
+      B.best = S->ks.best;
+      B.energy = S->ks.energy;
+      B.best_energy = S->ks.best_energy;
+      B.n = I->ks.n;
+      B.n_colours = I->ks.n_colours;
+      B.W = S->ks.W;
+      B.w = w;
+      B.t0 = t0[i];
+      B.t1 = t1[i];
+      B.k0 = static_cast<uint32_t>(S->seed);
+      B.k1 = static_cast<uint32_t>(S->seed >> 32);
+      by_kq[q].push_back(B);
+      cost[q].push_back(static_cast<long long>(I->ks.n_occ + I->ks.n) * (t1[i] - t0[i]));
+      if (I->ks.n > max_n[q]) max_n[q] = I->ks.n;
+    }
+  }
+  const size_t total = by_kq[0].size() + by_kq[1].size();
+  if (total == 0) return NMC_OK;
+  if (total > ctx->items_cap) {
+    NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    dev_free(ctx->items);
+    ctx->items_cap = 0;
+    NMC_CUDA(dev_alloc(&ctx->items, total), "allocate batch work list");
+    ctx->items_cap = total;
+  }
+  if (!ctx->next_item) NMC_CUDA(dev_alloc(&ctx->next_item, 2), "allocate batch counters");
+  // longest items first, so that the tail of the launch is short
+  std::vector<BatchItem> order;
+  order.reserve(total);
+  size_t off[2] = {0, 0};
+  for (int q = 0; q < 2; ++q) {
+    std::vector<size_t> idx(by_kq[q].size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return cost[q][a] > cost[q][b]; });
+    off[q] = order.size();
+    for (size_t k : idx) order.push_back(by_kq[q][k]);
+  }
+  NMC_CUDA(cudaMemcpyAsync(ctx->items, order.data(), sizeof(BatchItem) * total, cudaMemcpyHostToDevice,
+                           ctx->stream),
+           "upload batch work list");
+  int sms = 0;
+  NMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "query SMs");
+  for (int q = 0; q < 2; ++q) {
+    const int cnt = static_cast<int>(by_kq[q].size());
+    if (!cnt) continue;
+    // CTAs per item: spread few items over the SMs (word vectors replicated per cluster)
+    int cs = 1;
+    if (const char *env = getenv("NMC_BATCH_CTAS")) cs = atoi(env);
+    else
+      while (cs < 8 && static_cast<long long>(cnt) * cs * 2 <= sms) cs *= 2;
+    if (cs != 1 && cs != 2 && cs != 4 && cs != 8) cs = 1;
+    NMC_CUDA(ksat_batch(ctx->items + off[q], cnt, q + 1, cs, max_n[q], ctx->next_item + q,
+                        ctx->tab, ctx->tab_len, ctx->device, ctx->stream),
+             "launch batched sweep");
+  }
+  // the host vector is staged by cudaMemcpyAsync from pageable memory before it returns
+  return NMC_OK;
 }
 
 int nmc_anneal(nmc_ctx *ctx, int32_t inst, int32_t replicas, int32_t t0, int32_t t1,

@@ -48,46 +48,49 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident). Returns false when the
-// launch must stop (a wait expired here or in another CTA).
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident): each CTA stores its
+// barrier count into its own flag (release) and its first warp polls all flags (acquire)
+// until every CTA has arrived. No counter is shared, so arrivals do not serialise on one
+// address. Returns false when the launch must stop (a wait expired here or in another CTA).
 __device__ bool grid_sync(GridBarrier *gb, unsigned nblocks, unsigned &gen,
                           unsigned long long limit_ns) {
   __shared__ int s_ok;
+  const unsigned target = gen + 1u;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&gb->count, 1u) + 1u;
-    if (arrived == nblocks) {
-      atomicExch(&gb->count, 0u);
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
       __threadfence();
-      st_release(&gb->gen, gen + 1u);
-    } else {
-      const unsigned long long start = global_ns();
-      unsigned polls = 0;
-      while (ld_acquire(&gb->gen) == gen) {
-        ++polls;
-        if ((polls & 31u) == 0u) {
-          if (*(volatile int *)&gb->error) {
-            ok = 0;
-            break;
-          }
-          if (global_ns() - start > limit_ns || polls > kBarrierMaxPolls) {
+      st_release(&gb->flags[blockIdx.x], target);
+    }
+    __syncwarp();
+    int ok = 1;
+    const unsigned long long start = global_ns();
+    unsigned polls = 0;
+    while (true) {
+      bool mine = true;
+      for (unsigned i = threadIdx.x; i < nblocks; i += 32) mine &= ld_acquire(&gb->flags[i]) >= target;
+      if (__all_sync(0xFFFFFFFFu, mine)) break;
+      ++polls;
+      if ((polls & 15u) == 0u) {
+        int bad = 0;
+        if (threadIdx.x == 0) {
+          bad = *(volatile int *)&gb->error;
+          if (!bad && (global_ns() - start > limit_ns || polls > kBarrierMaxPolls)) {
             atomicExch(&gb->error, 1);
             atomicExch(&gb->sticky, 1);
-            ok = 0;
-            break;
+            bad = 1;
           }
         }
-        __nanosleep(40);
+        if (__shfl_sync(0xFFFFFFFFu, bad, 0)) {
+          ok = 0;
+          break;
+        }
       }
     }
-    __threadfence();
-    if (*(volatile int *)&gb->error) ok = 0;
-    s_ok = ok;
+    if (threadIdx.x == 0) s_ok = ok;
   }
   __syncthreads();
-  ++gen;
+  gen = target;
   return s_ok != 0;
 }
 
@@ -420,33 +423,48 @@ __device__ __forceinline__ void fast_attempt(const SweepArgs &a, const FastSmem 
   __syncwarp();
   const uint32_t vo = (uint32_t)__ldg(a.orig + v);
   uint32_t flip = 0u;
-  constexpr int GPW = 8 / P;  // Philox groups (4 replicas each) per warp
+  // Per-replica values: sign-extend D to 8 bit planes and transpose each 8x8 block (8 planes x
+  // 8 replicas) so that byte i of the result is replica i's signed energy change.
+  uint32_t s8[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s8[j] = j <= NB ? d[j] : d[NB];
+  constexpr int BPW = 4 / P;  // blocks of 8 replicas handled by this warp
 #pragma unroll 1
-  for (int gi = 0; gi < GPW; ++gi) {
-    const int g = p * GPW + gi;
-    int de[4];
-    uint32_t th[4];
-    bool need = false;
+  for (int qi = 0; qi < BPW; ++qi) {
+    const int q = p * BPW + qi;
+    const uint32_t sel = (uint32_t)q | ((uint32_t)(4 + q) << 4);
+    const uint32_t t01 = __byte_perm(s8[0], s8[1], sel), t23 = __byte_perm(s8[2], s8[3], sel);
+    const uint32_t t45 = __byte_perm(s8[4], s8[5], sel), t67 = __byte_perm(s8[6], s8[7], sel);
+    unsigned long long xm = (unsigned long long)__byte_perm(t01, t23, 0x5410) |
+                            ((unsigned long long)__byte_perm(t45, t67, 0x5410) << 32);
+    unsigned long long tt = (xm ^ (xm >> 7)) & 0x00AA00AA00AA00AAull;
+    xm = xm ^ tt ^ (tt << 7);
+    tt = (xm ^ (xm >> 14)) & 0x0000CCCC0000CCCCull;
+    xm = xm ^ tt ^ (tt << 14);
+    tt = (xm ^ (xm >> 28)) & 0x00000000F0F0F0F0ull;
+    xm = xm ^ tt ^ (tt << 28);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int b = 4 * g + j;
-      int val = 0;
+    for (int h = 0; h < 2; ++h) {
+      const int g = 2 * q + h;  // Philox group: replicas 4g..4g+3
+      int de[4];
+      uint32_t th[4];
+      bool need = false;
 #pragma unroll
-      for (int q = 0; q < NB; ++q) val |= (int)((d[q] >> b) & 1u) << q;
-      val -= (int)((d[NB] >> b) & 1u) << NB;
-      de[j] = val;
-      th[j] = val > 0 ? thr[val] : 0u;
-      need |= th[j] != 0u;
-    }
-    uint4 u = make_uint4(0u, 0u, 0u, 0u);
-    if (need) u = philox4x32_10(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * w + g), kTagKsatSweep),
-                                a.k0, a.k1);
+      for (int j = 0; j < 4; ++j) {
+        de[j] = (int)(signed char)(unsigned char)(xm >> (8 * (4 * h + j)));
+        th[j] = de[j] > 0 ? thr[de[j]] : 0u;
+        need |= th[j] != 0u;
+      }
+      uint4 u = make_uint4(0u, 0u, 0u, 0u);
+      if (need)
+        u = philox4x32_10(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * w + g), kTagKsatSweep), a.k0, a.k1);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const bool ok = de[j] <= 0 || uint4_word(u, j) < th[j];
-      if (ok) {
-        flip |= 1u << (4 * g + j);
-        if (de[j] != 0) sm.acc[(warp * (32 / P) + 4 * gi + j) * 32 + lane] += de[j];
+      for (int j = 0; j < 4; ++j) {
+        const bool ok = de[j] <= 0 || uint4_word(u, j) < th[j];
+        if (ok) {
+          flip |= 1u << (4 * g + j);
+          if (de[j] != 0) sm.acc[(warp * (32 / P) + 8 * qi + 4 * h + j) * 32 + lane] += de[j];
+        }
       }
     }
   }
@@ -695,7 +713,9 @@ cudaError_t launch_sweeps(const SweepArgs &a, int device, cudaStream_t st) {
   err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  while (per_sm > 1 && sms * per_sm > kMaxGridCtas) --per_sm;
   const int blocks = sms * per_sm;
+  if (blocks > kMaxGridCtas) return cudaErrorInvalidConfiguration;
   void *args[] = {(void *)&a};
   return cudaLaunchCooperativeKernel((const void *)kern, dim3(blocks), dim3(kSweepThreads), args,
                                      smem, st);
@@ -717,6 +737,8 @@ cudaError_t launch_fast(const SweepArgs &a, int device, cudaStream_t st) {
   err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  while (per_sm > 1 && sms * per_sm > kMaxGridCtas) --per_sm;
+  if (sms * per_sm > kMaxGridCtas) return cudaErrorInvalidConfiguration;
   void *args[] = {(void *)&a};
   return cudaLaunchCooperativeKernel((const void *)kern, dim3(sms * per_sm), dim3(threads), args,
                                      smem, st);
@@ -773,7 +795,7 @@ cudaError_t ksat_sweeps(const KsatDevice &I, KsatReplicas &Rp, const uint32_t *b
                         const uint32_t *tab, int32_t tab_len, int32_t t0, int32_t t1,
                         uint64_t seed, int device, cudaStream_t st) {
   if (t1 <= t0) return cudaSuccess;
-  cudaError_t err = cudaMemsetAsync(Rp.bar, 0, kBarrierResetBytes, st);
+  cudaError_t err = cudaMemsetAsync(reinterpret_cast<char *>(Rp.bar) + kBarrierResetOffset, 0, kBarrierResetBytes, st);
   if (err != cudaSuccess) return err;
   SweepArgs a;
   a.S = Rp.S;
@@ -823,7 +845,7 @@ cudaError_t ksat_unpack(const KsatDevice &I, const KsatReplicas &Rp, uint8_t *st
 }
 
 cudaError_t wait_selftest(GridBarrier *gb, unsigned long long limit_ns, cudaStream_t st) {
-  cudaError_t err = cudaMemsetAsync(gb, 0, kBarrierResetBytes, st);
+  cudaError_t err = cudaMemsetAsync(reinterpret_cast<char *>(gb) + kBarrierResetOffset, 0, kBarrierResetBytes, st);
   if (err != cudaSuccess) return err;
   wait_selftest_kernel<<<1, 32, 0, st>>>(gb, 2u, limit_ns);
   return cudaGetLastError();

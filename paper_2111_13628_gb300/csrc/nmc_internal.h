@@ -17,15 +17,17 @@ constexpr int kMaxReplicas = 4096;
 constexpr int kMaxDegree = 1023; // occurrences of one variable (10-bit sliced counters)
 constexpr int kMaxQapN = 256;
 
-// Barrier shared by all CTAs of a cooperative launch. Reset before every launch.
+// Barrier shared by all CTAs of a cooperative launch: every CTA publishes the number of
+// barriers it has passed in its own flag and waits until all flags reach it.
+constexpr int kMaxGridCtas = 1024;
 struct GridBarrier {
-  unsigned int count;
-  unsigned int gen;
-  int error;   // 1 = a wait expired (the launch stopped early); reset with the barrier
-  int sticky;  // also set on expiry, kept across launches until the host reads it
+  int sticky;  // set when a wait expired; kept across launches until the host reads it
+  int error;   // set when a wait expired; the launch stops early (cleared every launch)
+  unsigned int flags[kMaxGridCtas];
 };
-// Bytes of GridBarrier cleared before every launch (count, gen, error; not sticky).
-constexpr size_t kBarrierResetBytes = 3 * sizeof(unsigned int);
+// Bytes of GridBarrier cleared before every launch (everything but sticky).
+constexpr size_t kBarrierResetOffset = sizeof(int);
+constexpr size_t kBarrierResetBytes = sizeof(GridBarrier) - sizeof(int);
 
 // Device-resident k-SAT instance after the host build (variables renumbered so that every
 // colour class is a contiguous id range; "new" ids below).
@@ -64,6 +66,22 @@ struct QapReplicas {
   int64_t *energy, *best_energy;
 };
 
+// One work item of the batched kernel: one word (32 replicas) of one replica set, sweeps
+// [t0, t1), with pointers into the instance, its schedule and the replica set.
+struct BatchItem {
+  const int4 *occ;
+  const int32_t *occ_ptr;
+  const int32_t *col_ptr;
+  const int32_t *orig;
+  const uint32_t *bq;
+  uint32_t *S;
+  uint32_t *best;
+  int32_t *energy;
+  int32_t *best_energy;
+  int32_t n, n_colours, W, w, t0, t1;
+  uint32_t k0, k1;
+};
+
 // ---- k-SAT launchers (ksat.cu); all asynchronous on `st` -------------------------------
 cudaError_t ksat_init_states(const KsatDevice &I, KsatReplicas &Rp, uint64_t seed,
                              const uint8_t *init_dev, cudaStream_t st);
@@ -81,6 +99,15 @@ cudaError_t wait_selftest(GridBarrier *gb, unsigned long long limit_ns, cudaStre
 cudaError_t quantize_schedule(const float *beta, int32_t n_units, int32_t n_steps,
                               const int32_t *orig, uint32_t *bq, int32_t *bad,
                               cudaStream_t st);
+
+// ---- batched k-SAT (batch.cu) -----------------------------------------------------------
+// Largest n whose word vector fits the batched kernel's shared memory on `device`.
+size_t batch_max_vars(int tab_len, int device);
+// Runs n_items items (all of one occurrence width kq) in one launch with cs CTAs (1, 2, 4, 8)
+// per item; next_item is a device int.
+cudaError_t ksat_batch(const BatchItem *items_dev, int n_items, int kq, int cs, int max_n,
+                       int *next_item, const uint32_t *tab, int tab_len, int device,
+                       cudaStream_t st);
 
 // ---- QAP launchers (qap.cu) ------------------------------------------------------------
 cudaError_t qap_init_states(const QapDevice &I, QapReplicas &Rp, uint64_t seed,
