@@ -160,6 +160,52 @@ int32_t nmc_batch_max_vars(nmc_ctx *ctx);
 int nmc_anneal(nmc_ctx *ctx, int32_t inst, int32_t replicas, int32_t t0, int32_t t1,
                uint64_t seed, const void *init_states, const nmc_result *out);
 
+/*
+ * Serving: continuous batching of anneal requests on one GPU.
+ *
+ * A server owns a private context on `device` and one worker thread. Requests are copied at
+ * submission and queued; the worker admits them (FIFO) while at most max_active are active and
+ * the device memory they will hold stays within memory_budget bytes (a request larger than the
+ * whole budget fails with NMC_ENOMEM). Admitted requests keep their instance, schedule and
+ * replica state resident on the device until they finish. Every tick advances all active
+ * requests by a slice of about 2^slice_log2 variable-word updates each, k-SAT requests together
+ * in one batched launch (nmc_batch_run), so requests that arrive while others run share the
+ * following launches. Results are bit for bit those of nmc_anneal on the same inputs
+ * (segment invariance). All nmc_server_* calls are thread-safe.
+ */
+typedef struct nmc_server nmc_server;
+typedef struct nmc_server_config {
+  int32_t max_active;     /* >= 1 */
+  int64_t memory_budget;  /* bytes, >= 1 */
+  int32_t slice_log2;     /* 10..40 */
+} nmc_server_config;
+int nmc_server_create(int device, const nmc_server_config *cfg, nmc_server **out);
+/* Stops the worker (requests still queued or running fail with NMC_ESTATE) and frees all. */
+void nmc_server_destroy(nmc_server *srv);
+/* Queues an anneal of sweeps 0..n_steps-1 (arguments as nmc_load_ksat / nmc_set_schedule /
+ * nmc_replicas_create with Philox initial states). *req_out receives the request id. */
+int nmc_server_submit_ksat(nmc_server *srv, int32_t n_vars, int32_t n_clauses, int32_t k_max,
+                           const int32_t *lits, int32_t n_steps, const float *beta,
+                           int32_t replicas, uint64_t seed, int64_t *req_out);
+int nmc_server_submit_qap(nmc_server *srv, int32_t n, const int32_t *F, const int32_t *D,
+                          int32_t n_steps, const float *beta, int32_t replicas, uint64_t seed,
+                          int64_t *req_out);
+/* *status: 0 queued, 1 running, 2 done, or the negative error code of a failed request. Waits
+ * up to wait_ms for completion (0: no wait). */
+int nmc_server_poll(nmc_server *srv, int64_t req, int32_t wait_ms, int32_t *status);
+/* Copies a finished request's results to host buffers (layout as nmc_replicas_read; fields may
+ * be NULL), reports its latency from submission to completion in seconds, and forgets it.
+ * Returns the request's error code if it failed, NMC_ESTATE if it is not finished. */
+int nmc_server_result(nmc_server *srv, int64_t req, const nmc_result *out, double *latency_s);
+/* Asks for a request to be dropped at the next tick (its status becomes NMC_ESTATE). */
+int nmc_server_cancel(nmc_server *srv, int64_t req);
+/* Counters: ticks, Metropolis attempts executed, seconds spent in ticks, queue and active sizes,
+ * device memory held by active requests (estimate). Any pointer may be NULL. */
+int nmc_server_stats(nmc_server *srv, int64_t *ticks, int64_t *attempts, double *busy_s,
+                     int32_t *queued, int32_t *active, int64_t *mem_in_use);
+/* Message of the last failed nmc_server_result. */
+const char *nmc_server_last_error(nmc_server *srv);
+
 /* Self-test of the bounded device wait: launches one CTA that waits at the grid barrier the
  * sweep kernel uses, for a second arrival that never comes, with the given limit in
  * milliseconds (1..10000). Returns NMC_ETIMEOUT when the wait expired and was reported as

@@ -49,7 +49,10 @@ SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_
            "nmc_set_schedule_device", "nmc_replicas_create", "nmc_replicas_reset", "nmc_replicas_destroy",
            "nmc_replicas_run", "nmc_replicas_read", "nmc_replicas_read_device", "nmc_anneal",
            "nmc_threshold_table", "nmc_selftest_wait_timeout", "nmc_batch_run",
-           "nmc_batch_max_vars"]
+           "nmc_batch_max_vars", "nmc_server_create", "nmc_server_destroy",
+           "nmc_server_submit_ksat", "nmc_server_submit_qap", "nmc_server_poll",
+           "nmc_server_result", "nmc_server_cancel", "nmc_server_stats",
+           "nmc_server_last_error"]
 
 
 def library_path() -> str:
@@ -90,6 +93,15 @@ def load(build_if_missing: bool = True):
             "nmc_selftest_wait_timeout": ([P, i32], C.c_int),
             "nmc_batch_run": ([P, i32, P, P, P], C.c_int),
             "nmc_batch_max_vars": ([P], i32),
+            "nmc_server_create": ([C.c_int, P, P], C.c_int),
+            "nmc_server_destroy": ([P], None),
+            "nmc_server_submit_ksat": ([P, i32, i32, i32, P, i32, P, i32, u64, P], C.c_int),
+            "nmc_server_submit_qap": ([P, i32, P, P, i32, P, i32, u64, P], C.c_int),
+            "nmc_server_poll": ([P, C.c_int64, i32, P], C.c_int),
+            "nmc_server_result": ([P, C.c_int64, P, P], C.c_int),
+            "nmc_server_cancel": ([P, C.c_int64], C.c_int),
+            "nmc_server_stats": ([P, P, P, P, P, P, P], C.c_int),
+            "nmc_server_last_error": ([P], C.c_char_p),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -284,3 +296,99 @@ class Context:
         self._check(self._lib.nmc_anneal(self._h, int(inst), int(replicas), int(t0), int(t1),
                                          int(seed) & (2**64 - 1), _ptr(init), C.byref(res)))
         return out
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_active", C.c_int32), ("memory_budget", C.c_int64), ("slice_log2", C.c_int32)]
+
+
+class Server:
+    """Continuous-batching anneal server (nmc_server_*); thread-safe."""
+
+    def __init__(self, device: int = 0, max_active: int = 256, memory_budget: int = 64 << 30,
+                 slice_log2: int = 22):
+        self._lib = load()
+        cfg = ServerConfig(int(max_active), int(memory_budget), int(slice_log2))
+        h = C.c_void_p()
+        rc = self._lib.nmc_server_create(int(device), C.byref(cfg), C.byref(h))
+        if rc != NMC_OK:
+            raise NmcError(rc, "nmc_server_create failed")
+        self._h = h
+        self._meta = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nmc_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _id(self, rc, req, meta):
+        if rc != NMC_OK:
+            raise NmcError(rc, "submit rejected")
+        self._meta[req.value] = meta
+        return req.value
+
+    def submit_ksat(self, lits, n_vars, beta, replicas, seed) -> int:
+        lits = np.ascontiguousarray(lits, dtype=np.int32)
+        beta = np.ascontiguousarray(beta, dtype=np.float32)
+        req = C.c_int64()
+        rc = self._lib.nmc_server_submit_ksat(self._h, int(n_vars), lits.shape[0], lits.shape[1],
+                                              _ptr(lits), beta.shape[1], _ptr(beta), int(replicas),
+                                              int(seed) & (2**64 - 1), C.byref(req))
+        return self._id(rc, req, (KIND_KSAT, int(n_vars), int(replicas)))
+
+    def submit_qap(self, F, D, beta, replicas, seed) -> int:
+        F = np.ascontiguousarray(F, dtype=np.int32)
+        D = np.ascontiguousarray(D, dtype=np.int32)
+        beta = np.ascontiguousarray(beta, dtype=np.float32)
+        req = C.c_int64()
+        rc = self._lib.nmc_server_submit_qap(self._h, F.shape[0], _ptr(F), _ptr(D), beta.shape[1],
+                                             _ptr(beta), int(replicas), int(seed) & (2**64 - 1),
+                                             C.byref(req))
+        return self._id(rc, req, (KIND_QAP, F.shape[0], int(replicas)))
+
+    def poll(self, req: int, wait_ms: int = 0) -> int:
+        st = C.c_int32()
+        rc = self._lib.nmc_server_poll(self._h, C.c_int64(req), int(wait_ms), C.byref(st))
+        if rc != NMC_OK:
+            raise NmcError(rc, "poll failed")
+        return st.value
+
+    def result(self, req: int):
+        """(dict of arrays, latency seconds); raises NmcError if the request failed."""
+        kind, n, R = self._meta[req]
+        dt = np.uint8 if kind == KIND_KSAT else np.int16
+        out = dict(states=np.zeros((R, n), dtype=dt), energies=np.zeros(R, dtype=np.int64),
+                   best_energies=np.zeros(R, dtype=np.int64), best_states=np.zeros((R, n), dtype=dt))
+        res = Result(_ptr(out["states"]), _ptr(out["energies"]), _ptr(out["best_energies"]),
+                     _ptr(out["best_states"]))
+        lat = C.c_double()
+        rc = self._lib.nmc_server_result(self._h, C.c_int64(req), C.byref(res), C.byref(lat))
+        if rc != NMC_OK:
+            raise NmcError(rc, self._lib.nmc_server_last_error(self._h).decode())
+        self._meta.pop(req, None)
+        return out, lat.value
+
+    def cancel(self, req: int):
+        rc = self._lib.nmc_server_cancel(self._h, C.c_int64(req))
+        if rc != NMC_OK:
+            raise NmcError(rc, "cancel failed")
+
+    def stats(self) -> dict:
+        t, a, q, act, mem = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int32(), C.c_int64()
+        busy = C.c_double()
+        self._lib.nmc_server_stats(self._h, C.byref(t), C.byref(a), C.byref(busy), C.byref(q),
+                                   C.byref(act), C.byref(mem))
+        return dict(ticks=t.value, attempts=a.value, busy_s=busy.value, queued=q.value,
+                    active=act.value, mem_in_use=mem.value)

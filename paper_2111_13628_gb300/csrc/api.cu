@@ -124,6 +124,9 @@ void free_instance(Instance &I) {
   dev_free(I.ks.orig);
   dev_free(I.ks.newid);
   dev_free(I.ks.clits);
+  dev_free(I.ks.occ_t);
+  dev_free(I.ks.grp_base);
+  dev_free(I.ks.cgrp);
   dev_free(I.qp.F);
   dev_free(I.qp.D);
   dev_free(I.bq);
@@ -371,18 +374,21 @@ int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max
     colour[v] = c;
     if (c + 1 > n_colours) n_colours = c + 1;
   }
-  // -- renumber: colour-major, original id minor
+  // -- renumber: colour-major; inside a colour class by decreasing degree, then original id
+  //    (the order inside a class does not change the dynamics; similar degrees side by side
+  //    keep the warp-interleaved occurrence groups below nearly free of padding)
   std::vector<int32_t> col_ptr(n_colours + 1, 0);
   for (int32_t v = 0; v < n; ++v) ++col_ptr[colour[v] + 1];
   for (int32_t c = 0; c < n_colours; ++c) col_ptr[c + 1] += col_ptr[c];
   std::vector<int32_t> orig(n), newid(n);
   {
-    std::vector<int32_t> fill(col_ptr.begin(), col_ptr.end() - 1);
-    for (int32_t v = 0; v < n; ++v) {
-      const int32_t p = fill[colour[v]]++;
-      orig[p] = v;
-      newid[v] = p;
-    }
+    for (int32_t v = 0; v < n; ++v) orig[v] = v;
+    std::stable_sort(orig.begin(), orig.end(), [&](int32_t a, int32_t b) {
+      if (colour[a] != colour[b]) return colour[a] < colour[b];
+      if (deg[a] != deg[b]) return deg[a] > deg[b];
+      return a < b;
+    });
+    for (int32_t p = 0; p < n; ++p) newid[orig[p]] = p;
   }
   // -- occurrence lists in new ids, each padded to a multiple of 4 occurrences
   const int kq = K <= 4 ? 1 : 2;
@@ -416,6 +422,45 @@ int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max
       slot[1] = lit_true;
     }
   }
+  // -- the same lists interleaved per group of 32 consecutive variables of a colour class
+  //    (group g covers new ids [col_ptr[c] + 32k, +32)): occurrence j of the group's lane l
+  //    sits at grp_base[g] + (j*kq + q)*32 + l (int4 units), so one warp load of occurrence j
+  //    is contiguous. Each group is padded to its longest list with inert entries.
+  std::vector<int32_t> cgrp(n_colours + 1, 0), grp_base(1, 0);
+  for (int32_t c = 0; c < n_colours; ++c) {
+    const int32_t size = col_ptr[c + 1] - col_ptr[c];
+    cgrp[c + 1] = cgrp[c] + (size + 31) / 32;
+    for (int32_t g0 = col_ptr[c]; g0 < col_ptr[c + 1]; g0 += 32) {
+      int32_t len = 0;
+      for (int32_t v = g0; v < std::min(g0 + 32, col_ptr[c + 1]); ++v)
+        len = std::max(len, occ_ptr[v + 1] - occ_ptr[v]);
+      grp_base.push_back(grp_base.back() + len * kq * 32);
+    }
+  }
+  std::vector<int32_t> occ_t(static_cast<size_t>(std::max<int64_t>(grp_base.back(), 1)) * 4);
+  for (int32_t c = 0; c < n_colours; ++c) {
+    int32_t g = cgrp[c];
+    for (int32_t g0 = col_ptr[c]; g0 < col_ptr[c + 1]; g0 += 32, ++g) {
+      const int32_t len = (grp_base[g + 1] - grp_base[g]) / (kq * 32);
+      for (int32_t l = 0; l < 32; ++l) {
+        const int32_t v = g0 + l;
+        for (int32_t j = 0; j < len; ++j)
+          for (int q = 0; q < kq; ++q) {
+            int32_t *dst = &occ_t[(static_cast<size_t>(grp_base[g]) + (j * kq + q) * 32 + l) * 4];
+            const bool real = v < col_ptr[c + 1] && j < occ_ptr[v + 1] - occ_ptr[v];
+            if (real) {
+              const int32_t *src = &occ[(static_cast<size_t>(occ_ptr[v] + j) * slots) + 4 * q];
+              for (int z = 0; z < 4; ++z) dst[z] = src[z];
+            } else {  // inert: own sign 0, one always-true literal
+              dst[0] = q == 0 ? 0 : lit_false;
+              dst[1] = q == 0 ? lit_true : lit_false;
+              dst[2] = lit_false;
+              dst[3] = lit_false;
+            }
+          }
+      }
+    }
+  }
   std::vector<int32_t> clits(static_cast<size_t>(m > 0 ? m : 1) * K, lit_false);
   for (int64_t a = 0; a < m; ++a)
     for (int q = 0; q < K; ++q) {
@@ -446,6 +491,12 @@ int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max
       (e = dev_alloc(&I.ks.orig, n)) != cudaSuccess ||
       (e = dev_alloc(&I.ks.newid, n)) != cudaSuccess ||
       (e = dev_alloc(&I.ks.clits, clits.size())) != cudaSuccess ||
+      (e = dev_alloc(&I.ks.occ_t, occ_t.size() / 4)) != cudaSuccess ||
+      (e = dev_alloc(&I.ks.grp_base, grp_base.size())) != cudaSuccess ||
+      (e = dev_alloc(&I.ks.cgrp, cgrp.size())) != cudaSuccess ||
+      (e = cudaMemcpy(I.ks.occ_t, occ_t.data(), sizeof(int32_t) * occ_t.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(I.ks.grp_base, grp_base.data(), sizeof(int32_t) * grp_base.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(I.ks.cgrp, cgrp.data(), sizeof(int32_t) * cgrp.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(I.ks.occ, occ.data(), sizeof(int32_t) * occ.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(I.ks.occ_ptr, occ_ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(I.ks.col_ptr, col_ptr.data(), sizeof(int32_t) * (n_colours + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -774,8 +825,9 @@ int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t
     const int q = I->ks.kq == 1 ? 0 : 1;
     for (int32_t w = 0; w < S->ks.W; ++w) {
       BatchItem B;
-      B.occ = I->ks.occ;
-      B.occ_ptr = I->ks.occ_ptr;
+      B.occ_t = I->ks.occ_t;
+      B.grp_base = I->ks.grp_base;
+      B.cgrp = I->ks.cgrp;
       B.col_ptr = I->ks.col_ptr;
       B.orig = I->ks.orig;
       B.bq = I->bq;

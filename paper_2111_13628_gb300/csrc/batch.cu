@@ -48,10 +48,11 @@ __device__ __forceinline__ uint32_t lit_word(const uint32_t *xs, int l) {
   return xs[l >> 1] ^ (0u - (uint32_t)(l & 1));
 }
 
+// v = c0 + off is a variable of colour class c (starting at new id c0).
 template <int KQ>
 __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint32_t *xs,
-                                                  const uint32_t *tab_s, int tab_len, int v,
-                                                  int t, int (&acc)[32]) {
+                                                  const uint32_t *tab_s, int tab_len, int c,
+                                                  int c0, int v, int t, int (&acc)[32]) {
   constexpr int NB = 7;
   const uint32_t x = xs[v];
   const uint32_t bqv = __ldg(B.bq + (size_t)t * B.n + v);
@@ -61,15 +62,19 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
     bc[j] = 0u;
     mc[j] = 0u;
   }
-  const int e0 = __ldg(B.occ_ptr + v), e1 = __ldg(B.occ_ptr + v + 1);
-  for (int e = e0; e < e1; e += 4) {
+  const int off = v - c0;
+  const int g = __ldg(B.cgrp + c) + (off >> 5), ln = off & 31;
+  const int gb = __ldg(B.grp_base + g);
+  const int len = (__ldg(B.grp_base + g + 1) - gb) / (32 * KQ);
+  const int4 *ent = B.occ_t + gb + ln;
+  for (int e = 0; e < len; e += 4) {
     uint32_t bb[4], mm[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int4 q = __ldg(B.occ + (size_t)(e + j) * KQ);
+      const int4 q = __ldg(ent + (size_t)((e + j) * KQ) * 32);
       uint32_t o = lit_word(xs, q.y) | lit_word(xs, q.z) | lit_word(xs, q.w);
       if (KQ == 2) {
-        const int4 q2 = __ldg(B.occ + (size_t)(e + j) * KQ + 1);
+        const int4 q2 = __ldg(ent + (size_t)((e + j) * KQ + 1) * 32);
         o |= lit_word(xs, q2.x) | lit_word(xs, q2.y) | lit_word(xs, q2.z) | lit_word(xs, q2.w);
       }
       const uint32_t own = x ^ (uint32_t)q.x;
@@ -91,6 +96,9 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
     s8[NB] = br;
   }
   const uint32_t vo = (uint32_t)__ldg(B.orig + v);
+  // (bq * dE) >> 8 in 32-bit pieces: bq = 256 hi + lo, so the index is hi dE + (lo dE) >> 8
+  // exactly (dE <= 127 keeps both terms below 2^31).
+  const uint32_t bq_hi = bqv >> 8, bq_lo = bqv & 255u;
   uint32_t flip = 0u;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -116,8 +124,8 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
         de[j] = (int)(signed char)(unsigned char)(xm >> (8 * (4 * h + j)));
         th[j] = 0u;
         if (de[j] > 0) {
-          const unsigned long long idx = ((unsigned long long)bqv * (unsigned)de[j]) >> 8;
-          th[j] = idx < (unsigned long long)tab_len ? tab_s[idx] : 0u;
+          const uint32_t idx = bq_hi * (uint32_t)de[j] + ((bq_lo * (uint32_t)de[j]) >> 8);
+          th[j] = idx < (uint32_t)tab_len ? tab_s[idx] : 0u;
         }
         need |= th[j] != 0u;
       }
@@ -195,10 +203,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
       for (int b = 0; b < 32; ++b) acc[b] = 0;
       for (int c = 0; c < B.n_colours; ++c) {
         const int c0 = __ldg(B.col_ptr + c), c1 = __ldg(B.col_ptr + c + 1);
-        const int part = (c1 - c0 + CS - 1) / CS;
+        const int part = ((c1 - c0 + CS - 1) / CS + 31) & ~31;  // whole 32-variable groups
         const int v0 = c0 + rank * part, v1 = min(c1, v0 + part);
         for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-          const uint32_t xn = attempt_batch<KQ>(B, xs, tab_s, tab_len, v, t, acc);
+          const uint32_t xn = attempt_batch<KQ>(B, xs, tab_s, tab_len, c, c0, v, t, acc);
 #pragma unroll
           for (int r = 0; r < CS; ++r) rank_ptr<CS>(xs, r)[v] = xn;
         }

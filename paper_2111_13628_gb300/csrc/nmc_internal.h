@@ -41,6 +41,9 @@ struct KsatDevice {
   int32_t *orig;                      // n: new id -> original id
   int32_t *newid;                     // n: original id -> new id
   int32_t *clits;                     // m * kmax literal ids (2*new+neg), pad = 2n (false)
+  int4 *occ_t;                        // occurrence lists interleaved per 32-variable group
+  int32_t *grp_base;                  // groups+1: start of each group in occ_t (int4 units)
+  int32_t *cgrp;                      // n_colours+1: first group of each colour class
 };
 
 // Replica state of one k-SAT replica set: W = ceil(R/32) words per literal row.
@@ -69,8 +72,9 @@ struct QapReplicas {
 // One work item of the batched kernel: one word (32 replicas) of one replica set, sweeps
 // [t0, t1), with pointers into the instance, its schedule and the replica set.
 struct BatchItem {
-  const int4 *occ;
-  const int32_t *occ_ptr;
+  const int4 *occ_t;
+  const int32_t *grp_base;
+  const int32_t *cgrp;
   const int32_t *col_ptr;
   const int32_t *orig;
   const uint32_t *bq;

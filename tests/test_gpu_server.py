@@ -1,0 +1,91 @@
+"""Serving loop: requests that overlap on the device give, each, exactly what they give alone."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import nmc_inputs as W
+
+pytestmark = pytest.mark.gpu
+KEYS = ("states", "energies", "best_energies", "best_states")
+
+
+def _requests():
+    reqs = []
+    for i, (n, alpha, k, T, R) in enumerate([(700, 9.6, 4, 60, 32), (2500, 9.2, 4, 40, 32),
+                                             (300, 4.2, 3, 90, 64), (5000, 9.8, 4, 25, 32),
+                                             (150, 9.6, 4, 200, 96)]):
+        lits = W.random_ksat(n, alpha, k, 300 + i)
+        beta = W.beta_inhomogeneous_linear(n, T, 0.5, 4.0, 0.3, 0.5, 400 + i)
+        reqs.append(("ksat", dict(lits=lits, n_vars=n, beta=beta, replicas=R, seed=500 + i)))
+    for i, (n, T, R) in enumerate([(40, 12, 256), (97, 6, 256)]):
+        F, D = W.random_qap(n, 600 + i)
+        beta = W.beta_scaled_linear(n, T, 0.01, 1.0, 0.5, 1.5, 700 + i)
+        reqs.append(("qap", dict(F=F, D=D, beta=beta, replicas=R, seed=800 + i)))
+    return reqs
+
+
+def _alone(kind, r):
+    import paper_2111_13628_gb300 as nmc
+    with nmc.Context(0) as ctx:
+        if kind == "ksat":
+            inst = ctx.load_ksat(r["lits"], r["n_vars"])
+        else:
+            inst = ctx.load_qap(r["F"], r["D"])
+        ctx.set_schedule(inst, r["beta"])
+        return ctx.anneal(inst, r["replicas"], 0, r["beta"].shape[1], r["seed"])
+
+
+def test_mixed_requests_match_alone():
+    import paper_2111_13628_gb300 as nmc
+    reqs = _requests()
+    ids = [None] * len(reqs)
+    with nmc.Server(0, max_active=4, slice_log2=14) as srv:
+        def submit(i):
+            time.sleep(0.002 * i)  # staggered arrivals while earlier requests run
+            kind, r = reqs[i]
+            if kind == "ksat":
+                ids[i] = srv.submit_ksat(r["lits"], r["n_vars"], r["beta"], r["replicas"], r["seed"])
+            else:
+                ids[i] = srv.submit_qap(r["F"], r["D"], r["beta"], r["replicas"], r["seed"])
+        th = [threading.Thread(target=submit, args=(i,)) for i in range(len(reqs))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        outs = []
+        for i in ids:
+            deadline = time.time() + 120
+            while srv.poll(i, wait_ms=200) not in (2,) and time.time() < deadline:
+                pass
+            outs.append(srv.result(i))
+        st = srv.stats()
+        assert st["ticks"] > 1 and st["attempts"] > 0
+    for (kind, r), (got, lat) in zip(reqs, outs):
+        assert lat > 0
+        want = _alone(kind, r)
+        for key in KEYS:
+            assert np.array_equal(got[key], want[key]), (kind, key)
+
+
+def test_admission_limits_cancel_and_errors():
+    import paper_2111_13628_gb300 as nmc
+    lits = W.random_ksat(400, 9.6, 4, 1)
+    beta = W.beta_constant(400, 3000, 2.0)
+    with nmc.Server(0, max_active=1, memory_budget=64 << 20, slice_log2=12) as srv:
+        big = srv.submit_ksat(W.random_ksat(20000, 9.6, 4, 2), 20000,
+                              W.beta_constant(20000, 400, 1.0), 1024, 1)   # > 64 MB budget
+        a = srv.submit_ksat(lits, 400, beta, 32, 1)
+        b = srv.submit_ksat(lits, 400, beta, 32, 2)                      # waits for the slot
+        bad = srv.submit_ksat(np.array([[1, -1, 2]], np.int32), 5, W.beta_constant(5, 2, 1.0), 32, 3)
+        assert srv.poll(big, wait_ms=30000) == nmc.NMC_ENOMEM
+        with pytest.raises(nmc.NmcError):
+            srv.result(big)
+        time.sleep(0.05)
+        assert srv.poll(b) == 0          # still queued behind a (one active slot)
+        srv.cancel(a)
+        srv.cancel(b)
+        assert srv.poll(a, wait_ms=30000) == nmc.NMC_ESTATE
+        assert srv.poll(b, wait_ms=30000) == nmc.NMC_ESTATE
+        assert srv.poll(bad, wait_ms=60000) == nmc.NMC_EINVAL
