@@ -167,7 +167,7 @@ def run_ours(args, world, rank, local):
         if args.path == "batch":
             ctx.batch_run([rs], 0, T)
         else:
-            ctx.replicas_run(rs, 0, T)
+            ctx.replicas_run(rs, 0, T)  # "run": library's choice; "grid": NMC_RUN_PATH=grid
         if ev is not None:
             ev[1].record(stream)
         ctx.replicas_read_device(rs, **out)
@@ -327,10 +327,12 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=8)
     ap.add_argument("--cpu-replicas", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--path", default="batch", choices=["batch", "grid"],
-                    help="batch: clustered shared-memory kernel (nmc_batch_run); grid: "
-                         "grid-barrier kernel (nmc_replicas_run)")
+    ap.add_argument("--path", default="run", choices=["run", "batch", "grid"],
+                    help="run: nmc_replicas_run (the library picks the kernel); batch: "
+                         "nmc_batch_run; grid: nmc_replicas_run on the grid-barrier kernel")
     args = ap.parse_args()
+    if args.path == "grid":
+        os.environ["NMC_RUN_PATH"] = "grid"
     world, rank, local = dist_setup()
     if args.impl == "reference":
         res = run_reference(args, world, rank)

@@ -110,6 +110,12 @@ int nmc_ksat_colouring(nmc_ctx *ctx, int32_t inst, int32_t *colour_out, int32_t 
 int nmc_set_schedule(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const float *beta);
 /* As nmc_set_schedule, with beta in device memory (read on the context's stream). */
 int nmc_set_schedule_device(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const float *beta_dev);
+/* As nmc_set_schedule for the rank-one profile beta[u][t] = base[t] * factor[u] (the product
+ * rounded to float32, round to nearest even): a global anneal scaled per unit, the shape of
+ * the sampling stage's heated-backbone profiles. base: n_steps floats, factor: n_units floats,
+ * host memory. */
+int nmc_set_schedule_factored(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const float *base,
+                              const float *factor);
 
 /*
  * Creates a resident replica set of `replicas` chains (1..4096) of an instance, seeded by
@@ -128,7 +134,9 @@ int nmc_replicas_reset(nmc_ctx *ctx, int32_t rs, uint64_t seed, const void *init
 int nmc_replicas_destroy(nmc_ctx *ctx, int32_t rs);
 /*
  * Runs sweeps (k-SAT) or steps (QAP) t0..t1-1 of the schedule on the resident replica set,
- * asynchronously on the context's stream. t is absolute, so [t0,t1) then [t1,t2) equals
+ * asynchronously on the context's stream. A k-SAT set that nmc_batch_run accepts runs on that
+ * (shared-memory, cluster) kernel, any other on the grid-barrier kernel; the results are the
+ * same bit for bit (the environment variable NMC_RUN_PATH=grid forces the grid kernel). t is absolute, so [t0,t1) then [t1,t2) equals
  * [t0,t2) bit for bit. Requires 0 <= t0 <= t1 <= n_steps of the current schedule
  * (NMC_ESTATE otherwise). A device-side wait that expires is reported as NMC_ETIMEOUT by the
  * next synchronising call on this replica set.
@@ -174,6 +182,14 @@ int nmc_anneal(nmc_ctx *ctx, int32_t inst, int32_t replicas, int32_t t0, int32_t
  * (segment invariance). All nmc_server_* calls are thread-safe.
  */
 typedef struct nmc_server nmc_server;
+/* A request's schedule: either beta ([n_units][n_steps], as nmc_set_schedule) or, when beta is
+ * NULL, the factored form base[n_steps] x factor[n_units] (as nmc_set_schedule_factored). */
+typedef struct nmc_schedule {
+  int32_t n_steps;
+  const float *beta;
+  const float *base;
+  const float *factor;
+} nmc_schedule;
 typedef struct nmc_server_config {
   int32_t max_active;     /* >= 1 */
   int64_t memory_budget;  /* bytes, >= 1 */
@@ -182,13 +198,14 @@ typedef struct nmc_server_config {
 int nmc_server_create(int device, const nmc_server_config *cfg, nmc_server **out);
 /* Stops the worker (requests still queued or running fail with NMC_ESTATE) and frees all. */
 void nmc_server_destroy(nmc_server *srv);
-/* Queues an anneal of sweeps 0..n_steps-1 (arguments as nmc_load_ksat / nmc_set_schedule /
- * nmc_replicas_create with Philox initial states). *req_out receives the request id. */
+/* Queues an anneal of sweeps 0..n_steps-1 (arguments as nmc_load_ksat / nmc_set_schedule(_factored)
+ * / nmc_replicas_create with Philox initial states; all inputs are copied). *req_out receives
+ * the request id. */
 int nmc_server_submit_ksat(nmc_server *srv, int32_t n_vars, int32_t n_clauses, int32_t k_max,
-                           const int32_t *lits, int32_t n_steps, const float *beta,
-                           int32_t replicas, uint64_t seed, int64_t *req_out);
+                           const int32_t *lits, const nmc_schedule *sched, int32_t replicas,
+                           uint64_t seed, int64_t *req_out);
 int nmc_server_submit_qap(nmc_server *srv, int32_t n, const int32_t *F, const int32_t *D,
-                          int32_t n_steps, const float *beta, int32_t replicas, uint64_t seed,
+                          const nmc_schedule *sched, int32_t replicas, uint64_t seed,
                           int64_t *req_out);
 /* *status: 0 queued, 1 running, 2 done, or the negative error code of a failed request. Waits
  * up to wait_ms for completion (0: no wait). */

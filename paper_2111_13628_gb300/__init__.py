@@ -35,6 +35,11 @@ class NmcError(RuntimeError):
         self.code = code
 
 
+class Schedule(C.Structure):
+    _fields_ = [("n_steps", C.c_int32), ("beta", C.c_void_p), ("base", C.c_void_p),
+                ("factor", C.c_void_p)]
+
+
 class Result(C.Structure):
     _fields_ = [("states", C.c_void_p), ("energies", C.c_void_p),
                 ("best_energies", C.c_void_p), ("best_states", C.c_void_p)]
@@ -46,7 +51,7 @@ _lib = None
 # Exported C-ABI symbols (every function declared in include/nmc.h).
 SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_ksat",
            "nmc_load_qap", "nmc_unload", "nmc_ksat_colouring", "nmc_set_schedule",
-           "nmc_set_schedule_device", "nmc_replicas_create", "nmc_replicas_reset", "nmc_replicas_destroy",
+           "nmc_set_schedule_device", "nmc_set_schedule_factored", "nmc_replicas_create", "nmc_replicas_reset", "nmc_replicas_destroy",
            "nmc_replicas_run", "nmc_replicas_read", "nmc_replicas_read_device", "nmc_anneal",
            "nmc_threshold_table", "nmc_selftest_wait_timeout", "nmc_batch_run",
            "nmc_batch_max_vars", "nmc_server_create", "nmc_server_destroy",
@@ -82,6 +87,7 @@ def load(build_if_missing: bool = True):
             "nmc_ksat_colouring": ([P, i32, P, P], C.c_int),
             "nmc_set_schedule": ([P, i32, i32, P], C.c_int),
             "nmc_set_schedule_device": ([P, i32, i32, P], C.c_int),
+            "nmc_set_schedule_factored": ([P, i32, i32, P, P], C.c_int),
             "nmc_replicas_create": ([P, i32, i32, u64, P, P], C.c_int),
             "nmc_replicas_reset": ([P, i32, u64, P], C.c_int),
             "nmc_replicas_destroy": ([P, i32], C.c_int),
@@ -95,8 +101,8 @@ def load(build_if_missing: bool = True):
             "nmc_batch_max_vars": ([P], i32),
             "nmc_server_create": ([C.c_int, P, P], C.c_int),
             "nmc_server_destroy": ([P], None),
-            "nmc_server_submit_ksat": ([P, i32, i32, i32, P, i32, P, i32, u64, P], C.c_int),
-            "nmc_server_submit_qap": ([P, i32, P, P, i32, P, i32, u64, P], C.c_int),
+            "nmc_server_submit_ksat": ([P, i32, i32, i32, P, P, i32, u64, P], C.c_int),
+            "nmc_server_submit_qap": ([P, i32, P, P, P, i32, u64, P], C.c_int),
             "nmc_server_poll": ([P, C.c_int64, i32, P], C.c_int),
             "nmc_server_result": ([P, C.c_int64, P, P], C.c_int),
             "nmc_server_cancel": ([P, C.c_int64], C.c_int),
@@ -221,6 +227,15 @@ class Context:
             raise ValueError("beta must be [n_units, n_steps]")
         self._check(self._lib.nmc_set_schedule(self._h, int(inst), beta.shape[1], _ptr(beta)))
 
+    def set_schedule_factored(self, inst: int, base, factor):
+        """beta[u][t] = float32(base[t] * factor[u])."""
+        base = np.ascontiguousarray(base, dtype=np.float32)
+        factor = np.ascontiguousarray(factor, dtype=np.float32)
+        if factor.shape[0] != self._units[inst]:
+            raise ValueError("factor must have one entry per unit")
+        self._check(self._lib.nmc_set_schedule_factored(self._h, int(inst), base.shape[0],
+                                                        _ptr(base), _ptr(factor)))
+
     # -- replica sets
     def replicas_create(self, inst: int, replicas: int, seed: int, init=None) -> int:
         if init is not None:
@@ -339,23 +354,38 @@ class Server:
         self._meta[req.value] = meta
         return req.value
 
-    def submit_ksat(self, lits, n_vars, beta, replicas, seed) -> int:
+    @staticmethod
+    def _sched(beta=None, base=None, factor=None):
+        keep = []
+        if beta is not None:
+            beta = np.ascontiguousarray(beta, dtype=np.float32)
+            keep.append(beta)
+            return Schedule(beta.shape[1], _ptr(beta), None, None), keep
+        base = np.ascontiguousarray(base, dtype=np.float32)
+        factor = np.ascontiguousarray(factor, dtype=np.float32)
+        keep += [base, factor]
+        return Schedule(base.shape[0], None, _ptr(base), _ptr(factor)), keep
+
+    def submit_ksat(self, lits, n_vars, beta=None, replicas=32, seed=0, base=None,
+                    factor=None) -> int:
+        """Queues a k-SAT anneal; schedule as beta [n, T] or as base [T] x factor [n]."""
         lits = np.ascontiguousarray(lits, dtype=np.int32)
-        beta = np.ascontiguousarray(beta, dtype=np.float32)
+        sc, keep = self._sched(beta, base, factor)
         req = C.c_int64()
         rc = self._lib.nmc_server_submit_ksat(self._h, int(n_vars), lits.shape[0], lits.shape[1],
-                                              _ptr(lits), beta.shape[1], _ptr(beta), int(replicas),
+                                              _ptr(lits), C.byref(sc), int(replicas),
                                               int(seed) & (2**64 - 1), C.byref(req))
+        del keep
         return self._id(rc, req, (KIND_KSAT, int(n_vars), int(replicas)))
 
-    def submit_qap(self, F, D, beta, replicas, seed) -> int:
+    def submit_qap(self, F, D, beta=None, replicas=256, seed=0, base=None, factor=None) -> int:
         F = np.ascontiguousarray(F, dtype=np.int32)
         D = np.ascontiguousarray(D, dtype=np.int32)
-        beta = np.ascontiguousarray(beta, dtype=np.float32)
+        sc, keep = self._sched(beta, base, factor)
         req = C.c_int64()
-        rc = self._lib.nmc_server_submit_qap(self._h, F.shape[0], _ptr(F), _ptr(D), beta.shape[1],
-                                             _ptr(beta), int(replicas), int(seed) & (2**64 - 1),
-                                             C.byref(req))
+        rc = self._lib.nmc_server_submit_qap(self._h, F.shape[0], _ptr(F), _ptr(D), C.byref(sc),
+                                             int(replicas), int(seed) & (2**64 - 1), C.byref(req))
+        del keep
         return self._id(rc, req, (KIND_QAP, F.shape[0], int(replicas)))
 
     def poll(self, req: int, wait_ms: int = 0) -> int:

@@ -220,6 +220,9 @@ int init_replicas(nmc_ctx *ctx, const Instance &I, ReplicaSet &S, const void *in
 
 extern "C" {
 
+int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
+                  const int32_t *t1);
+
 int nmc_create(nmc_ctx **out, int device, void *cuda_stream) {
   if (!out) return NMC_EINVAL;
   *out = nullptr;
@@ -615,6 +618,46 @@ static int set_schedule_impl(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const 
   return NMC_OK;
 }
 
+int nmc_set_schedule_factored(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const float *base,
+                              const float *factor) {
+  if (!ctx) return NMC_EINVAL;
+  Instance *I = find_inst(ctx, inst);
+  if (!I) return fail(ctx, NMC_EINVAL, "unknown instance");
+  if (n_steps < 1 || !base || !factor) return fail(ctx, NMC_EINVAL, "need n_steps >= 1, base and factor");
+  DeviceGuard g(ctx->device);
+  const size_t count = static_cast<size_t>(I->n_units) * static_cast<size_t>(n_steps);
+  float *src = nullptr;
+  const size_t nb = sizeof(float) * (static_cast<size_t>(n_steps) + I->n_units);
+  NMC_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&src), nb, ctx->stream), "allocate schedule staging");
+  uint32_t *bq = nullptr;
+  int32_t bad = 0;
+  cudaError_t e = cudaMemcpyAsync(src, base, sizeof(float) * n_steps, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(src + n_steps, factor, sizeof(float) * I->n_units, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&bq, sizeof(uint32_t) * count);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->flag, 0, sizeof(int32_t), ctx->stream);
+  if (e == cudaSuccess)
+    e = quantize_schedule_factored(src, src + n_steps, I->n_units, n_steps,
+                                   I->kind == NMC_KIND_KSAT ? I->ks.orig : nullptr, bq, ctx->flag,
+                                   ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&bad, ctx->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(src, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    if (bq) cudaFree(bq);
+    return cuda_fail(ctx, e, "factored schedule");
+  }
+  if (bad) {
+    cudaFree(bq);
+    return fail(ctx, NMC_EINVAL, "beta must be finite and in [0, 65535]");
+  }
+  dev_free(I->bq);
+  I->bq = bq;
+  I->n_steps = n_steps;
+  return NMC_OK;
+}
+
 int nmc_set_schedule(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const float *beta) {
   return set_schedule_impl(ctx, inst, n_steps, beta, false);
 }
@@ -722,6 +765,15 @@ int nmc_replicas_run(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1) {
   if (t1 > t0 && (!I->bq || t1 > I->n_steps))
     return fail(ctx, NMC_ESTATE, "schedule missing or shorter than t1");
   if (t1 == t0) return NMC_OK;
+  if (I->kind == NMC_KIND_KSAT) {
+    // one set through the shared-memory kernel (clusters of CTAs per word) when it fits;
+    // the grid-barrier kernel otherwise (or when NMC_RUN_PATH=grid)
+    const char *path = getenv("NMC_RUN_PATH");
+    const bool force_grid = path && std::strcmp(path, "grid") == 0;
+    if (!force_grid && I->ks.nb <= 7 &&
+        static_cast<size_t>(I->ks.n) <= batch_max_vars(ctx->tab_len, ctx->device))
+      return nmc_batch_run(ctx, 1, &rs, &t0, &t1);
+  }
   DeviceGuard g(ctx->device);
   cudaError_t e;
   if (I->kind == NMC_KIND_KSAT)

@@ -7,6 +7,9 @@
 // for the 32 replicas of the word) and a CTA barrier between classes, and writes the state
 // back. Words are independent chains, so no grid-wide synchronisation is needed and uneven
 // instances fill the GPU. The dynamics are identical to the single-instance kernels.
+// Occurrence lists are read in a warp-interleaved layout (one coalesced load per occurrence
+// for 32 variables); each thread keeps its share of the sweep's energy change as 16
+// bit-sliced planes and converts them to per-replica sums once per sweep.
 #include <cooperative_groups.h>
 
 #include "nmc_internal.h"
@@ -18,7 +21,7 @@ namespace nmc {
 
 namespace {
 
-constexpr int kBatchThreads = 512;
+constexpr int kBatchThreads = 768;
 
 __device__ __forceinline__ uint32_t maj3b(uint32_t a, uint32_t b, uint32_t c) {
   return (a & b) | (a & c) | (b & c);
@@ -43,6 +46,29 @@ __device__ __forceinline__ void csa4(uint32_t (&c)[NB], uint32_t a0, uint32_t a1
   }
 }
 
+// Transposes the 8x8 bit matrix held as 8 bytes (byte j = row j) so that byte i holds
+// column i: with row j = bit plane j of 8 replicas, byte i becomes replica i's value.
+__device__ __forceinline__ unsigned long long transpose8(unsigned long long x) {
+  unsigned long long t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+  x = x ^ t ^ (t << 7);
+  t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+  x = x ^ t ^ (t << 14);
+  t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+  x = x ^ t ^ (t << 28);
+  return x;
+}
+
+// Gathers byte q of each of the 8 planes p[0..7] into one 64-bit word (byte j from plane j).
+__device__ __forceinline__ unsigned long long gather_bytes(const uint32_t *p, int q) {
+  const uint32_t sel = (uint32_t)q | ((uint32_t)(4 + q) << 4);
+  const uint32_t t01 = __byte_perm(p[0], p[1], sel), t23 = __byte_perm(p[2], p[3], sel);
+  const uint32_t t45 = __byte_perm(p[4], p[5], sel), t67 = __byte_perm(p[6], p[7], sel);
+  return (unsigned long long)__byte_perm(t01, t23, 0x5410) |
+         ((unsigned long long)__byte_perm(t45, t67, 0x5410) << 32);
+}
+
+constexpr int kAccPlanes = 16;  // per-thread energy accumulator: 16-bit two's complement
+
 // Truth value (32 replicas) of literal id l = 2u + neg from the word vector in shared memory.
 __device__ __forceinline__ uint32_t lit_word(const uint32_t *xs, int l) {
   return xs[l >> 1] ^ (0u - (uint32_t)(l & 1));
@@ -52,7 +78,8 @@ __device__ __forceinline__ uint32_t lit_word(const uint32_t *xs, int l) {
 template <int KQ>
 __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint32_t *xs,
                                                   const uint32_t *tab_s, int tab_len, int c,
-                                                  int c0, int v, int t, int (&acc)[32]) {
+                                                  int c0, int v, int t,
+                                                  uint32_t (&acc)[kAccPlanes]) {
   constexpr int NB = 7;
   const uint32_t x = xs[v];
   const uint32_t bqv = __ldg(B.bq + (size_t)t * B.n + v);
@@ -102,17 +129,7 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
   uint32_t flip = 0u;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const uint32_t sel = (uint32_t)q | ((uint32_t)(4 + q) << 4);
-    const uint32_t t01 = __byte_perm(s8[0], s8[1], sel), t23 = __byte_perm(s8[2], s8[3], sel);
-    const uint32_t t45 = __byte_perm(s8[4], s8[5], sel), t67 = __byte_perm(s8[6], s8[7], sel);
-    unsigned long long xm = (unsigned long long)__byte_perm(t01, t23, 0x5410) |
-                            ((unsigned long long)__byte_perm(t45, t67, 0x5410) << 32);
-    unsigned long long tt = (xm ^ (xm >> 7)) & 0x00AA00AA00AA00AAull;
-    xm = xm ^ tt ^ (tt << 7);
-    tt = (xm ^ (xm >> 14)) & 0x0000CCCC0000CCCCull;
-    xm = xm ^ tt ^ (tt << 14);
-    tt = (xm ^ (xm >> 28)) & 0x00000000F0F0F0F0ull;
-    xm = xm ^ tt ^ (tt << 28);
+    const unsigned long long xm = transpose8(gather_bytes(s8, q));
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int g = 2 * q + h;
@@ -133,13 +150,19 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
       if (need)
         u = philox4x32_10(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + g), kTagKsatSweep), B.k0, B.k1);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool ok = de[j] <= 0 || uint4_word(u, j) < th[j];
-        if (ok) {
-          flip |= 1u << (4 * g + j);
-          acc[4 * g + j] += de[j];
-        }
-      }
+      for (int j = 0; j < 4; ++j)
+        if (de[j] <= 0 || uint4_word(u, j) < th[j]) flip |= 1u << (4 * g + j);
+    }
+  }
+  // energy bookkeeping: acc += D on the flipped replicas (bit-sliced, sign-extended add)
+  {
+    uint32_t carry = 0u;
+#pragma unroll
+    for (int j = 0; j < kAccPlanes; ++j) {
+      const uint32_t b = s8[j < 8 ? j : 7] & flip;
+      const uint32_t a = acc[j];
+      acc[j] = a ^ b ^ carry;
+      carry = maj3b(a, b, carry);
     }
   }
   return x ^ flip;
@@ -154,6 +177,13 @@ __device__ __forceinline__ void group_sync() {
   } else {
     cg::this_cluster().sync();
   }
+}
+
+// Stores v at the same shared-memory word of CTA `rank` of the cluster (32-bit addressing).
+__device__ __forceinline__ void st_rank(uint32_t saddr, int rank, uint32_t v) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(saddr), "r"(rank));
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
 }
 
 template <int CS, typename T>
@@ -175,6 +205,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   __shared__ int e_s[32], be_s[32], ep_s[32];
   __shared__ uint32_t imp_s;
   __shared__ int item_s;
+  __shared__ BatchItem item_b;  // the current item, read from shared memory where needed
   const int rank = CS == 1 ? 0 : (int)cg::this_cluster().block_rank();
   for (int i = threadIdx.x; i < tab_len; i += blockDim.x) tab_s[i] = tab[i];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -182,9 +213,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     if (rank == 0 && threadIdx.x == 0) item_s = atomicAdd(next_item, 1);
     group_sync<CS>();
     const int it = *rank_ptr<CS>(&item_s, 0);
+    if (it < n_items && threadIdx.x == 0) item_b = items[it];
     group_sync<CS>();  // every rank has read the item id before any rank moves on or exits
     if (it >= n_items) break;
-    const BatchItem B = items[it];
+    const BatchItem &B = item_b;
     const int n = B.n, W = B.W, w = B.w;
     const int share = (n + CS - 1) / CS;
     for (int v = threadIdx.x; v < n; v += blockDim.x) xs[v] = B.S[(size_t)(2 * v) * W + w];
@@ -198,24 +230,38 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     }
     group_sync<CS>();
     for (int t = B.t0; t < B.t1; ++t) {
-      int acc[32];
+      uint32_t acc[kAccPlanes];
 #pragma unroll
-      for (int b = 0; b < 32; ++b) acc[b] = 0;
+      for (int j = 0; j < kAccPlanes; ++j) acc[j] = 0u;
       for (int c = 0; c < B.n_colours; ++c) {
         const int c0 = __ldg(B.col_ptr + c), c1 = __ldg(B.col_ptr + c + 1);
         const int part = ((c1 - c0 + CS - 1) / CS + 31) & ~31;  // whole 32-variable groups
         const int v0 = c0 + rank * part, v1 = min(c1, v0 + part);
         for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
           const uint32_t xn = attempt_batch<KQ>(B, xs, tab_s, tab_len, c, c0, v, t, acc);
+          if (CS == 1) {
+            xs[v] = xn;
+          } else {
+            const uint32_t sa = (uint32_t)__cvta_generic_to_shared(xs + v);
 #pragma unroll
-          for (int r = 0; r < CS; ++r) rank_ptr<CS>(xs, r)[v] = xn;
+            for (int r = 0; r < CS; ++r) st_rank(sa, r, xn);
+          }
         }
         group_sync<CS>();
       }
+      // per-replica sums of this sweep: planes -> 16-bit values (two byte transposes per block
+      // of 8 replicas), then a warp reduction per replica
 #pragma unroll
-      for (int b = 0; b < 32; ++b) {
-        const int s2 = __reduce_add_sync(0xFFFFFFFFu, acc[b]);
-        if (lane == 0 && s2 != 0) atomicAdd(&ep_s[b], s2);
+      for (int q = 0; q < 4; ++q) {
+        const unsigned long long lo = transpose8(gather_bytes(acc, q));
+        const unsigned long long hi = transpose8(gather_bytes(acc + 8, q));
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int val = (int)(short)(unsigned short)(((lo >> (8 * i)) & 0xFFull) |
+                                                       (((hi >> (8 * i)) & 0xFFull) << 8));
+          const int s2 = __reduce_add_sync(0xFFFFFFFFu, val);
+          if (lane == 0 && s2 != 0) atomicAdd(&ep_s[8 * q + i], s2);
+        }
       }
       group_sync<CS>();
       if (rank == 0 && warp == 0) {
@@ -313,8 +359,8 @@ size_t batch_max_vars(int tab_len, int device) {
   int optin = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
     return 0;
-  // dynamic shared memory: table + n+1 words; the static part is under 128 words
-  const long long words = (long long)optin / 4 - ((tab_len + 31) & ~31) - 1 - 128;
+  // dynamic shared memory: table + n+1 words; the static part is under 192 words
+  const long long words = (long long)optin / 4 - ((tab_len + 31) & ~31) - 1 - 192;
   return words > 0 ? (size_t)words : 0;
 }
 

@@ -699,6 +699,26 @@ __global__ void quantize_kernel(const float *beta, int32_t n_units, int32_t n_st
   }
 }
 
+// beta[u][t] = base[t] * factor[u] (float32, round to nearest) -> bq[t][new(u)], validated.
+__global__ void quantize_factored_kernel(const float *base, const float *factor, int32_t n_units,
+                                         int32_t n_steps, const int32_t *orig, uint32_t *bq,
+                                         int32_t *bad) {
+  const long long total = (long long)n_units * n_steps;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(i / n_units), v = (int)(i % n_units);
+    const int u = orig ? orig[v] : v;
+    const float b = __fmul_rn(base[t], factor[u]);
+    uint32_t q = 0u;
+    if (!(b >= 0.0f && b <= 65535.0f)) {
+      atomicExch(bad, 1);
+    } else {
+      q = __float2uint_rn(b * 65536.0f);
+    }
+    bq[i] = q;
+  }
+}
+
 template <int NB, int KQ>
 cudaError_t launch_sweeps(const SweepArgs &a, int device, cudaStream_t st) {
   const size_t smem = sizeof(uint32_t) * (((a.tab_len + 31) & ~31) + (size_t)a.W * 33);
@@ -848,6 +868,15 @@ cudaError_t wait_selftest(GridBarrier *gb, unsigned long long limit_ns, cudaStre
   cudaError_t err = cudaMemsetAsync(reinterpret_cast<char *>(gb) + kBarrierResetOffset, 0, kBarrierResetBytes, st);
   if (err != cudaSuccess) return err;
   wait_selftest_kernel<<<1, 32, 0, st>>>(gb, 2u, limit_ns);
+  return cudaGetLastError();
+}
+
+cudaError_t quantize_schedule_factored(const float *base, const float *factor, int32_t n_units,
+                                       int32_t n_steps, const int32_t *orig, uint32_t *bq,
+                                       int32_t *bad, cudaStream_t st) {
+  const long long work = (long long)n_units * n_steps;
+  quantize_factored_kernel<<<grid_for(work, 256), 256, 0, st>>>(base, factor, n_units, n_steps,
+                                                                  orig, bq, bad);
   return cudaGetLastError();
 }
 

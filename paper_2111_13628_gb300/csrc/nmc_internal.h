@@ -100,6 +100,9 @@ cudaError_t ksat_unpack(const KsatDevice &I, const KsatReplicas &Rp, uint8_t *st
 // general kernel).
 void set_sweep_shape(int warps_per_variable);
 cudaError_t wait_selftest(GridBarrier *gb, unsigned long long limit_ns, cudaStream_t st);
+cudaError_t quantize_schedule_factored(const float *base, const float *factor, int32_t n_units,
+                                       int32_t n_steps, const int32_t *orig, uint32_t *bq,
+                                       int32_t *bad, cudaStream_t st);
 cudaError_t quantize_schedule(const float *beta, int32_t n_units, int32_t n_steps,
                               const int32_t *orig, uint32_t *bq, int32_t *bad,
                               cudaStream_t st);

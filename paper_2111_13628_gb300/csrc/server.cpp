@@ -37,7 +37,7 @@ struct Request {
   int32_t n = 0, m = 0, kmax = 0, n_steps = 0, replicas = 0;
   uint64_t seed = 0;
   std::vector<int32_t> lits, F, D;
-  std::vector<float> beta;
+  std::vector<float> beta, base, factor;  // full profile, or the factored form
   // device residency
   int32_t inst = -1, rs = -1;
   int32_t t = 0;
@@ -102,6 +102,8 @@ void finish(nmc_server *s, const std::shared_ptr<Request> &r, int status, const 
   r->lits.shrink_to_fit();
   r->beta.clear();
   r->beta.shrink_to_fit();
+  r->base.clear();
+  r->factor.clear();
   s->cv_done.notify_all();
 }
 
@@ -112,7 +114,9 @@ bool admit(nmc_server *s, const std::shared_ptr<Request> &r) {
     rc = nmc_load_ksat(c, r->n, r->m, r->kmax, r->lits.data(), &r->inst);
   else
     rc = nmc_load_qap(c, r->n, r->F.data(), r->D.data(), &r->inst);
-  if (rc == NMC_OK) rc = nmc_set_schedule(c, r->inst, r->n_steps, r->beta.data());
+  if (rc == NMC_OK)
+    rc = r->beta.empty() ? nmc_set_schedule_factored(c, r->inst, r->n_steps, r->base.data(), r->factor.data())
+                         : nmc_set_schedule(c, r->inst, r->n_steps, r->beta.data());
   if (rc == NMC_OK) rc = nmc_replicas_create(c, r->inst, r->replicas, r->seed, nullptr, &r->rs);
   if (rc != NMC_OK) {
     finish(s, r, rc, nmc_last_error(c));
@@ -243,6 +247,20 @@ int submit(nmc_server *s, std::shared_ptr<Request> r, int64_t *id_out) {
   return NMC_OK;
 }
 
+// Copies a schedule given in either form; false if it is malformed.
+bool copy_schedule(Request &r, const nmc_schedule *sc, int32_t n_units) {
+  if (!sc || sc->n_steps < 1) return false;
+  r.n_steps = sc->n_steps;
+  if (sc->beta) {
+    r.beta.assign(sc->beta, sc->beta + static_cast<size_t>(n_units) * sc->n_steps);
+    return true;
+  }
+  if (!sc->base || !sc->factor) return false;
+  r.base.assign(sc->base, sc->base + sc->n_steps);
+  r.factor.assign(sc->factor, sc->factor + n_units);
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -266,21 +284,20 @@ int nmc_server_create(int device, const nmc_server_config *cfg, nmc_server **out
 }
 
 int nmc_server_submit_ksat(nmc_server *s, int32_t n_vars, int32_t n_clauses, int32_t k_max,
-                           const int32_t *lits, int32_t n_steps, const float *beta,
-                           int32_t replicas, uint64_t seed, int64_t *req_out) {
-  if (!s || !req_out || n_vars < 1 || n_clauses < 0 || k_max < 1 || k_max > 8 || n_steps < 1 ||
-      !beta || (n_clauses > 0 && !lits) || replicas < 1 || replicas > 4096)
+                           const int32_t *lits, const nmc_schedule *sched, int32_t replicas,
+                           uint64_t seed, int64_t *req_out) {
+  if (!s || !req_out || n_vars < 1 || n_clauses < 0 || k_max < 1 || k_max > 8 ||
+      (n_clauses > 0 && !lits) || replicas < 1 || replicas > 4096)
     return NMC_EINVAL;
   auto r = std::make_shared<Request>();
   r->kind = NMC_KIND_KSAT;
   r->n = n_vars;
   r->m = n_clauses;
   r->kmax = k_max;
-  r->n_steps = n_steps;
   r->replicas = replicas;
   r->seed = seed;
+  if (!copy_schedule(*r, sched, n_vars)) return NMC_EINVAL;
   r->lits.assign(lits, lits + static_cast<size_t>(n_clauses) * k_max);
-  r->beta.assign(beta, beta + static_cast<size_t>(n_vars) * n_steps);
   std::vector<int32_t> deg(static_cast<size_t>(n_vars) + 1, 0);
   int32_t dmax = 0;
   for (int32_t l : r->lits) {
@@ -292,19 +309,17 @@ int nmc_server_submit_ksat(nmc_server *s, int32_t n_vars, int32_t n_clauses, int
 }
 
 int nmc_server_submit_qap(nmc_server *s, int32_t n, const int32_t *F, const int32_t *D,
-                          int32_t n_steps, const float *beta, int32_t replicas, uint64_t seed,
+                          const nmc_schedule *sched, int32_t replicas, uint64_t seed,
                           int64_t *req_out) {
-  if (!s || !req_out || n < 1 || !F || !D || n_steps < 1 || !beta || replicas < 1 || replicas > 4096)
-    return NMC_EINVAL;
+  if (!s || !req_out || n < 1 || !F || !D || replicas < 1 || replicas > 4096) return NMC_EINVAL;
   auto r = std::make_shared<Request>();
   r->kind = NMC_KIND_QAP;
   r->n = n;
-  r->n_steps = n_steps;
   r->replicas = replicas;
   r->seed = seed;
+  if (!copy_schedule(*r, sched, n)) return NMC_EINVAL;
   r->F.assign(F, F + static_cast<size_t>(n) * n);
   r->D.assign(D, D + static_cast<size_t>(n) * n);
-  r->beta.assign(beta, beta + static_cast<size_t>(n) * n_steps);
   return submit(s, r, req_out);
 }
 

@@ -56,6 +56,14 @@ def test_small_workload_full_parity(ctx):
     _same(got, want)
 
 
+@pytest.fixture(params=["auto", "grid"])
+def run_path(request, monkeypatch):
+    """Runs a test through the default kernel choice and through the grid-barrier kernel."""
+    if request.param == "grid":
+        monkeypatch.setenv("NMC_RUN_PATH", "grid")
+    return request.param
+
+
 @pytest.mark.parametrize("n,alpha,k,R,T", [
     (1, 0.0, 1, 5, 7),          # one variable, no clauses
     (2, 1.0, 2, 1, 9),          # single replica
@@ -65,7 +73,7 @@ def test_small_workload_full_parity(ctx):
     (120, 2.0, 6, 40, 15),      # k > 4: two int4 per occurrence
     (90, 1.2, 8, 64, 10),       # k = 8
 ])
-def test_parity_shapes(ctx, n, alpha, k, R, T):
+def test_parity_shapes(ctx, run_path, n, alpha, k, R, T):
     lits = W.random_ksat(n, alpha, k, 100 + n) if alpha > 0 else np.zeros((0, k), np.int32)
     beta = W.beta_inhomogeneous_linear(n, T, 0.2, 3.0, 0.3, 0.5, 200 + n)
     got = _run(ctx, lits, n, beta, R, 0, T, seed=5 + n)
@@ -73,7 +81,7 @@ def test_parity_shapes(ctx, n, alpha, k, R, T):
     _same(got, want)
 
 
-def test_padded_clauses_and_high_degree(ctx):
+def test_padded_clauses_and_high_degree(ctx, run_path):
     rng = np.random.default_rng(4)
     n, m, kmax = 60, 900, 5
     rows = np.zeros((m, kmax), np.int32)
@@ -91,7 +99,7 @@ def test_padded_clauses_and_high_degree(ctx):
     _same(got, want)
 
 
-def test_segments_resident_state_and_given_init(ctx):
+def test_segments_resident_state_and_given_init(ctx, run_path):
     wl = W.workload_ksat_small(80)
     lits, n, beta = wl["lits"], wl["n_vars"], wl["beta"]
     inst = ctx.load_ksat(lits, n)
@@ -110,7 +118,7 @@ def test_segments_resident_state_and_given_init(ctx):
     ctx.unload(inst)
 
 
-def test_beta_zero_and_infinite(ctx):
+def test_beta_zero_and_infinite(ctx, run_path):
     n = 300
     lits = W.random_ksat(n, 9.6, 4, 77)
     for val in (0.0, 65535.0):
@@ -183,7 +191,7 @@ def test_bounded_wait_expires_and_context_survives(ctx):
     _same(got, want)
 
 
-def test_full_size_sampled_replicas(ctx):
+def test_full_size_sampled_replicas(ctx, run_path):
     """The N=50,000 / 1024-replica workload in the bench's launch configuration: every replica
     is checked for energy consistency, and sampled replicas bit for bit (short schedule)."""
     T = 40
@@ -212,11 +220,26 @@ def test_full_size_sampled_replicas(ctx):
     (2000, 4.2, 3, 1024, 8),    # low degree: 5-bit counters
 ])
 def test_sweep_shapes_agree(ctx, monkeypatch, warps, n, alpha, k, R, T):
-    """Every kernel shape (general kernel, teams of 1, 2 or 4 warps per variable) gives the
-    oracle's trajectories."""
+    """Every grid-kernel shape (general kernel, teams of 1, 2 or 4 warps per variable) gives
+    the oracle's trajectories."""
+    monkeypatch.setenv("NMC_RUN_PATH", "grid")
     monkeypatch.setenv("NMC_SWEEP_WARPS", str(warps))
     lits = W.random_ksat(n, alpha, k, 700 + n)
     beta = W.beta_inhomogeneous_linear(n, T, 0.3, 4.0, 0.3, 0.5, 800 + n)
     got = _run(ctx, lits, n, beta, R, 0, T, seed=n)
     want = O.ksat_anneal(lits, n, beta, 0, T, n, replicas=R)
     _same(got, want)
+
+
+def test_factored_schedule_equals_expanded(ctx):
+    """beta[u][t] = float32(base[t] * factor[u]) on the device equals the expanded array."""
+    n, T, R = 500, 30, 64
+    lits = W.random_ksat(n, 9.6, 4, 31)
+    base = W.geometric_profile(0.3, 6.0, T).astype(np.float32)
+    factor = np.where(W.seeded_subset(n, 0.2, 32), 0.4, 1.0).astype(np.float32)
+    beta = (factor[:, None] * base[None, :]).astype(np.float32)  # IEEE float32 products
+    inst = ctx.load_ksat(lits, n)
+    ctx.set_schedule_factored(inst, base, factor)
+    got = ctx.anneal(inst, R, 0, T, seed=33)
+    ctx.unload(inst)
+    _same(got, O.ksat_anneal(lits, n, beta, 0, T, 33, replicas=R))

@@ -46,9 +46,11 @@ def test_mixed_requests_match_alone():
             time.sleep(0.002 * i)  # staggered arrivals while earlier requests run
             kind, r = reqs[i]
             if kind == "ksat":
-                ids[i] = srv.submit_ksat(r["lits"], r["n_vars"], r["beta"], r["replicas"], r["seed"])
+                ids[i] = srv.submit_ksat(r["lits"], r["n_vars"], beta=r["beta"],
+                                         replicas=r["replicas"], seed=r["seed"])
             else:
-                ids[i] = srv.submit_qap(r["F"], r["D"], r["beta"], r["replicas"], r["seed"])
+                ids[i] = srv.submit_qap(r["F"], r["D"], beta=r["beta"], replicas=r["replicas"],
+                                        seed=r["seed"])
         th = [threading.Thread(target=submit, args=(i,)) for i in range(len(reqs))]
         for t in th:
             t.start()
@@ -57,7 +59,7 @@ def test_mixed_requests_match_alone():
         outs = []
         for i in ids:
             deadline = time.time() + 120
-            while srv.poll(i, wait_ms=200) not in (2,) and time.time() < deadline:
+            while srv.poll(i, wait_ms=200) in (0, 1) and time.time() < deadline:
                 pass
             outs.append(srv.result(i))
         st = srv.stats()
@@ -69,16 +71,40 @@ def test_mixed_requests_match_alone():
             assert np.array_equal(got[key], want[key]), (kind, key)
 
 
+def test_factored_requests_match_alone():
+    import paper_2111_13628_gb300 as nmc
+    n, T = 3000, 50
+    lits = W.random_ksat(n, 9.6, 4, 41)
+    base = W.linear_profile(0.5, 4.0, T).astype(np.float32)
+    factor = np.where(W.seeded_subset(n, 0.3, 42), 0.5, 1.0).astype(np.float32)
+    with nmc.Server(0, max_active=8, slice_log2=13) as srv:
+        ids = [srv.submit_ksat(lits, n, base=base, factor=factor, replicas=32, seed=s)
+               for s in range(3)]
+        outs = []
+        for i in ids:
+            deadline = time.time() + 120
+            while srv.poll(i, wait_ms=200) in (0, 1) and time.time() < deadline:
+                pass
+            outs.append(srv.result(i)[0])
+    beta = (factor[:, None] * base[None, :]).astype(np.float32)
+    for s, got in enumerate(outs):
+        want = _alone("ksat", dict(lits=lits, n_vars=n, beta=beta, replicas=32, seed=s))
+        for key in KEYS:
+            assert np.array_equal(got[key], want[key]), key
+
+
 def test_admission_limits_cancel_and_errors():
     import paper_2111_13628_gb300 as nmc
     lits = W.random_ksat(400, 9.6, 4, 1)
     beta = W.beta_constant(400, 3000, 2.0)
     with nmc.Server(0, max_active=1, memory_budget=64 << 20, slice_log2=12) as srv:
         big = srv.submit_ksat(W.random_ksat(20000, 9.6, 4, 2), 20000,
-                              W.beta_constant(20000, 400, 1.0), 1024, 1)   # > 64 MB budget
-        a = srv.submit_ksat(lits, 400, beta, 32, 1)
-        b = srv.submit_ksat(lits, 400, beta, 32, 2)                      # waits for the slot
-        bad = srv.submit_ksat(np.array([[1, -1, 2]], np.int32), 5, W.beta_constant(5, 2, 1.0), 32, 3)
+                              base=np.ones(400, np.float32), factor=np.ones(20000, np.float32),
+                              replicas=1024, seed=1)                     # > 64 MB budget
+        a = srv.submit_ksat(lits, 400, beta=beta, replicas=32, seed=1)
+        b = srv.submit_ksat(lits, 400, beta=beta, replicas=32, seed=2)   # waits for the slot
+        bad = srv.submit_ksat(np.array([[1, -1, 2]], np.int32), 5, beta=W.beta_constant(5, 2, 1.0),
+                              replicas=32, seed=3)
         assert srv.poll(big, wait_ms=30000) == nmc.NMC_ENOMEM
         with pytest.raises(nmc.NmcError):
             srv.result(big)
