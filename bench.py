@@ -260,7 +260,8 @@ def run_ours(args, world, rank, local):
                    "l2": "flushed between steps (512 MB write); beta schedule 1 GB > L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "ksat_sweep_kernel (one persistent launch per step)",
+                     "kernel": ("ksat_batch_kernel (clusters of CTAs per replica word)"
+                                if args.path != "grid" else "ksat_sweep_fast_kernel (grid barrier)"),
                      "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "launch_ms_mean": statistics.mean(sweep_ms)},
@@ -314,6 +315,238 @@ def run_reference(args, world, rank):
                     "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------------------------------------
+# Secondary workloads (one JSON line each; the default line above is the headline)
+# ---------------------------------------------------------------------------------------------
+
+def _ctx_stream():
+    import torch
+
+    import paper_2111_13628_gb300 as nmc
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    return nmc.Context(0, stream=stream), stream
+
+
+def run_ksat_small(args):
+    """4-SAT N=200, M=1920, 64 replicas, 1000 sweeps: one step = one whole anneal."""
+    import torch
+    ctx, stream = _ctx_stream()
+    wl = W.workload_ksat_small(1000)
+    lits, n, beta, R, T = wl["lits"], wl["n_vars"], wl["beta"], wl["replicas"], wl["n_steps"]
+    inst = ctx.load_ksat(lits, n)
+    ctx.set_schedule(inst, beta)
+    rs = ctx.replicas_create(inst, R, seed=wl["seed"])
+    steps = max(args.steps, 10)
+    for i in range(args.warmup):
+        ctx.replicas_reset(rs, i)
+        ctx.replicas_run(rs, 0, T)
+    ctx.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i in range(steps):
+        ctx.replicas_reset(rs, 100 + i)
+        ctx.replicas_run(rs, 0, T)
+    b.record(stream)
+    ctx.sync()
+    ms = a.elapsed_time(b) / steps
+    ctx.close()
+    return {"metric": "Metropolis attempts/s", "value": n * R * T / (ms / 1e3), "unit": UNIT,
+            "config": {"workload": wl["name"] + "_t1000"}, "ms_per_step": ms, "steps": steps,
+            "note": "launch- and latency-bound size (one CTA per replica word)"}
+
+
+def run_ksat_batch(args):
+    """Uneven batch: 256 instances (3-SAT alpha 4.2 / 4-SAT alpha 9.6), N in [1000, 20000],
+    32..256 replicas, 2000 sweeps, one batched launch per step; schedules in factored form."""
+    import torch
+    ctx, stream = _ctx_stream()
+    n_inst, T = args.batch_instances, 2000
+    s = W.Stream(1003)
+    kind = s.below(2, n_inst)
+    ns = 1000 + s.below(19001, n_inst)
+    rs_n = 32 + s.below(225, n_inst)
+    sets, attempts, per = [], 0, []
+    base = W.linear_profile(0.5, 4.0, T).astype(np.float32)
+    for i in range(n_inst):
+        k, alpha = (3, 4.2) if kind[i] == 0 else (4, 9.6)
+        n = int(ns[i])
+        lits = W.random_ksat(n, alpha, k, 1003 * 1000 + i)
+        factor = np.where(W.seeded_subset(n, 0.3, 1003 * 2000 + i), 0.5, 1.0).astype(np.float32)
+        inst = ctx.load_ksat(lits, n)
+        ctx.set_schedule_factored(inst, base, factor)
+        R = int(rs_n[i])
+        rs = ctx.replicas_create(inst, R, seed=10_000 + i)
+        sets.append(rs)
+        attempts += n * R * T
+        per.append((rs, n * R * T))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(args.warmup + args.steps):
+        for j, rs in enumerate(sets):
+            ctx.replicas_reset(rs, 10_000 + j + 1000 * i)
+        if i == args.warmup:
+            ctx.sync()
+            a.record(stream)
+        ctx.batch_run(sets, 0, T)
+    b.record(stream)
+    ctx.sync()
+    ms = a.elapsed_time(b) / args.steps
+    # plain per-instance form on a sample of the sets: one nmc_replicas_run per set, in turn
+    sample = per[:: max(1, len(per) // 16)]
+    c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c.record(stream)
+    for rs, _ in sample:
+        ctx.replicas_run(rs, 0, T)
+    d.record(stream)
+    ctx.sync()
+    plain = sum(x for _, x in sample) / (c.elapsed_time(d) / 1e3)
+    ctx.close()
+    return {"metric": "Metropolis attempts/s (batched, one launch)", "value": attempts / (ms / 1e3),
+            "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
+            "config": {"workload": f"ksat_batch_{n_inst}x_N1k-20k_R32-256_t{T}",
+                       "attempts_per_step": attempts},
+            "plain_per_instance": {"value": plain, "unit": UNIT,
+                                   "sample": f"{len(sample)} of the {n_inst} sets, one launch each"}}
+
+
+def run_qap_batch(args):
+    """64 QAP instances, n in [32, 256], 4096 replicas each; a sample of the 10^4 steps."""
+    import torch
+    ctx, stream = _ctx_stream()
+    steps_s = args.qap_steps
+    s = W.Stream(1004)
+    ns = 32 + s.below(225, 64)
+    sets, attempts = [], 0
+    for i in range(64):
+        n = int(ns[i])
+        F, D = W.random_qap(n, 1004 * 1000 + i)
+        beta = W.beta_scaled_linear(n, steps_s, 0.01, 1.0, 0.5, 1.5, 1004 * 2000 + i)
+        inst = ctx.load_qap(F, D)
+        ctx.set_schedule(inst, beta)
+        sets.append(ctx.replicas_create(inst, 4096, seed=20_000 + i))
+        attempts += n * 4096 * steps_s
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            ctx.sync()
+            a.record(stream)
+        for rs in sets:
+            ctx.replicas_run(rs, 0, steps_s)
+    b.record(stream)
+    ctx.sync()
+    ms = a.elapsed_time(b) / args.steps
+    ctx.close()
+    return {"metric": "swap attempts/s", "value": attempts / (ms / 1e3), "unit": "swap attempts/s",
+            "ms_per_step": ms, "steps": args.steps,
+            "config": {"workload": f"qap_64x_n32-256_R4096_sample{steps_s}of10000steps",
+                       "attempts_per_step": attempts}}
+
+
+def run_serving(args):
+    """Poisson arrivals of random 4-SAT (N log-uniform [500, 50000], alpha U[9.0, 9.8], 32
+    replicas) and QAP (n U[32, 192], 256 replicas) requests of 1000..5000 sweeps, each with its
+    own factored beta profile; instances drawn from a pre-generated pool."""
+    import threading
+
+    import paper_2111_13628_gb300 as nmc
+    rate, dur = args.rate, args.duration
+    s = W.Stream(1005)
+    pool_k, pool_q = [], []
+    for i in range(args.pool):
+        n = int(round(float(np.exp(np.log(500) + (np.log(50000) - np.log(500)) * s.unit(1)[0]))))
+        alpha = 9.0 + 0.8 * s.unit(1)[0]
+        pool_k.append((W.random_ksat(n, alpha, 4, 1005 * 1000 + i), n))
+    for i in range(max(2, args.pool // 4)):
+        n = 32 + int(s.below(161, 1)[0])
+        F, D = W.random_qap(n, 1005 * 3000 + i)
+        pool_q.append((F, D, n))
+    t_arr = np.cumsum(-np.log(1.0 - s.unit(int(rate * dur * 1.5) + 10)) / rate)
+    t_arr = t_arr[t_arr < dur]
+    nreq = len(t_arr)
+    is_q = s.below(2, nreq)
+    which = s.below(1 << 30, nreq)
+    sweeps = 1000 + s.below(4001, nreq)
+    reqs = []
+    for i in range(nreq):
+        T = int(sweeps[i])
+        base = W.linear_profile(0.5, 4.0, T).astype(np.float32)
+        if is_q[i]:
+            F, D, n = pool_q[int(which[i]) % len(pool_q)]
+            factor = (0.5 + W.Stream(7000 + i).unit(n)).astype(np.float32)
+            reqs.append(("qap", (F, D, n), base * 0.25, factor, 256, T))
+        else:
+            lits, n = pool_k[int(which[i]) % len(pool_k)]
+            factor = np.where(W.seeded_subset(n, 0.3, 8000 + i), 0.5, 1.0).astype(np.float32)
+            reqs.append(("ksat", (lits, n), base, factor, 32, T))
+    work = sum(r[1][-1] * r[4] * r[5] for r in reqs)
+    srv = nmc.Server(0, max_active=args.max_active, slice_log2=args.slice_log2)
+    ids = [None] * nreq
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            wait = t0 + t_arr[i] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            kind, inst, base, factor, R, T = r
+            if kind == "ksat":
+                ids[i] = srv.submit_ksat(inst[0], inst[1], base=base, factor=factor, replicas=R,
+                                         seed=i)
+            else:
+                ids[i] = srv.submit_qap(inst[0], inst[1], base=base, factor=factor, replicas=R,
+                                        seed=i)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    print(f"serving: {nreq} requests submitted in {time.perf_counter() - t0:.1f} s; "
+          f"stats {srv.stats()}", file=sys.stderr, flush=True)
+    lat, failed = [], 0
+    for i in ids:
+        while srv.poll(i, wait_ms=500) in (0, 1):
+            pass
+        try:
+            _, l = srv.result(i)
+            lat.append(l)
+        except nmc.NmcError:
+            failed += 1
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    print(f"serving: all done after {wall:.1f} s; stats {st}", file=sys.stderr, flush=True)
+    srv.close()
+    lat = np.array(lat)
+    # plain single-instance path: measured service times of a sample through nmc_anneal,
+    # then a FIFO queue over the same arrival times
+    ctx = nmc.Context(0)
+    samp = list(range(0, nreq, max(1, nreq // args.plain_sample)))
+    svc = {}
+    for i in samp:
+        kind, inst, base, factor, R, T = reqs[i]
+        tt = time.perf_counter()
+        h = ctx.load_ksat(inst[0], inst[1]) if kind == "ksat" else ctx.load_qap(inst[0], inst[1])
+        ctx.set_schedule_factored(h, base, factor)
+        ctx.anneal(h, R, 0, T, seed=i)
+        ctx.unload(h)
+        svc[i] = time.perf_counter() - tt
+    ctx.close()
+    rate_plain = sum(reqs[i][1][-1] * reqs[i][4] * reqs[i][5] for i in samp) / sum(svc.values())
+    busy, plat = 0.0, []
+    for i in samp:  # FIFO on the sampled requests with service time scaled to the full stream
+        start = max(busy, t_arr[i])
+        busy = start + svc[i] * (nreq / len(samp))
+        plat.append(busy - t_arr[i])
+    return {"metric": "serving latency and throughput", "unit": "s",
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "requests": nreq, "failed": failed, "offered_attempts_per_s": work / dur,
+            "achieved_attempts_per_s": work / wall, "wall_s": wall,
+            "server": st,
+            "config": {"workload": f"serving_poisson{rate}rps_{dur}s", "pool": args.pool,
+                       "max_active": args.max_active, "slice_log2": args.slice_log2},
+            "plain_fifo": {"attempts_per_s": rate_plain, "p50_s": float(np.percentile(plat, 50)),
+                           "p99_s": float(np.percentile(plat, 99)),
+                           "sample": f"{len(samp)} requests through nmc_anneal alone"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,6 +560,16 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=8)
     ap.add_argument("--cpu-replicas", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--workload", default="ksat_large",
+                    choices=["ksat_large", "ksat_small", "ksat_batch", "qap_batch", "serving"])
+    ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--qap-steps", type=int, default=50)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--duration", type=float, default=20.0)
+    ap.add_argument("--pool", type=int, default=32)
+    ap.add_argument("--max-active", type=int, default=512)
+    ap.add_argument("--slice-log2", type=int, default=22)
+    ap.add_argument("--plain-sample", type=int, default=24)
     ap.add_argument("--path", default="run", choices=["run", "batch", "grid"],
                     help="run: nmc_replicas_run (the library picks the kernel); batch: "
                          "nmc_batch_run; grid: nmc_replicas_run on the grid-barrier kernel")
@@ -336,6 +579,10 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         res = run_reference(args, world, rank)
+    elif args.workload != "ksat_large":
+        fn = {"ksat_small": run_ksat_small, "ksat_batch": run_ksat_batch,
+              "qap_batch": run_qap_batch, "serving": run_serving}[args.workload]
+        res = fn(args) if rank == 0 else None
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

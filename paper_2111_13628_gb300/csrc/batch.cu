@@ -12,6 +12,9 @@
 // bit-sliced planes and converts them to per-replica sums once per sweep.
 #include <cooperative_groups.h>
 
+#include <map>
+#include <mutex>
+
 #include "nmc_internal.h"
 #include "philox.cuh"
 
@@ -301,17 +304,59 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   }
 }
 
+// The launch shape of each kernel instance is queried once per (device, shared-memory size):
+// occupancy and cluster queries are slow host calls.
 template <int KQ, int CS>
 cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
                          const uint32_t *tab, int tab_len, int max_n, int device,
                          cudaStream_t st) {
   const size_t smem = sizeof(uint32_t) * (((tab_len + 31) & ~31) + (size_t)max_n + 1);
   auto kern = ksat_batch_kernel<KQ, CS>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  int sms = 0;
-  err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  if (err != cudaSuccess) return err;
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, int> shapes;  // (device, smem) -> resident clusters
+  static std::map<int, size_t> smem_set;                // device -> largest smem attribute set
+  int clusters = 0;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    cudaError_t err;
+    size_t &cur = smem_set[device];
+    if (smem > cur) {
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+      cur = smem;
+    }
+    auto it = shapes.find({device, smem});
+    if (it != shapes.end()) {
+      clusters = it->second;
+    } else {
+      int sms = 0;
+      err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+      if (err != cudaSuccess) return err;
+      if (CS == 1) {
+        int per_sm = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem);
+        if (err != cudaSuccess) return err;
+        clusters = sms * per_sm;
+      } else {
+        cudaLaunchConfig_t q = {};
+        q.blockDim = dim3(kBatchThreads);
+        q.dynamicSmemBytes = smem;
+        q.gridDim = dim3(CS * sms);
+        cudaLaunchAttribute qa[1];
+        qa[0].id = cudaLaunchAttributeClusterDimension;
+        qa[0].val.clusterDim.x = CS;
+        qa[0].val.clusterDim.y = 1;
+        qa[0].val.clusterDim.z = 1;
+        q.attrs = qa;
+        q.numAttrs = 1;
+        err = cudaOccupancyMaxActiveClusters(&clusters, kern, &q);
+        if (err != cudaSuccess) return err;
+      }
+      shapes[{device, smem}] = clusters;
+    }
+  }
+  if (clusters < 1) return cudaErrorInvalidConfiguration;
+  if (clusters > n_items) clusters = n_items;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kBatchThreads);
   cfg.dynamicSmemBytes = smem;
@@ -323,21 +368,8 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  int clusters = 0;
-  if (CS == 1) {
-    int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem);
-    if (err != cudaSuccess) return err;
-    clusters = sms * per_sm;
-  } else {
-    cfg.gridDim = dim3(CS * sms);
-    err = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
-    if (err != cudaSuccess) return err;
-  }
-  if (clusters < 1) return cudaErrorInvalidConfiguration;
-  if (clusters > n_items) clusters = n_items;
   cfg.gridDim = dim3(clusters * CS);
-  err = cudaMemsetAsync(next_item, 0, sizeof(int), st);
+  cudaError_t err = cudaMemsetAsync(next_item, 0, sizeof(int), st);
   if (err != cudaSuccess) return err;
   return cudaLaunchKernelEx(&cfg, kern, items, n_items, next_item, tab, tab_len);
 }
@@ -354,6 +386,7 @@ cudaError_t dispatch_batch(int cs, const BatchItem *items, int n_items, int *nex
 }
 
 }  // namespace
+
 
 size_t batch_max_vars(int tab_len, int device) {
   int optin = 0;

@@ -20,6 +20,8 @@
 // CTA returns.
 #include <cooperative_groups.h>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 
 #include "nmc_internal.h"
 #include "philox.cuh"
@@ -748,20 +750,35 @@ cudaError_t launch_fast(const SweepArgs &a, int device, cudaStream_t st) {
   const int nwarps = threads / 32;
   const size_t smem = fast_smem_bytes<NB, KQ, P>(a.tab_len, a.W, nwarps);
   auto kern = ksat_sweep_fast_kernel<NB, KQ, P, THREADS>;
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, int> grids;  // (device, smem) -> co-resident CTAs
+  int blocks = 0;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = grids.find({device, smem});
+    if (it != grids.end()) {
+      blocks = it->second;
+    } else {
+      cudaError_t err =
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+      int per_sm = 0;
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+      if (err != cudaSuccess) return err;
+      int sms = 0;
+      err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+      if (err != cudaSuccess) return err;
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      while (per_sm > 1 && sms * per_sm > kMaxGridCtas) --per_sm;
+      if (sms * per_sm > kMaxGridCtas) return cudaErrorInvalidConfiguration;
+      blocks = sms * per_sm;
+      grids[{device, smem}] = blocks;
+    }
+  }
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-  if (err != cudaSuccess) return err;
-  int sms = 0;
-  err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  if (err != cudaSuccess) return err;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  while (per_sm > 1 && sms * per_sm > kMaxGridCtas) --per_sm;
-  if (sms * per_sm > kMaxGridCtas) return cudaErrorInvalidConfiguration;
   void *args[] = {(void *)&a};
-  return cudaLaunchCooperativeKernel((const void *)kern, dim3(sms * per_sm), dim3(threads), args,
-                                     smem, st);
+  return cudaLaunchCooperativeKernel((const void *)kern, dim3(blocks), dim3(threads), args, smem, st);
 }
 
 // Fast-path shape: warps per variable (teams of P warps; at most 15 teams per CTA).
