@@ -158,6 +158,23 @@ int nmc_replicas_read_device(nmc_ctx *ctx, int32_t rs, const nmc_result *out_dev
  */
 int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
                   const int32_t *t1);
+/*
+ * nmc_batch_run for callers that must not allocate device memory during the call. The paper
+ * has no counterpart: this serves host programs that cannot call cudaMalloc at this point -
+ * code running inside a framework whose allocator owns all free device memory, or a loop
+ * that cannot afford the device-wide synchronisation an allocation may cause. It does the
+ * same work with the same results as nmc_batch_run on the same arguments, but its work list
+ * and counters live in one fixed 1 MiB device array of the library instead of memory the
+ * context allocates. Limit: one call takes at most (1 MiB - 256 B) / 112 B = 9360 work items,
+ * one per 32-replica word of each set (NMC_EINVAL beyond, with a message). The array is
+ * reserved on every GPU that loads the library until the process exits. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture. Every call shares the one array, which keeps
+ * the last call's work list: calls whose launches overlap on the GPU (other streams, other
+ * contexts, other host threads) race on it and must be serialised by the caller.
+ */
+int nmc_batch_run_noalloc(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
+                          const int32_t *t1);
 /* Largest n_vars nmc_batch_run accepts on this context's device. */
 int32_t nmc_batch_max_vars(nmc_ctx *ctx);
 

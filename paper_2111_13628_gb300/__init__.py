@@ -57,7 +57,7 @@ SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_
            "nmc_batch_max_vars", "nmc_server_create", "nmc_server_destroy",
            "nmc_server_submit_ksat", "nmc_server_submit_qap", "nmc_server_poll",
            "nmc_server_result", "nmc_server_cancel", "nmc_server_stats",
-           "nmc_server_last_error"]
+           "nmc_server_last_error", "nmc_batch_run_noalloc"]
 
 
 def library_path() -> str:
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
             "nmc_selftest_wait_timeout": ([P, i32], C.c_int),
             "nmc_batch_run": ([P, i32, P, P, P], C.c_int),
             "nmc_batch_max_vars": ([P], i32),
+            "nmc_batch_run_noalloc": ([P, i32, P, P, P], C.c_int),
             "nmc_server_create": ([C.c_int, P, P], C.c_int),
             "nmc_server_destroy": ([P], None),
             "nmc_server_submit_ksat": ([P, i32, i32, i32, P, P, i32, u64, P], C.c_int),
@@ -256,6 +257,15 @@ class Context:
         t0 = np.ascontiguousarray(np.broadcast_to(t0, rs.shape), dtype=np.int32)
         t1 = np.ascontiguousarray(np.broadcast_to(t1, rs.shape), dtype=np.int32)
         self._check(self._lib.nmc_batch_run(self._h, rs.size, _ptr(rs), _ptr(t0), _ptr(t1)))
+
+    def batch_run_noalloc(self, rs, t0, t1):
+        """nmc_batch_run_noalloc: the batched sweep with its work list in the library's fixed
+        device array (no device allocation during the call)."""
+        rs = np.ascontiguousarray(rs, dtype=np.int32)
+        t0 = np.ascontiguousarray(np.broadcast_to(t0, rs.shape), dtype=np.int32)
+        t1 = np.ascontiguousarray(np.broadcast_to(t1, rs.shape), dtype=np.int32)
+        self._check(self._lib.nmc_batch_run_noalloc(self._h, rs.size, _ptr(rs), _ptr(t0),
+                                                    _ptr(t1)))
 
     def batch_max_vars(self) -> int:
         return int(self._lib.nmc_batch_max_vars(self._h))

@@ -218,6 +218,88 @@ int init_replicas(nmc_ctx *ctx, const Instance &I, ReplicaSet &S, const void *in
 
 }  // namespace
 
+namespace nmc {
+
+int set_ctx_error(nmc_ctx *ctx, int code, const char *msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
+               const int32_t *t1, BatchPlan *plan) {
+  if (!ctx || !plan) return NMC_EINVAL;
+  if (n_sets < 0 || (n_sets > 0 && (!rs || !t0 || !t1)))
+    return fail(ctx, NMC_EINVAL, "bad batch arrays");
+  const size_t max_vars = batch_max_vars(ctx->tab_len, ctx->device);
+  std::vector<BatchItem> by_kq[2];
+  std::vector<long long> cost[2];
+  std::map<int32_t, int> seen;
+  plan->max_n[0] = plan->max_n[1] = 0;
+  for (int32_t i = 0; i < n_sets; ++i) {
+    ReplicaSet *S = find_set(ctx, rs[i]);
+    if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set in batch");
+    if (seen[rs[i]]++) return fail(ctx, NMC_EINVAL, "replica set repeated in batch");
+    Instance *I = find_inst(ctx, S->inst);
+    if (!I || I->kind != NMC_KIND_KSAT) return fail(ctx, NMC_EINVAL, "batch sets must be k-SAT");
+    if (t0[i] < 0 || t1[i] < t0[i]) return fail(ctx, NMC_EINVAL, "need 0 <= t0 <= t1");
+    if (t1[i] > t0[i] && (!I->bq || t1[i] > I->n_steps))
+      return fail(ctx, NMC_ESTATE, "schedule missing or shorter than t1");
+    if (I->ks.nb > 7) return fail(ctx, NMC_EINVAL, "batched sets need every variable in <= 127 clauses");
+    if (static_cast<size_t>(I->ks.n) > max_vars)
+      return fail(ctx, NMC_EINVAL, "instance too large for the batched kernel");
+    if (t1[i] == t0[i]) continue;
+    const int q = I->ks.kq == 1 ? 0 : 1;
+    for (int32_t w = 0; w < S->ks.W; ++w) {
+      BatchItem B;
+      B.occ_t = I->ks.occ_t;
+      B.grp_base = I->ks.grp_base;
+      B.cgrp = I->ks.cgrp;
+      B.col_ptr = I->ks.col_ptr;
+      B.orig = I->ks.orig;
+      B.bq = I->bq;
+      B.S = S->ks.S;
+      B.best = S->ks.best;
+      B.energy = S->ks.energy;
+      B.best_energy = S->ks.best_energy;
+      B.n = I->ks.n;
+      B.n_colours = I->ks.n_colours;
+      B.W = S->ks.W;
+      B.w = w;
+      B.t0 = t0[i];
+      B.t1 = t1[i];
+      B.k0 = static_cast<uint32_t>(S->seed);
+      B.k1 = static_cast<uint32_t>(S->seed >> 32);
+      by_kq[q].push_back(B);
+      cost[q].push_back(static_cast<long long>(I->ks.n_occ + I->ks.n) * (t1[i] - t0[i]));
+      if (I->ks.n > plan->max_n[q]) plan->max_n[q] = I->ks.n;
+    }
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, NMC_ECUDA, "query SMs");
+  }
+  plan->items.clear();
+  for (int q = 0; q < 2; ++q) {
+    std::vector<size_t> idx(by_kq[q].size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return cost[q][a] > cost[q][b]; });
+    plan->off[q] = plan->items.size();
+    plan->cnt[q] = static_cast<int>(idx.size());
+    for (size_t k : idx) plan->items.push_back(by_kq[q][k]);
+    int cs = 1;
+    while (cs < 8 && static_cast<long long>(plan->cnt[q]) * cs * 2 <= sms) cs *= 2;
+    plan->cs[q] = cs;
+  }
+  plan->device = ctx->device;
+  plan->stream = ctx->stream;
+  plan->tab = ctx->tab;
+  plan->tab_len = ctx->tab_len;
+  return NMC_OK;
+}
+
+}  // namespace nmc
+
 extern "C" {
 
 int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,

@@ -15,6 +15,7 @@
 #include <map>
 #include <mutex>
 
+#include "nmc.h"
 #include "nmc_internal.h"
 #include "philox.cuh"
 
@@ -387,6 +388,87 @@ cudaError_t dispatch_batch(int cs, const BatchItem *items, int n_items, int *nex
 
 }  // namespace
 
+// ---- batched sweep without any allocation ----------------------------------------------------
+//
+// Work list and counters live in one fixed device array of this file instead of memory the
+// context allocates on demand. kNoAllocBytes bounds one call: two counters, then up to
+// kNoAllocItems work items (one item = one 32-replica word of one replica set).
+constexpr size_t kNoAllocBytes = 1u << 20;  // 1 MiB on every GPU that loads the library
+constexpr size_t kNoAllocHeader = 256;      // two int counters, padded to the item alignment
+constexpr size_t kNoAllocItems = (kNoAllocBytes - kNoAllocHeader) / sizeof(BatchItem);
+static_assert(sizeof(BatchItem) == 112 && kNoAllocItems == 9360, "limit stated in nmc.h");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+// Device address of g_noalloc_scratch, looked up once per device (with that device current).
+// In host code the array's name is only a host-side stand-in, never a device address.
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[64] = {};
+
+int noalloc_scratch(int device, void **out) {
+  if (device < 0 || device >= 64) return NMC_EINVAL;
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return NMC_ECUDA;
+    }
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return NMC_OK;
+}
+
+}  // namespace
+
+}  // namespace nmc
+
+extern "C" int nmc_batch_run_noalloc(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs,
+                                     const int32_t *t0, const int32_t *t1) {
+  using namespace nmc;
+  if (!ctx) return NMC_EINVAL;
+  BatchPlan plan;
+  int rc = batch_plan(ctx, n_sets, rs, t0, t1, &plan);
+  if (rc != NMC_OK) return rc;
+  if (plan.items.empty()) return NMC_OK;
+  if (plan.items.size() > kNoAllocItems)
+    return set_ctx_error(ctx, NMC_EINVAL,
+                         "nmc_batch_run_noalloc: more work items (32-replica words) than the "
+                         "fixed scratch array holds; split the batch or use nmc_batch_run");
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  if (cudaSetDevice(plan.device) != cudaSuccess) {
+    cudaGetLastError();
+    return set_ctx_error(ctx, NMC_ECUDA, "nmc_batch_run_noalloc: cannot select the device");
+  }
+  void *base = nullptr;
+  rc = noalloc_scratch(plan.device, &base);
+  cudaError_t e = cudaSuccess;
+  if (rc == NMC_OK) {
+    int *counters = static_cast<int *>(base);
+    BatchItem *items = reinterpret_cast<BatchItem *>(static_cast<char *>(base) + kNoAllocHeader);
+    e = cudaMemcpyAsync(items, plan.items.data(), sizeof(BatchItem) * plan.items.size(),
+                        cudaMemcpyHostToDevice, plan.stream);
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+      if (plan.cnt[q] > 0)  // the launcher clears counters[q] on the stream before the kernel
+        e = ksat_batch(items + plan.off[q], plan.cnt[q], q + 1, plan.cs[q], plan.max_n[q],
+                       counters + q, plan.tab, plan.tab_len, plan.device, plan.stream);
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  if (rc != NMC_OK)
+    return set_ctx_error(ctx, rc, "nmc_batch_run_noalloc: cudaGetSymbolAddress failed");
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_ctx_error(ctx, NMC_ECUDA, cudaGetErrorString(e));
+  }
+  return NMC_OK;
+}
+
+namespace nmc {
 
 size_t batch_max_vars(int tab_len, int device) {
   int optin = 0;

@@ -4,6 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
+struct nmc_ctx;
+
 namespace nmc {
 
 // Philox counter tags (word 3 of the counter) that separate the streams of the chain.
@@ -115,6 +119,27 @@ size_t batch_max_vars(int tab_len, int device);
 cudaError_t ksat_batch(const BatchItem *items_dev, int n_items, int kq, int cs, int max_n,
                        int *next_item, const uint32_t *tab, int tab_len, int device,
                        cudaStream_t st);
+
+// A validated batched launch, ready to be placed into device memory: the work items in launch
+// order (occurrence width 1 first, then 2), with their counts, shapes and the context's
+// stream, table and device. Filled by batch_plan (api.cu).
+struct BatchPlan {
+  std::vector<BatchItem> items;
+  size_t off[2];
+  int cnt[2];
+  int max_n[2];
+  int cs[2];
+  int device;
+  cudaStream_t stream;
+  const uint32_t *tab;
+  int tab_len;
+};
+// Validates a batch as nmc_batch_run does and fills `plan`; returns NMC_OK or an error code
+// (recorded on the context).
+int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
+               const int32_t *t1, BatchPlan *plan);
+// Records an error message on the context; returns `code`.
+int set_ctx_error(nmc_ctx *ctx, int code, const char *msg);
 
 // ---- QAP launchers (qap.cu) ------------------------------------------------------------
 cudaError_t qap_init_states(const QapDevice &I, QapReplicas &Rp, uint64_t seed,
