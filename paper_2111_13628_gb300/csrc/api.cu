@@ -510,7 +510,11 @@ int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max
   // -- the same lists interleaved per group of 32 consecutive variables of a colour class
   //    (group g covers new ids [col_ptr[c] + 32k, +32)): occurrence j of the group's lane l
   //    sits at grp_base[g] + (j*kq + q)*32 + l (int4 units), so one warp load of occurrence j
-  //    is contiguous. Each group is padded to its longest list with inert entries.
+  //    is contiguous. Each group is padded to its longest list with inert entries. For k <= 4
+  //    an entry is {sign bytes, 4u1, 4u2, 4u3}: the other literals as byte offsets of their
+  //    variable's word in the shared-memory word vector, and bit 7 of byte 0 / 1 / 2 / 3 of the
+  //    first field set when the own literal / literal 1 / 2 / 3 is negated. For k > 4 the two
+  //    int4 hold the literal ids as in the per-variable lists.
   std::vector<int32_t> cgrp(n_colours + 1, 0), grp_base(1, 0);
   for (int32_t c = 0; c < n_colours; ++c) {
     const int32_t size = col_ptr[c + 1] - col_ptr[c];
@@ -533,8 +537,18 @@ int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max
           for (int q = 0; q < kq; ++q) {
             int32_t *dst = &occ_t[(static_cast<size_t>(grp_base[g]) + (j * kq + q) * 32 + l) * 4];
             const bool real = v < col_ptr[c + 1] && j < occ_ptr[v + 1] - occ_ptr[v];
-            if (real) {
-              const int32_t *src = &occ[(static_cast<size_t>(occ_ptr[v] + j) * slots) + 4 * q];
+            const int32_t *src = real ? &occ[(static_cast<size_t>(occ_ptr[v] + j) * slots) + 4 * q] : nullptr;
+            if (kq == 1) {
+              // src: {own sign mask, lit1, lit2, lit3} in literal ids (2u + neg)
+              const int32_t own_neg = real ? (src[0] != 0) : 0;
+              uint32_t signs = static_cast<uint32_t>(own_neg) << 7;
+              for (int z = 1; z < 4; ++z) {
+                const int32_t lit = real ? src[z] : (z == 1 ? lit_true : lit_false);
+                signs |= static_cast<uint32_t>(lit & 1) << (8 * z + 7);
+                dst[z] = (lit >> 1) * 4;
+              }
+              dst[0] = static_cast<int32_t>(signs);
+            } else if (real) {
               for (int z = 0; z < 4; ++z) dst[z] = src[z];
             } else {  // inert: own sign 0, one always-true literal
               dst[0] = q == 0 ? 0 : lit_false;

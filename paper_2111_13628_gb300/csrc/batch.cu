@@ -12,6 +12,7 @@
 // bit-sliced planes and converts them to per-replica sums once per sweep.
 #include <cooperative_groups.h>
 
+#include <cstdlib>
 #include <map>
 #include <mutex>
 
@@ -25,7 +26,7 @@ namespace nmc {
 
 namespace {
 
-constexpr int kBatchThreads = 768;
+constexpr int kBatchThreads = 640;
 
 __device__ __forceinline__ uint32_t maj3b(uint32_t a, uint32_t b, uint32_t c) {
   return (a & b) | (a & c) | (b & c);
@@ -73,6 +74,18 @@ __device__ __forceinline__ unsigned long long gather_bytes(const uint32_t *p, in
 
 constexpr int kAccPlanes = 16;  // per-thread energy accumulator: 16-bit two's complement
 
+// k <= 4 entries of the interleaved lists: literal words by byte offset into the word vector
+// (which starts at the beginning of dynamic shared memory); sign i is bit 7 of byte i of the
+// first field, turned into an all-zeros / all-ones mask.
+__device__ __forceinline__ uint32_t xs_at(const uint32_t *xs, int byte_off) {
+  return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(xs) + byte_off);
+}
+
+template <int I>
+__device__ __forceinline__ uint32_t sign_mask(uint32_t sg) {
+  return (uint32_t)((int32_t)(sg << (24 - 8 * I)) >> 31);
+}
+
 // Truth value (32 replicas) of literal id l = 2u + neg from the word vector in shared memory.
 __device__ __forceinline__ uint32_t lit_word(const uint32_t *xs, int l) {
   return xs[l >> 1] ^ (0u - (uint32_t)(l & 1));
@@ -98,17 +111,38 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
   const int gb = __ldg(B.grp_base + g);
   const int len = (__ldg(B.grp_base + g + 1) - gb) / (32 * KQ);
   const int4 *ent = B.occ_t + gb + ln;
+  // The entries of the next group of 4 occurrences are requested before the current group is
+  // evaluated, so the L2 latency of the list overlaps the shared-memory gathers and counting.
+  int4 qn[4 * KQ];
+  if (len > 0) {
+#pragma unroll
+    for (int j = 0; j < 4 * KQ; ++j) qn[j] = __ldg(ent + (size_t)j * 32);
+  }
   for (int e = 0; e < len; e += 4) {
+    int4 qc[4 * KQ];
+#pragma unroll
+    for (int j = 0; j < 4 * KQ; ++j) qc[j] = qn[j];
+    if (e + 4 < len) {
+#pragma unroll
+      for (int j = 0; j < 4 * KQ; ++j) qn[j] = __ldg(ent + (size_t)((e + 4) * KQ + j) * 32);
+    }
     uint32_t bb[4], mm[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int4 q = __ldg(ent + (size_t)((e + j) * KQ) * 32);
-      uint32_t o = lit_word(xs, q.y) | lit_word(xs, q.z) | lit_word(xs, q.w);
-      if (KQ == 2) {
-        const int4 q2 = __ldg(ent + (size_t)((e + j) * KQ + 1) * 32);
+      const int4 q = qc[j * KQ];
+      uint32_t o, own;
+      if (KQ == 1) {
+        const uint32_t sg = (uint32_t)q.x;
+        o = (xs_at(xs, q.y) ^ sign_mask<1>(sg)) |
+            (xs_at(xs, q.z) ^ sign_mask<2>(sg)) |
+            (xs_at(xs, q.w) ^ sign_mask<3>(sg));
+        own = x ^ sign_mask<0>(sg);
+      } else {
+        o = lit_word(xs, q.y) | lit_word(xs, q.z) | lit_word(xs, q.w);
+        const int4 q2 = qc[j * KQ + 1];
         o |= lit_word(xs, q2.x) | lit_word(xs, q2.y) | lit_word(xs, q2.z) | lit_word(xs, q2.w);
+        own = x ^ (uint32_t)q.x;
       }
-      const uint32_t own = x ^ (uint32_t)q.x;
       bb[j] = own & ~o;
       mm[j] = ~(own | o);
     }
@@ -202,10 +236,10 @@ __device__ __forceinline__ T *rank_ptr(T *p, int r) {
 template <int KQ, int CS>
 __global__ void __launch_bounds__(kBatchThreads, 1)
     ksat_batch_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
-                      const uint32_t *tab, int tab_len) {
+                      const uint32_t *tab, int tab_len, int xs_words) {
   extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t *tab_s = smem;
-  uint32_t *xs = smem + ((tab_len + 31) & ~31);
+  uint32_t *xs = smem;                               // word vector first (byte offsets in lists)
+  uint32_t *tab_s = smem + ((xs_words + 31) & ~31);  // then the acceptance table
   __shared__ int e_s[32], be_s[32], ep_s[32];
   __shared__ uint32_t imp_s;
   __shared__ int item_s;
@@ -305,14 +339,254 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   }
 }
 
+
+// ---- team variant: TL lanes per variable --------------------------------------------------------
+//
+// Same dynamics, shorter critical path: a team of TL consecutive lanes evaluates one variable.
+// Lane t of the team takes occurrences t, t+TL, ... of the variable's list, counts its break /
+// make masks in bit-sliced counters, and the team adds its TL partial counters with an xor
+// butterfly of shuffles, so every lane ends with the totals. Lane t then resolves the
+// acceptance of replica groups [t*8/TL, (t+1)*8/TL) (one Philox block per group of 4 replicas)
+// and the team ORs the flip bits. A colour class of a few hundred variables then costs the
+// latency of a TL-th of one attempt instead of a whole one.
+template <int NB>
+__device__ __forceinline__ void add_planes(uint32_t (&c)[NB], const uint32_t (&p)[NB]) {
+  uint32_t carry = 0u;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    const uint32_t a = c[j], b = p[j];
+    c[j] = a ^ b ^ carry;
+    carry = maj3b(a, b, carry);
+  }
+}
+
+template <int KQ, int TL>
+__device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint32_t *xs,
+                                                 const uint32_t *tab_s, int tab_len, int c,
+                                                 int c0, int v, bool active, int t, int tl,
+                                                 int (&acc)[32 / TL]) {
+  constexpr int NB = 7;
+  const uint32_t x = active ? xs[v] : 0u;
+  const uint32_t bqv = active ? __ldg(B.bq + (size_t)t * B.n + v) : 0u;
+  uint32_t bc[NB], mc[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    bc[j] = 0u;
+    mc[j] = 0u;
+  }
+  int len = 0;
+  const int4 *ent = nullptr;
+  if (active) {
+    const int off = v - c0;
+    const int g = __ldg(B.cgrp + c) + (off >> 5), ln = off & 31;
+    const int gb = __ldg(B.grp_base + g);
+    len = (__ldg(B.grp_base + g + 1) - gb) / (32 * KQ);
+    ent = B.occ_t + gb + ln;
+  }
+  for (int j0 = tl; j0 < len; j0 += 4 * TL) {
+    uint32_t bb[4], mm[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = j0 + i * TL;
+      bb[i] = 0u;
+      mm[i] = 0u;
+      if (j < len) {
+        const int4 q = __ldg(ent + (size_t)(j * KQ) * 32);
+        uint32_t o, own;
+        if (KQ == 1) {
+          const uint32_t sg = (uint32_t)q.x;
+          o = (xs_at(xs, q.y) ^ sign_mask<1>(sg)) |
+              (xs_at(xs, q.z) ^ sign_mask<2>(sg)) |
+              (xs_at(xs, q.w) ^ sign_mask<3>(sg));
+          own = x ^ sign_mask<0>(sg);
+        } else {
+          o = lit_word(xs, q.y) | lit_word(xs, q.z) | lit_word(xs, q.w);
+          const int4 q2 = __ldg(ent + (size_t)(j * KQ + 1) * 32);
+          o |= lit_word(xs, q2.x) | lit_word(xs, q2.y) | lit_word(xs, q2.z) | lit_word(xs, q2.w);
+          own = x ^ (uint32_t)q.x;
+        }
+        bb[i] = own & ~o;
+        mm[i] = ~(own | o);
+      }
+    }
+    csa4<NB>(bc, bb[0], bb[1], bb[2], bb[3]);
+    csa4<NB>(mc, mm[0], mm[1], mm[2], mm[3]);
+  }
+#pragma unroll
+  for (int sft = 1; sft < TL; sft <<= 1) {
+    uint32_t pb[NB], pm[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      pb[j] = __shfl_xor_sync(0xFFFFFFFFu, bc[j], sft);
+      pm[j] = __shfl_xor_sync(0xFFFFFFFFu, mc[j], sft);
+    }
+    add_planes<NB>(bc, pb);
+    add_planes<NB>(mc, pm);
+  }
+  uint32_t d[NB + 1];
+  {
+    uint32_t br = 0u;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      d[j] = bc[j] ^ mc[j] ^ br;
+      br = maj3b(~bc[j], mc[j], br);
+    }
+    d[NB] = br;
+  }
+  const uint32_t vo = active ? (uint32_t)__ldg(B.orig + v) : 0u;
+  const uint32_t bq_hi = bqv >> 8, bq_lo = bqv & 255u;
+  constexpr int GPL = 8 / TL;  // Philox groups per lane
+  uint32_t flip = 0u;
+#pragma unroll
+  for (int gi = 0; gi < GPL; ++gi) {
+    const int g = tl * GPL + gi;
+    int de[4];
+    uint32_t th[4];
+    bool need = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = 4 * g + j;
+      int val = 0;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) val |= (int)((d[k] >> r) & 1u) << k;
+      val -= (int)((d[NB] >> r) & 1u) << NB;
+      de[j] = val;
+      th[j] = 0u;
+      if (val > 0) {
+        const uint32_t idx = bq_hi * (uint32_t)val + ((bq_lo * (uint32_t)val) >> 8);
+        th[j] = idx < (uint32_t)tab_len ? tab_s[idx] : 0u;
+      }
+      need |= th[j] != 0u;
+    }
+    uint4 u = make_uint4(0u, 0u, 0u, 0u);
+    if (need && active)
+      u = philox4x32_10(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + g), kTagKsatSweep), B.k0, B.k1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (de[j] <= 0 || uint4_word(u, j) < th[j]) {
+        flip |= 1u << (4 * g + j);
+        if (active) acc[4 * gi + j] += de[j];
+      }
+    }
+  }
+#pragma unroll
+  for (int sft = 1; sft < TL; sft <<= 1) flip |= __shfl_xor_sync(0xFFFFFFFFu, flip, sft);
+  return x ^ flip;
+}
+
+template <int KQ, int CS, int TL>
+__global__ void __launch_bounds__(kBatchThreads, 1)
+    ksat_team_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
+                     const uint32_t *tab, int tab_len, int xs_words) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t *xs = smem;                               // word vector first (byte offsets in lists)
+  uint32_t *tab_s = smem + ((xs_words + 31) & ~31);  // then the acceptance table
+  __shared__ int e_s[32], be_s[32], ep_s[32];
+  __shared__ uint32_t imp_s;
+  __shared__ int item_s;
+  __shared__ BatchItem item_b;
+  const int rank = CS == 1 ? 0 : (int)cg::this_cluster().block_rank();
+  for (int i = threadIdx.x; i < tab_len; i += blockDim.x) tab_s[i] = tab[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tl = lane % TL;                       // lane inside the team
+  const int team = threadIdx.x / TL;              // team inside the CTA
+  const int nteams = blockDim.x / TL;
+  while (true) {
+    if (rank == 0 && threadIdx.x == 0) item_s = atomicAdd(next_item, 1);
+    group_sync<CS>();
+    const int it = *rank_ptr<CS>(&item_s, 0);
+    if (it < n_items && threadIdx.x == 0) item_b = items[it];
+    group_sync<CS>();
+    if (it >= n_items) break;
+    const BatchItem &B = item_b;
+    const int n = B.n, W = B.W, w = B.w;
+    const int share = (n + CS - 1) / CS;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) xs[v] = B.S[(size_t)(2 * v) * W + w];
+    if (threadIdx.x == 0) xs[n] = 0u;
+    if (threadIdx.x < 32) {
+      ep_s[threadIdx.x] = 0;
+      if (rank == 0) {
+        e_s[threadIdx.x] = B.energy[32 * w + threadIdx.x];
+        be_s[threadIdx.x] = B.best_energy[32 * w + threadIdx.x];
+      }
+    }
+    group_sync<CS>();
+    for (int t = B.t0; t < B.t1; ++t) {
+      int acc[32 / TL];
+#pragma unroll
+      for (int i = 0; i < 32 / TL; ++i) acc[i] = 0;
+      for (int c = 0; c < B.n_colours; ++c) {
+        const int c0 = __ldg(B.col_ptr + c), c1 = __ldg(B.col_ptr + c + 1);
+        const int part = ((c1 - c0 + CS - 1) / CS + 31) & ~31;
+        const int v0 = c0 + rank * part, v1 = min(c1, v0 + part);
+        // warp-uniform trip count: the warp's teams take consecutive variables each round
+        for (int vw = v0 + warp * (32 / TL); vw < v1; vw += nteams) {
+          const int v = vw + (lane / TL);
+          const bool active = v < v1;
+          const uint32_t xn = attempt_team<KQ, TL>(B, xs, tab_s, tab_len, c, c0, v, active, t, tl, acc);
+          if (active && tl == 0) {
+            if (CS == 1) {
+              xs[v] = xn;
+            } else {
+              const uint32_t sa = (uint32_t)__cvta_generic_to_shared(xs + v);
+#pragma unroll
+              for (int r = 0; r < CS; ++r) st_rank(sa, r, xn);
+            }
+          }
+        }
+        group_sync<CS>();
+      }
+#pragma unroll
+      for (int i = 0; i < 32 / TL; ++i)
+        if (acc[i] != 0) atomicAdd(&ep_s[4 * (tl * (8 / TL) + i / 4) + (i & 3)], acc[i]);
+      group_sync<CS>();
+      if (rank == 0 && warp == 0) {
+        int sum = e_s[lane];
+#pragma unroll
+        for (int r = 0; r < CS; ++r) sum += rank_ptr<CS>(ep_s, r)[lane];
+        e_s[lane] = sum;
+        const bool better = sum < be_s[lane];
+        if (better) be_s[lane] = sum;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, better);
+        if (lane == 0) imp_s = m;
+      }
+      group_sync<CS>();
+      const uint32_t m = *rank_ptr<CS>(&imp_s, 0);
+      if (threadIdx.x < 32) ep_s[threadIdx.x] = 0;
+      if (m) {
+        const int b0 = rank * share, b1 = min(n, b0 + share);
+        for (int v = b0 + threadIdx.x; v < b1; v += blockDim.x) {
+          const size_t bi = (size_t)v * W + w;
+          B.best[bi] = (B.best[bi] & ~m) | (xs[v] & m);
+        }
+        group_sync<CS>();
+      }
+    }
+    {
+      const int b0 = rank * share, b1 = min(n, b0 + share);
+      for (int v = b0 + threadIdx.x; v < b1; v += blockDim.x) {
+        B.S[(size_t)(2 * v) * W + w] = xs[v];
+        B.S[(size_t)(2 * v + 1) * W + w] = ~xs[v];
+      }
+    }
+    if (rank == 0 && threadIdx.x < 32) {
+      B.energy[32 * w + threadIdx.x] = e_s[threadIdx.x];
+      B.best_energy[32 * w + threadIdx.x] = be_s[threadIdx.x];
+    }
+    group_sync<CS>();
+  }
+  (void)team;
+}
+
 // The launch shape of each kernel instance is queried once per (device, shared-memory size):
 // occupancy and cluster queries are slow host calls.
-template <int KQ, int CS>
+template <int KQ, int CS, int TL>
 cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
                          const uint32_t *tab, int tab_len, int max_n, int device,
                          cudaStream_t st) {
-  const size_t smem = sizeof(uint32_t) * (((tab_len + 31) & ~31) + (size_t)max_n + 1);
-  auto kern = ksat_batch_kernel<KQ, CS>;
+  const int xs_words = max_n + 1;
+  const size_t smem = sizeof(uint32_t) * (((size_t)xs_words + 31) / 32 * 32 + (size_t)tab_len);
+  auto kern = TL == 1 ? ksat_batch_kernel<KQ, CS> : ksat_team_kernel<KQ, CS, (TL > 1 ? TL : 4)>;
   static std::mutex mu;
   static std::map<std::pair<int, size_t>, int> shapes;  // (device, smem) -> resident clusters
   static std::map<int, size_t> smem_set;                // device -> largest smem attribute set
@@ -372,17 +646,42 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
   cfg.gridDim = dim3(clusters * CS);
   cudaError_t err = cudaMemsetAsync(next_item, 0, sizeof(int), st);
   if (err != cudaSuccess) return err;
-  return cudaLaunchKernelEx(&cfg, kern, items, n_items, next_item, tab, tab_len);
+  return cudaLaunchKernelEx(&cfg, kern, items, n_items, next_item, tab, tab_len, xs_words);
+}
+
+// Lanes per variable of the batched kernel: 1 (one thread per variable) or a team of 4 or 8.
+// Few variables per CTA per colour class favour teams (latency), many favour single threads.
+int batch_lanes(int cs, int max_n) {
+  if (const char *env = getenv("NMC_BATCH_LANES")) {
+    const int l = atoi(env);
+    if (l == 1 || l == 4 || l == 8) return l;
+  }
+  // variables of one colour class per CTA, taking ~32 classes: teams only when single
+  // threads would leave most of the CTA idle in every class
+  const int per_cta = max_n / (32 * cs);
+  if (per_cta * 8 <= kBatchThreads) return 8;
+  if (per_cta * 4 <= kBatchThreads) return 4;
+  return 1;
+}
+
+template <int KQ, int CS>
+cudaError_t dispatch_lanes(const BatchItem *items, int n_items, int *next_item, const uint32_t *tab,
+                           int tab_len, int max_n, int device, cudaStream_t st) {
+  switch (batch_lanes(CS, max_n)) {
+    case 4: return launch_batch<KQ, CS, 4>(items, n_items, next_item, tab, tab_len, max_n, device, st);
+    case 8: return launch_batch<KQ, CS, 8>(items, n_items, next_item, tab, tab_len, max_n, device, st);
+    default: return launch_batch<KQ, CS, 1>(items, n_items, next_item, tab, tab_len, max_n, device, st);
+  }
 }
 
 template <int KQ>
 cudaError_t dispatch_batch(int cs, const BatchItem *items, int n_items, int *next_item,
                            const uint32_t *tab, int tab_len, int max_n, int device, cudaStream_t st) {
   switch (cs) {
-    case 8: return launch_batch<KQ, 8>(items, n_items, next_item, tab, tab_len, max_n, device, st);
-    case 4: return launch_batch<KQ, 4>(items, n_items, next_item, tab, tab_len, max_n, device, st);
-    case 2: return launch_batch<KQ, 2>(items, n_items, next_item, tab, tab_len, max_n, device, st);
-    default: return launch_batch<KQ, 1>(items, n_items, next_item, tab, tab_len, max_n, device, st);
+    case 8: return dispatch_lanes<KQ, 8>(items, n_items, next_item, tab, tab_len, max_n, device, st);
+    case 4: return dispatch_lanes<KQ, 4>(items, n_items, next_item, tab, tab_len, max_n, device, st);
+    case 2: return dispatch_lanes<KQ, 2>(items, n_items, next_item, tab, tab_len, max_n, device, st);
+    default: return dispatch_lanes<KQ, 1>(items, n_items, next_item, tab, tab_len, max_n, device, st);
   }
 }
 
@@ -475,7 +774,7 @@ size_t batch_max_vars(int tab_len, int device) {
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
     return 0;
   // dynamic shared memory: table + n+1 words; the static part is under 192 words
-  const long long words = (long long)optin / 4 - ((tab_len + 31) & ~31) - 1 - 192;
+  const long long words = (long long)optin / 4 - tab_len - 32 - 1 - 192;
   return words > 0 ? (size_t)words : 0;
 }
 

@@ -18,7 +18,9 @@ def ctx():
     c.close()
 
 
-def test_uneven_batch_matches_oracle(ctx):
+@pytest.mark.parametrize("lanes", [1, 4, 8])
+def test_uneven_batch_matches_oracle(ctx, monkeypatch, lanes):
+    monkeypatch.setenv("NMC_BATCH_LANES", str(lanes))
     specs = [(120, 4.2, 3, 32, 30), (333, 9.6, 4, 70, 30), (57, 9.6, 4, 1, 30),
              (900, 4.2, 3, 96, 30), (64, 2.0, 6, 40, 30), (1500, 9.6, 4, 33, 30)]
     sets, inputs = [], []
@@ -81,11 +83,14 @@ def test_batch_rejects(ctx):
     ctx.unload(inst)
 
 
+@pytest.mark.parametrize("lanes", [1, 4, 8])
 @pytest.mark.parametrize("ctas", [1, 2, 4, 8])
-def test_cluster_shapes_agree(ctx, monkeypatch, ctas):
-    """One large instance spread over clusters of 1, 2, 4 or 8 CTAs per 32-replica word gives
-    the oracle's trajectories (sampled replicas) and the single-set path's results."""
+def test_cluster_shapes_agree(ctx, monkeypatch, ctas, lanes):
+    """One large instance spread over clusters of 1, 2, 4 or 8 CTAs per 32-replica word, with 1,
+    4 or 8 lanes per variable, gives the oracle's trajectories (sampled replicas) and the
+    grid-kernel path's results."""
     monkeypatch.setenv("NMC_BATCH_CTAS", str(ctas))
+    monkeypatch.setenv("NMC_BATCH_LANES", str(lanes))
     n, T, R = 3000, 6, 1024
     lits = W.random_ksat(n, 9.6, 4, 91)
     beta = W.beta_frozen_ramp(n, T, 0.3, 6.0, 0.2, 0.4, 92)
@@ -94,7 +99,9 @@ def test_cluster_shapes_agree(ctx, monkeypatch, ctas):
     a = ctx.replicas_create(inst, R, seed=93)
     b = ctx.replicas_create(inst, R, seed=93)
     ctx.batch_run([a], 0, T)
+    monkeypatch.setenv("NMC_RUN_PATH", "grid")
     ctx.replicas_run(b, 0, T)
+    monkeypatch.delenv("NMC_RUN_PATH")
     ga, gb = ctx.replicas_read(a), ctx.replicas_read(b)
     for key in KEYS:
         assert np.array_equal(ga[key], gb[key]), key
