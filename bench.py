@@ -42,6 +42,22 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def captured_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu capture, or None if the kernel source has
+    changed since the counters were taken (or the workload differs)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        if h != rec["source_sha256_16"] or rec["workload"] != workload:
+            return None
+        return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+    except Exception:
+        return None
+
+
 def algorithmic_bytes_per_sweep(lits: np.ndarray, n_vars: int, replicas: int) -> int:
     """Bytes one sweep must move: for every attempt the (k-1) neighbour literals of each
     clause of the variable, one bit per replica (replica-private state), the variable's own
@@ -259,7 +275,9 @@ def run_ours(args, world, rank, local):
                    "parallelism": "replicas only" if world == 1 else f"replicas x{world} GPUs",
                    "l2": "flushed between steps (512 MB write); beta schedule 1 GB > L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (captured_traffic("ksat_batch_kernel", wl["name"] + f"_t{T}")
+                                 if args.path != "grid" else None),
                      "kernel": ("ksat_batch_kernel (clusters of CTAs per replica word)"
                                 if args.path != "grid" else "ksat_sweep_fast_kernel (grid barrier)"),
                      "peak_source": peak_kind,
