@@ -448,8 +448,7 @@ def run_qap_batch(args):
         if i == args.warmup:
             ctx.sync()
             a.record(stream)
-        for rs in sets:
-            ctx.replicas_run(rs, 0, steps_s)
+        ctx.qap_batch_run(sets, 0, steps_s)  # one launch, one CTA per 32-replica block
     b.record(stream)
     ctx.sync()
     ms = a.elapsed_time(b) / args.steps
@@ -497,26 +496,26 @@ def run_serving(args):
             factor = np.where(W.seeded_subset(n, 0.3, 8000 + i), 0.5, 1.0).astype(np.float32)
             reqs.append(("ksat", (lits, n), base, factor, 32, T))
     work = sum(r[1][-1] * r[4] * r[5] for r in reqs)
-    srv = nmc.Server(0, max_active=args.max_active, slice_log2=args.slice_log2)
+    srv = nmc.Server(0, max_active=args.max_active, slice_log2=args.slice_log2,
+                     memory_budget=int(args.memory_budget_gb * (1 << 30)))
     ids = [None] * nreq
     t0 = time.perf_counter()
 
-    def submitter():
-        for i, r in enumerate(reqs):
-            wait = t0 + t_arr[i] - time.perf_counter()
-            if wait > 0:
-                time.sleep(wait)
-            kind, inst, base, factor, R, T = r
-            if kind == "ksat":
-                ids[i] = srv.submit_ksat(inst[0], inst[1], base=base, factor=factor, replicas=R,
-                                         seed=i)
-            else:
-                ids[i] = srv.submit_qap(inst[0], inst[1], base=base, factor=factor, replicas=R,
-                                        seed=i)
+    def submit_one(i):
+        kind, inst, base, factor, R, T = reqs[i]
+        wait = t0 + t_arr[i] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        if kind == "ksat":
+            ids[i] = srv.submit_ksat(inst[0], inst[1], base=base, factor=factor, replicas=R, seed=i)
+        else:
+            ids[i] = srv.submit_qap(inst[0], inst[1], base=base, factor=factor, replicas=R, seed=i)
 
-    th = threading.Thread(target=submitter)
-    th.start()
-    th.join()
+    from concurrent.futures import ThreadPoolExecutor
+    # submissions run on a pool: a k-SAT submit builds the instance on the host (colouring,
+    # lists) on the calling thread, so arrivals are not serialised behind one another
+    with ThreadPoolExecutor(max_workers=16) as pool:
+        list(pool.map(submit_one, range(nreq)))
     print(f"serving: {nreq} requests submitted in {time.perf_counter() - t0:.1f} s; "
           f"stats {srv.stats()}", file=sys.stderr, flush=True)
     lat, failed = [], 0
@@ -585,8 +584,9 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=20.0)
     ap.add_argument("--pool", type=int, default=32)
-    ap.add_argument("--max-active", type=int, default=512)
-    ap.add_argument("--slice-log2", type=int, default=22)
+    ap.add_argument("--max-active", type=int, default=4096)
+    ap.add_argument("--slice-log2", type=int, default=27)
+    ap.add_argument("--memory-budget-gb", type=float, default=200.0)
     ap.add_argument("--plain-sample", type=int, default=24)
     ap.add_argument("--path", default="run", choices=["run", "batch", "grid"],
                     help="run: nmc_replicas_run (the library picks the kernel); batch: "

@@ -175,6 +175,10 @@ int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t
  */
 int nmc_batch_run_noalloc(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
                           const int32_t *t1);
+/* Batched QAP steps: runs steps t0[i]..t1[i]-1 of QAP replica sets rs[i] in one launch (one CTA
+ * per block of 32 replicas), asynchronously; results as nmc_replicas_run on each set alone. */
+int nmc_qap_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
+                      const int32_t *t1);
 /* Largest n_vars nmc_batch_run accepts on this context's device. */
 int32_t nmc_batch_max_vars(nmc_ctx *ctx);
 
@@ -193,7 +197,9 @@ int nmc_anneal(nmc_ctx *ctx, int32_t inst, int32_t replicas, int32_t t0, int32_t
  * the device memory they will hold stays within memory_budget bytes (a request larger than the
  * whole budget fails with NMC_ENOMEM). Admitted requests keep their instance, schedule and
  * replica state resident on the device until they finish. Every tick advances all active
- * requests by a slice of about 2^slice_log2 variable-word updates each, k-SAT requests together
+ * requests by a slice of about 2^slice_log2 units of work each (one unit: one clause
+ * occurrence of one variable for 32 replicas; a QAP swap attempt on one replica counts as n/3
+ * units), so that requests progress at similar wall-clock rates, k-SAT requests together
  * in one batched launch (nmc_batch_run), so requests that arrive while others run share the
  * following launches. Results are bit for bit those of nmc_anneal on the same inputs
  * (segment invariance). All nmc_server_* calls are thread-safe.

@@ -57,7 +57,7 @@ SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_
            "nmc_batch_max_vars", "nmc_server_create", "nmc_server_destroy",
            "nmc_server_submit_ksat", "nmc_server_submit_qap", "nmc_server_poll",
            "nmc_server_result", "nmc_server_cancel", "nmc_server_stats",
-           "nmc_server_last_error", "nmc_batch_run_noalloc"]
+           "nmc_server_last_error", "nmc_batch_run_noalloc", "nmc_qap_batch_run"]
 
 
 def library_path() -> str:
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
             "nmc_batch_run": ([P, i32, P, P, P], C.c_int),
             "nmc_batch_max_vars": ([P], i32),
             "nmc_batch_run_noalloc": ([P, i32, P, P, P], C.c_int),
+            "nmc_qap_batch_run": ([P, i32, P, P, P], C.c_int),
             "nmc_server_create": ([C.c_int, P, P], C.c_int),
             "nmc_server_destroy": ([P], None),
             "nmc_server_submit_ksat": ([P, i32, i32, i32, P, P, i32, u64, P], C.c_int),
@@ -266,6 +267,13 @@ class Context:
         t1 = np.ascontiguousarray(np.broadcast_to(t1, rs.shape), dtype=np.int32)
         self._check(self._lib.nmc_batch_run_noalloc(self._h, rs.size, _ptr(rs), _ptr(t0),
                                                     _ptr(t1)))
+
+    def qap_batch_run(self, rs, t0, t1):
+        """Runs steps t0[i]..t1[i]-1 of QAP replica sets rs[i] in one batched launch."""
+        rs = np.ascontiguousarray(rs, dtype=np.int32)
+        t0 = np.ascontiguousarray(np.broadcast_to(t0, rs.shape), dtype=np.int32)
+        t1 = np.ascontiguousarray(np.broadcast_to(t1, rs.shape), dtype=np.int32)
+        self._check(self._lib.nmc_qap_batch_run(self._h, rs.size, _ptr(rs), _ptr(t0), _ptr(t1)))
 
     def batch_max_vars(self) -> int:
         return int(self._lib.nmc_batch_max_vars(self._h))

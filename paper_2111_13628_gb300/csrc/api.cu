@@ -71,6 +71,8 @@ struct nmc_ctx {
   BatchItem *items = nullptr;  // batched-kernel work list (grown on demand)
   size_t items_cap = 0;
   int32_t *next_item = nullptr;  // two work counters (one per occurrence width)
+  QapArgs *qitems = nullptr;     // batched QAP work list (grown on demand)
+  size_t qitems_cap = 0;
 };
 
 namespace {
@@ -353,6 +355,7 @@ void nmc_destroy(nmc_ctx *ctx) {
   dev_free(ctx->flag);
   dev_free(ctx->items);
   dev_free(ctx->next_item);
+  dev_free(ctx->qitems);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaGetLastError();
   delete ctx;
@@ -396,14 +399,22 @@ int32_t nmc_threshold_table(uint32_t *out, int32_t cap) {
   return len;
 }
 
-int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max,
-                  const int32_t *lits, int32_t *inst_out) {
-  if (!ctx) return NMC_EINVAL;
-  if (!inst_out) return fail(ctx, NMC_EINVAL, "inst_out is NULL");
-  if (n_vars < 1 || n_vars >= (1 << 28)) return fail(ctx, NMC_EINVAL, "n_vars out of range");
-  if (n_clauses < 0) return fail(ctx, NMC_EINVAL, "n_clauses < 0");
-  if (k_max < 1 || k_max > 8) return fail(ctx, NMC_EINVAL, "k_max must be in [1, 8]");
-  if (n_clauses > 0 && !lits) return fail(ctx, NMC_EINVAL, "lits is NULL");
+}  // extern "C"
+
+namespace nmc {
+
+int prep_fail(HostKsat *out, int code, const std::string &msg) {
+  out->code = code;
+  out->err = msg;
+  return code;
+}
+
+int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t *lits,
+                 HostKsat *out) {
+  if (n_vars < 1 || n_vars >= (1 << 28)) return prep_fail(out, NMC_EINVAL, "n_vars out of range");
+  if (n_clauses < 0) return prep_fail(out, NMC_EINVAL, "n_clauses < 0");
+  if (k_max < 1 || k_max > 8) return prep_fail(out, NMC_EINVAL, "k_max must be in [1, 8]");
+  if (n_clauses > 0 && !lits) return prep_fail(out, NMC_EINVAL, "lits is NULL");
   const int32_t n = n_vars, m = n_clauses, K = k_max;
   // -- checks and variable -> clause incidence (clauses in ascending order)
   std::vector<int32_t> deg(n + 1, 0);
@@ -412,22 +423,22 @@ int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max
     for (int q = 0; q < K; ++q) {
       const int32_t l = lits[a * K + q];
       if (l == 0) continue;
-      if (l < -n || l > n) return fail(ctx, NMC_EINVAL, "literal out of range in clause " + std::to_string(a));
+      if (l < -n || l > n) return prep_fail(out, NMC_EINVAL, "literal out of range in clause " + std::to_string(a));
       const int32_t v = (l > 0 ? l : -l) - 1;
       for (int q2 = 0; q2 < q; ++q2) {
         const int32_t l2 = lits[a * K + q2];
         if (l2 != 0 && ((l2 > 0 ? l2 : -l2) - 1) == v)
-          return fail(ctx, NMC_EINVAL, "variable repeated in clause " + std::to_string(a));
+          return prep_fail(out, NMC_EINVAL, "variable repeated in clause " + std::to_string(a));
       }
       ++used;
       ++deg[v];
     }
-    if (used == 0) return fail(ctx, NMC_EINVAL, "empty clause " + std::to_string(a));
+    if (used == 0) return prep_fail(out, NMC_EINVAL, "empty clause " + std::to_string(a));
   }
   int32_t dmax = 0;
   for (int32_t v = 0; v < n; ++v) dmax = deg[v] > dmax ? deg[v] : dmax;
   if (dmax > kMaxDegree)
-    return fail(ctx, NMC_EINVAL, "a variable occurs in more than 1023 clauses");
+    return prep_fail(out, NMC_EINVAL, "a variable occurs in more than 1023 clauses");
   std::vector<int32_t> vptr(n + 1, 0);
   for (int32_t v = 0; v < n; ++v) vptr[v + 1] = vptr[v] + deg[v];
   std::vector<int32_t> vcl(vptr[n] > 0 ? vptr[n] : 1);
@@ -570,7 +581,35 @@ int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max
     }
   int nb = 2;
   while ((1 << nb) <= dmax) ++nb;
-  // -- upload
+  out->n = n;
+  out->m = m;
+  out->K = K;
+  out->n_colours = n_colours;
+  out->kq = kq;
+  out->nb = nb;
+  out->n_occ = static_cast<int32_t>(n_occ);
+  out->occ = std::move(occ);
+  out->occ_ptr = std::move(occ_ptr);
+  out->col_ptr = std::move(col_ptr);
+  out->orig = std::move(orig);
+  out->newid = std::move(newid);
+  out->clits = std::move(clits);
+  out->occ_t = std::move(occ_t);
+  out->grp_base = std::move(grp_base);
+  out->cgrp = std::move(cgrp);
+  out->colour = std::move(colour);
+  out->code = NMC_OK;
+  return NMC_OK;
+}
+
+int upload_ksat(nmc_ctx *ctx, HostKsat &h, int32_t *inst_out) {
+  if (!ctx || !inst_out) return NMC_EINVAL;
+  if (h.code != NMC_OK) return fail(ctx, h.code, h.err);
+  const int32_t n = h.n, m = h.m, K = h.K, n_colours = h.n_colours, kq = h.kq, nb = h.nb;
+  const int64_t n_occ = h.n_occ;
+  std::vector<int32_t> &occ = h.occ, &occ_ptr = h.occ_ptr, &col_ptr = h.col_ptr, &orig = h.orig,
+                       &newid = h.newid, &clits = h.clits, &occ_t = h.occ_t,
+                       &grp_base = h.grp_base, &cgrp = h.cgrp, &colour = h.colour;
   DeviceGuard g(ctx->device);
   Instance I;
   I.kind = NMC_KIND_KSAT;
@@ -609,6 +648,20 @@ int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max
   ctx->insts[id] = I;
   *inst_out = id;
   return NMC_OK;
+}
+
+
+}  // namespace nmc
+
+extern "C" {
+
+int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max,
+                  const int32_t *lits, int32_t *inst_out) {
+  if (!ctx) return NMC_EINVAL;
+  if (!inst_out) return fail(ctx, NMC_EINVAL, "inst_out is NULL");
+  HostKsat h;
+  if (prepare_ksat(n_vars, n_clauses, k_max, lits, &h) != NMC_OK) return fail(ctx, h.code, h.err);
+  return upload_ksat(ctx, h, inst_out);
 }
 
 int nmc_load_qap(nmc_ctx *ctx, int32_t n, const int32_t *F, const int32_t *D, int32_t *inst_out) {
@@ -938,6 +991,61 @@ int nmc_replicas_read(nmc_ctx *ctx, int32_t rs, const nmc_result *out) {
 
 int nmc_replicas_read_device(nmc_ctx *ctx, int32_t rs, const nmc_result *out_dev) {
   return read_impl(ctx, rs, out_dev, false);
+}
+
+int nmc_qap_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
+                      const int32_t *t1) {
+  if (!ctx) return NMC_EINVAL;
+  if (n_sets < 0 || (n_sets > 0 && (!rs || !t0 || !t1)))
+    return fail(ctx, NMC_EINVAL, "bad batch arrays");
+  DeviceGuard g(ctx->device);
+  std::vector<QapArgs> by_npl[8];
+  int max_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  std::map<int32_t, int> seen;
+  for (int32_t i = 0; i < n_sets; ++i) {
+    ReplicaSet *S = find_set(ctx, rs[i]);
+    if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set in batch");
+    if (seen[rs[i]]++) return fail(ctx, NMC_EINVAL, "replica set repeated in batch");
+    Instance *I = find_inst(ctx, S->inst);
+    if (!I || I->kind != NMC_KIND_QAP) return fail(ctx, NMC_EINVAL, "batch sets must be QAP");
+    if (t0[i] < 0 || t1[i] < t0[i]) return fail(ctx, NMC_EINVAL, "need 0 <= t0 <= t1");
+    if (t1[i] > t0[i] && (!I->bq || t1[i] > I->n_steps))
+      return fail(ctx, NMC_ESTATE, "schedule missing or shorter than t1");
+    if (t1[i] == t0[i]) continue;
+    const int n = I->qp.n;
+    const int q = (n + 31) / 32 - 1;  // registers per lane - 1
+    for (int b = 0; b < (S->R + 31) / 32; ++b)
+      by_npl[q].push_back(qap_block_args(I->qp, S->qp, I->bq, ctx->tab, ctx->tab_len, t0[i], t1[i],
+                                         S->seed, b));
+    max_n[q] = std::max(max_n[q], n);
+  }
+  size_t total = 0;
+  for (int q = 0; q < 8; ++q) total += by_npl[q].size();
+  if (total == 0) return NMC_OK;
+  if (total > ctx->qitems_cap) {
+    NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    dev_free(ctx->qitems);
+    ctx->qitems_cap = 0;
+    NMC_CUDA(dev_alloc(&ctx->qitems, total), "allocate QAP work list");
+    ctx->qitems_cap = total;
+  }
+  std::vector<QapArgs> all;
+  all.reserve(total);
+  size_t off[8];
+  for (int q = 0; q < 8; ++q) {
+    off[q] = all.size();
+    all.insert(all.end(), by_npl[q].begin(), by_npl[q].end());
+  }
+  NMC_CUDA(cudaMemcpyAsync(ctx->qitems, all.data(), sizeof(QapArgs) * total, cudaMemcpyHostToDevice,
+                           ctx->stream),
+           "upload QAP work list");
+  for (int q = 0; q < 8; ++q) {
+    if (by_npl[q].empty()) continue;
+    NMC_CUDA(qap_batch(ctx->qitems + off[q], static_cast<int>(by_npl[q].size()), q + 1, max_n[q],
+                       ctx->tab_len, ctx->stream),
+             "launch batched QAP");
+  }
+  return NMC_OK;
 }
 
 int32_t nmc_batch_max_vars(nmc_ctx *ctx) {

@@ -81,9 +81,13 @@ __device__ __forceinline__ uint32_t xs_at(const uint32_t *xs, int byte_off) {
   return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(xs) + byte_off);
 }
 
+// prmt with the top bit of every selector nibble set replicates the sign (bit 7) of byte I of
+// sg into all four result bytes: one instruction per mask.
 template <int I>
 __device__ __forceinline__ uint32_t sign_mask(uint32_t sg) {
-  return (uint32_t)((int32_t)(sg << (24 - 8 * I)) >> 31);
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(sg), "r"(0u), "n"(0x8888 + 0x1111 * I));
+  return r;
 }
 
 // Truth value (32 replicas) of literal id l = 2u + neg from the word vector in shared memory.
@@ -180,7 +184,7 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
         th[j] = 0u;
         if (de[j] > 0) {
           const uint32_t idx = bq_hi * (uint32_t)de[j] + ((bq_lo * (uint32_t)de[j]) >> 8);
-          th[j] = idx < (uint32_t)tab_len ? tab_s[idx] : 0u;
+          th[j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
         }
         need |= th[j] != 0u;
       }
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   __shared__ int item_s;
   __shared__ BatchItem item_b;  // the current item, read from shared memory where needed
   const int rank = CS == 1 ? 0 : (int)cg::this_cluster().block_rank();
-  for (int i = threadIdx.x; i < tab_len; i += blockDim.x) tab_s[i] = tab[i];
+  for (int i = threadIdx.x; i <= tab_len; i += blockDim.x) tab_s[i] = i < tab_len ? tab[i] : 0u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   while (true) {
     if (rank == 0 && threadIdx.x == 0) item_s = atomicAdd(next_item, 1);
@@ -454,7 +458,7 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
       th[j] = 0u;
       if (val > 0) {
         const uint32_t idx = bq_hi * (uint32_t)val + ((bq_lo * (uint32_t)val) >> 8);
-        th[j] = idx < (uint32_t)tab_len ? tab_s[idx] : 0u;
+        th[j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
       }
       need |= th[j] != 0u;
     }
@@ -486,7 +490,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   __shared__ int item_s;
   __shared__ BatchItem item_b;
   const int rank = CS == 1 ? 0 : (int)cg::this_cluster().block_rank();
-  for (int i = threadIdx.x; i < tab_len; i += blockDim.x) tab_s[i] = tab[i];
+  for (int i = threadIdx.x; i <= tab_len; i += blockDim.x) tab_s[i] = i < tab_len ? tab[i] : 0u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tl = lane % TL;                       // lane inside the team
   const int team = threadIdx.x / TL;              // team inside the CTA
@@ -585,7 +589,7 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
                          const uint32_t *tab, int tab_len, int max_n, int device,
                          cudaStream_t st) {
   const int xs_words = max_n + 1;
-  const size_t smem = sizeof(uint32_t) * (((size_t)xs_words + 31) / 32 * 32 + (size_t)tab_len);
+  const size_t smem = sizeof(uint32_t) * (((size_t)xs_words + 31) / 32 * 32 + (size_t)tab_len + 1);
   auto kern = TL == 1 ? ksat_batch_kernel<KQ, CS> : ksat_team_kernel<KQ, CS, (TL > 1 ? TL : 4)>;
   static std::mutex mu;
   static std::map<std::pair<int, size_t>, int> shapes;  // (device, smem) -> resident clusters
@@ -774,7 +778,7 @@ size_t batch_max_vars(int tab_len, int device) {
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
     return 0;
   // dynamic shared memory: table + n+1 words; the static part is under 192 words
-  const long long words = (long long)optin / 4 - tab_len - 32 - 1 - 192;
+  const long long words = (long long)optin / 4 - tab_len - 1 - 32 - 1 - 192;
   return words > 0 ? (size_t)words : 0;
 }
 

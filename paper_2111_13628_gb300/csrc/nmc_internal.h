@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 struct nmc_ctx;
@@ -141,7 +142,40 @@ int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t
 // Records an error message on the context; returns `code`.
 int set_ctx_error(nmc_ctx *ctx, int code, const char *msg);
 
+// A k-SAT instance prepared on the host (checks, colouring, renumbering, occurrence lists),
+// ready to upload. prepare_ksat needs no context or device, so callers can run it on any
+// thread; upload_ksat makes it resident on the context's device (nmc_load_ksat = both).
+struct HostKsat {
+  int code = 0;
+  std::string err;
+  int32_t n = 0, m = 0, K = 0, n_colours = 0, kq = 1, nb = 2, n_occ = 0;
+  std::vector<int32_t> occ, occ_ptr, col_ptr, orig, newid, clits, occ_t, grp_base, cgrp, colour;
+};
+int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t *lits,
+                 HostKsat *out);
+int upload_ksat(nmc_ctx *ctx, HostKsat &h, int32_t *inst_out);
+
 // ---- QAP launchers (qap.cu) ------------------------------------------------------------
+// Arguments of one QAP launch (or, in a batched launch, of one CTA: one block of 32 replicas).
+struct QapArgs {
+  const uint8_t *F, *D;
+  int16_t *perm, *best_perm;
+  long long *energy, *best_energy;
+  const uint32_t *bq;
+  const uint32_t *tab;
+  int32_t tab_len, n, R, t0, t1;
+  uint32_t k0, k1;
+  int init_mode;  // 0: run steps; 1: draw initial states (Fisher-Yates); 2: states given
+  int block;      // batched launches: replica block (32 replicas) this CTA runs; else -1
+};
+
+QapArgs qap_block_args(const QapDevice &I, QapReplicas &Rp, const uint32_t *bq, const uint32_t *tab,
+                       int32_t tab_len, int32_t t0, int32_t t1, uint64_t seed, int block);
+// Runs n_blocks QAP replica blocks (items_dev[b] for CTA b) in one launch; npl = 1..8
+// registers per lane (n <= 32 npl for every item), max_n sizes the shared memory.
+cudaError_t qap_batch(const QapArgs *items_dev, int n_blocks, int npl, int max_n, int tab_len,
+                      cudaStream_t st);
+// (older single-set launchers below) ------------------------------------------------------------
 cudaError_t qap_init_states(const QapDevice &I, QapReplicas &Rp, uint64_t seed,
                             const int16_t *init_dev, cudaStream_t st);
 cudaError_t qap_steps(const QapDevice &I, QapReplicas &Rp, const uint32_t *bq,

@@ -40,40 +40,32 @@ __device__ long long warp_cost(const uint8_t *Fs, const uint8_t *Ds, const uint8
   long long acc = 0;
   for (int i = lane; i < n; i += 32) {
     const int pi = ps[i];
-    for (int j = 0; j < n; ++j) acc += (long long)Fs[i * n + j] * (long long)Ds[pi * n + ps[j]];
+    for (int j = 0; j < n; ++j)
+      acc += (long long)Fs[i * (32 * NPL) + j] * (long long)Ds[pi * n + ps[j]];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
   return acc;
 }
 
-struct QapArgs {
-  const uint8_t *F, *D;
-  int16_t *perm, *best_perm;
-  long long *energy, *best_energy;
-  const uint32_t *bq;
-  const uint32_t *tab;
-  int32_t tab_len, n, R, t0, t1;
-  uint32_t k0, k1;
-  int init_mode;  // 0: run steps; 1: draw initial states (Fisher-Yates); 2: states given
-};
-
 template <int NPL>
-__global__ void __launch_bounds__(kQapWarps * 32) qap_kernel(QapArgs a) {
+__device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
   extern __shared__ uint32_t smem[];
   const int n = a.n;
+  constexpr int LDF = 32 * NPL;  // F rows padded with zeros to the lanes' reach
   uint32_t *tab_s = smem;
   uint8_t *Fs = (uint8_t *)(smem + ((a.tab_len + 31) & ~31));
-  uint8_t *Ds = Fs + ((n * n + 15) & ~15);
+  uint8_t *Ds = Fs + ((n * LDF + 15) & ~15);
   uint8_t *pw_all = Ds + ((n * n + 15) & ~15);  // one n-byte row per warp (permutation copy)
   for (int i = threadIdx.x; i < a.tab_len; i += blockDim.x) tab_s[i] = a.tab[i];
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-    Fs[i] = a.F[i];
-    Ds[i] = a.D[i];
+  for (int i = threadIdx.x; i < n * LDF; i += blockDim.x) {
+    const int row = i / LDF, col = i % LDF;
+    Fs[i] = col < n ? a.F[row * n + col] : (uint8_t)0;
   }
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) Ds[i] = a.D[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int r = blockIdx.x * kQapWarps + warp;
+  const int r = block * kQapWarps + warp;
   if (r >= a.R) return;
   uint8_t *pw = pw_all + warp * ((n + 15) & ~15);
   int16_t *gp = a.perm + (size_t)r * n;
@@ -149,19 +141,20 @@ __global__ void __launch_bounds__(kQapWarps * 32) qap_kernel(QapArgs a) {
           const int ss = __shfl_sync(0xFFFFFFFFu, fs, j);
           const int pr = __shfl_sync(0xFFFFFFFFu, pick<NPL>(p, rr >> 5), rr & 31);
           const int ps = __shfl_sync(0xFFFFFFFFu, pick<NPL>(p, ss >> 5), ss & 31);
-          const uint8_t *Fr = Fs + rr * n, *Fsr = Fs + ss * n;
+          const uint8_t *Fr = Fs + rr * LDF, *Fsr = Fs + ss * LDF;
           const uint8_t *Dr = Ds + pr * n, *Dsr = Ds + ps * n;
+          // sum over every k (padded columns of F are zero); the k = r and k = s terms sum to
+          // -2 F_rs D_{p(r)p(s)} by symmetry and are added back below
           int acc = 0;
 #pragma unroll
           for (int i = 0; i < NPL; ++i) {
             const int k = lane + 32 * i;
-            if (k < n && k != rr && k != ss) {
-              const int pk = p[i];
-              acc += ((int)Fr[k] - (int)Fsr[k]) * ((int)Dsr[pk] - (int)Dr[pk]);
-            }
+            const int pk = p[i];
+            acc += ((int)Fr[k] - (int)Fsr[k]) * ((int)Dsr[pk] - (int)Dr[pk]);
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+          acc += 2 * (int)Fr[ss] * (int)Dr[ps];
           const long long d = 2LL * acc;
           bool ok = d <= 0;
           if (!ok) {
@@ -199,10 +192,22 @@ __global__ void __launch_bounds__(kQapWarps * 32) qap_kernel(QapArgs a) {
 }
 
 template <int NPL>
+__global__ void __launch_bounds__(kQapWarps * 32) qap_kernel(QapArgs a) {
+  qap_body<NPL>(a, blockIdx.x);
+}
+
+// Batched QAP: CTA b runs replica block items[b].block of the replica set items[b] describes.
+template <int NPL>
+__global__ void __launch_bounds__(kQapWarps * 32) qap_batch_kernel(const QapArgs *items) {
+  const QapArgs a = items[blockIdx.x];
+  qap_body<NPL>(a, a.block);
+}
+
+template <int NPL>
 cudaError_t launch_qap(const QapArgs &a, cudaStream_t st) {
   const int n = a.n;
-  const size_t smem = sizeof(uint32_t) * ((a.tab_len + 31) & ~31) + 2 * (size_t)((n * n + 15) & ~15) +
-                      (size_t)kQapWarps * ((n + 15) & ~15);
+  const size_t smem = sizeof(uint32_t) * ((a.tab_len + 31) & ~31) + (size_t)((n * 32 * NPL + 15) & ~15) +
+                      (size_t)((n * n + 15) & ~15) + (size_t)kQapWarps * ((n + 15) & ~15);
   auto kern = qap_kernel<NPL>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -212,10 +217,16 @@ cudaError_t launch_qap(const QapArgs &a, cudaStream_t st) {
 }
 
 cudaError_t dispatch_qap(const QapArgs &a, cudaStream_t st) {
-  if (a.n <= 32) return launch_qap<1>(a, st);
-  if (a.n <= 64) return launch_qap<2>(a, st);
-  if (a.n <= 128) return launch_qap<4>(a, st);
-  return launch_qap<8>(a, st);
+  switch ((a.n + 31) / 32) {
+    case 1: return launch_qap<1>(a, st);
+    case 2: return launch_qap<2>(a, st);
+    case 3: return launch_qap<3>(a, st);
+    case 4: return launch_qap<4>(a, st);
+    case 5: return launch_qap<5>(a, st);
+    case 6: return launch_qap<6>(a, st);
+    case 7: return launch_qap<7>(a, st);
+    default: return launch_qap<8>(a, st);
+  }
 }
 
 __global__ void qap_unpack_kernel(const int16_t *perm, const int16_t *best_perm,
@@ -251,10 +262,54 @@ QapArgs make_args(const QapDevice &I, QapReplicas &Rp, uint64_t seed) {
   a.k0 = (uint32_t)seed;
   a.k1 = (uint32_t)(seed >> 32);
   a.init_mode = 0;
+  a.block = -1;
   return a;
 }
 
+size_t qap_smem(int n, int npl, int tab_len) {
+  return sizeof(uint32_t) * ((tab_len + 31) & ~31) + (size_t)((n * 32 * npl + 15) & ~15) +
+         (size_t)((n * n + 15) & ~15) + (size_t)kQapWarps * ((n + 15) & ~15);
+}
+
+template <int NPL>
+cudaError_t launch_qap_batch(const QapArgs *items_dev, int n_blocks, int max_n, int tab_len,
+                             cudaStream_t st) {
+  const size_t smem = qap_smem(max_n, NPL, tab_len);
+  auto kern = qap_batch_kernel<NPL>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  kern<<<n_blocks, kQapWarps * 32, smem, st>>>(items_dev);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+QapArgs qap_block_args(const QapDevice &I, QapReplicas &Rp, const uint32_t *bq, const uint32_t *tab,
+                       int32_t tab_len, int32_t t0, int32_t t1, uint64_t seed, int block) {
+  QapArgs a = make_args(I, Rp, seed);
+  a.bq = bq;
+  a.tab = tab;
+  a.tab_len = tab_len;
+  a.t0 = t0;
+  a.t1 = t1;
+  a.block = block;
+  return a;
+}
+
+cudaError_t qap_batch(const QapArgs *items_dev, int n_blocks, int npl, int max_n, int tab_len,
+                      cudaStream_t st) {
+  if (n_blocks <= 0) return cudaSuccess;
+  switch (npl) {
+    case 1: return launch_qap_batch<1>(items_dev, n_blocks, max_n, tab_len, st);
+    case 2: return launch_qap_batch<2>(items_dev, n_blocks, max_n, tab_len, st);
+    case 3: return launch_qap_batch<3>(items_dev, n_blocks, max_n, tab_len, st);
+    case 4: return launch_qap_batch<4>(items_dev, n_blocks, max_n, tab_len, st);
+    case 5: return launch_qap_batch<5>(items_dev, n_blocks, max_n, tab_len, st);
+    case 6: return launch_qap_batch<6>(items_dev, n_blocks, max_n, tab_len, st);
+    case 7: return launch_qap_batch<7>(items_dev, n_blocks, max_n, tab_len, st);
+    default: return launch_qap_batch<8>(items_dev, n_blocks, max_n, tab_len, st);
+  }
+}
 
 cudaError_t qap_init_states(const QapDevice &I, QapReplicas &Rp, uint64_t seed,
                             const int16_t *init_dev, cudaStream_t st) {

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "nmc.h"
+#include "nmc_internal.h"
 
 namespace {
 
@@ -36,7 +37,8 @@ struct Request {
   int kind = 0;
   int32_t n = 0, m = 0, kmax = 0, n_steps = 0, replicas = 0;
   uint64_t seed = 0;
-  std::vector<int32_t> lits, F, D;
+  std::vector<int32_t> F, D;
+  nmc::HostKsat prep;  // k-SAT instance prepared on the submitting thread
   std::vector<float> beta, base, factor;  // full profile, or the factored form
   // device residency
   int32_t inst = -1, rs = -1;
@@ -98,8 +100,7 @@ void finish(nmc_server *s, const std::shared_ptr<Request> &r, int status, const 
   r->status = status;
   r->error = msg;
   r->t_done = Clock::now();
-  r->lits.clear();
-  r->lits.shrink_to_fit();
+  r->prep = nmc::HostKsat();
   r->beta.clear();
   r->beta.shrink_to_fit();
   r->base.clear();
@@ -110,9 +111,10 @@ void finish(nmc_server *s, const std::shared_ptr<Request> &r, int status, const 
 bool admit(nmc_server *s, const std::shared_ptr<Request> &r) {
   nmc_ctx *c = s->ctx;
   int rc;
-  if (r->kind == NMC_KIND_KSAT)
-    rc = nmc_load_ksat(c, r->n, r->m, r->kmax, r->lits.data(), &r->inst);
-  else
+  if (r->kind == NMC_KIND_KSAT) {
+    rc = nmc::upload_ksat(c, r->prep, &r->inst);
+    r->prep = nmc::HostKsat();
+  } else
     rc = nmc_load_qap(c, r->n, r->F.data(), r->D.data(), &r->inst);
   if (rc == NMC_OK)
     rc = r->beta.empty() ? nmc_set_schedule_factored(c, r->inst, r->n_steps, r->base.data(), r->factor.data())
@@ -170,20 +172,27 @@ void worker_loop(nmc_server *s) {
     if (s->active.empty()) continue;
     // one tick: equal-work slices, k-SAT in one batched launch, QAP after it
     const auto t0 = Clock::now();
-    std::vector<int32_t> rs, a, b;
+    std::vector<int32_t> rs, a, b, qrs, qa, qb;
     int64_t tick_attempts = 0;
     int rc = NMC_OK;
     for (auto &r : s->active) {
       if (r->cancelled) continue;
-      const int64_t per_sweep = r->kind == NMC_KIND_KSAT
-                                    ? static_cast<int64_t>(r->n) * ((r->replicas + 31) / 32)
-                                    : static_cast<int64_t>(r->n) * r->n * r->replicas / 32;
+      // work of one sweep / step in occurrence-word updates (one clause occurrence of one
+      // variable for 32 replicas); a QAP swap attempt on one replica costs about n/3 of them
+      const int64_t per_sweep =
+          r->kind == NMC_KIND_KSAT
+              ? static_cast<int64_t>(r->m) * r->kmax * ((r->replicas + 31) / 32)
+              : static_cast<int64_t>(r->n) * r->n * r->replicas / 3;
       const int64_t sweeps = std::max<int64_t>(1, slice / std::max<int64_t>(1, per_sweep));
       const int32_t t1 = static_cast<int32_t>(std::min<int64_t>(r->n_steps, r->t + sweeps));
       if (r->kind == NMC_KIND_KSAT && r->batchable) {
         rs.push_back(r->rs);
         a.push_back(r->t);
         b.push_back(t1);
+      } else if (r->kind == NMC_KIND_QAP) {
+        qrs.push_back(r->rs);
+        qa.push_back(r->t);
+        qb.push_back(t1);
       } else if (rc == NMC_OK) {
         rc = nmc_replicas_run(s->ctx, r->rs, r->t, t1);
       }
@@ -192,6 +201,9 @@ void worker_loop(nmc_server *s) {
     }
     if (rc == NMC_OK && !rs.empty())
       rc = nmc_batch_run(s->ctx, static_cast<int32_t>(rs.size()), rs.data(), a.data(), b.data());
+    if (rc == NMC_OK && !qrs.empty())
+      rc = nmc_qap_batch_run(s->ctx, static_cast<int32_t>(qrs.size()), qrs.data(), qa.data(),
+                             qb.data());
     if (rc == NMC_OK) rc = nmc_sync(s->ctx);
     const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
     if (rc != NMC_OK) {
@@ -297,14 +309,10 @@ int nmc_server_submit_ksat(nmc_server *s, int32_t n_vars, int32_t n_clauses, int
   r->replicas = replicas;
   r->seed = seed;
   if (!copy_schedule(*r, sched, n_vars)) return NMC_EINVAL;
-  r->lits.assign(lits, lits + static_cast<size_t>(n_clauses) * k_max);
-  std::vector<int32_t> deg(static_cast<size_t>(n_vars) + 1, 0);
-  int32_t dmax = 0;
-  for (int32_t l : r->lits) {
-    const int64_t v = l > 0 ? l : -static_cast<int64_t>(l);
-    if (l != 0 && v <= n_vars) dmax = std::max(dmax, ++deg[v - 1]);
-  }
-  r->batchable = dmax <= 127 && n_vars <= s->batch_max_vars;
+  // host-side build (checks, colouring, lists) here, on the caller's thread; a malformed
+  // formula is reported by the request's status, as any admission failure
+  nmc::prepare_ksat(n_vars, n_clauses, k_max, lits, &r->prep);
+  r->batchable = r->prep.code == NMC_OK && r->prep.nb <= 7 && n_vars <= s->batch_max_vars;
   return submit(s, r, req_out);
 }
 

@@ -87,3 +87,28 @@ def test_full_size_sampled_replicas(ctx):
     _same(got, O.qap_anneal(F, D, beta, 0, T, 20_000, replica_ids=ids), ids)
     for r in range(0, R, 411):
         assert got["energies"][r] == O.qap_cost(F, D, got["states"][r])
+
+
+def test_batched_qap_matches_single_sets_and_oracle(ctx):
+    specs = [(20, 40, 9), (33, 70, 6), (64, 33, 5), (100, 64, 4), (200, 40, 3), (256, 35, 2)]
+    sets, data = [], []
+    for i, (n, R, T) in enumerate(specs):
+        F, D = W.random_qap(n, 900 + i)
+        beta = W.beta_scaled_linear(n, T, 0.01, 1.0, 0.5, 1.5, 910 + i)
+        inst = ctx.load_qap(F, D)
+        ctx.set_schedule(inst, beta)
+        a = ctx.replicas_create(inst, R, seed=920 + i)
+        b = ctx.replicas_create(inst, R, seed=920 + i)
+        sets.append((inst, a, b))
+        data.append((F, D, beta, R, T, 920 + i))
+    ctx.qap_batch_run([a for _, a, _ in sets], 0, [d[4] for d in data])
+    for (inst, a, b), (F, D, beta, R, T, seed) in zip(sets, data):
+        ctx.replicas_run(b, 0, T)
+        ga, gb = ctx.replicas_read(a), ctx.replicas_read(b)
+        for key in ("states", "energies", "best_energies", "best_states"):
+            assert np.array_equal(ga[key], gb[key]), key
+        ids = np.array([0, R - 1], dtype=np.int32)
+        _same(ga, O.qap_anneal(F, D, beta, 0, T, seed, replica_ids=ids), ids)
+        ctx.replicas_destroy(a)
+        ctx.replicas_destroy(b)
+        ctx.unload(inst)
