@@ -130,6 +130,12 @@ int nmc_replicas_create(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t s
 /* Re-initialises an existing replica set in place (no allocation): new seed, new initial
  * states (init_states as in nmc_replicas_create), energies recomputed, best-so-far reset. */
 int nmc_replicas_reset(nmc_ctx *ctx, int32_t rs, uint64_t seed, const void *init_states);
+/* Checkpoint resume: sets a replica set's current states and best-so-far states from host
+ * buffers in the layout nmc_replicas_read writes (in->states and in->best_states required; the
+ * energy fields are ignored and recomputed from the states). Reading a set after sweeps
+ * [0, t1) and restoring the result into a fresh set of the same instance and seed continues
+ * the chains exactly: running [t1, t2) there equals running [0, t2) in one set. */
+int nmc_replicas_restore(nmc_ctx *ctx, int32_t rs, const nmc_result *in);
 /* Frees a replica set. */
 int nmc_replicas_destroy(nmc_ctx *ctx, int32_t rs);
 /*

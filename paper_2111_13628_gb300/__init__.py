@@ -51,7 +51,7 @@ _lib = None
 # Exported C-ABI symbols (every function declared in include/nmc.h).
 SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_ksat",
            "nmc_load_qap", "nmc_unload", "nmc_ksat_colouring", "nmc_set_schedule",
-           "nmc_set_schedule_device", "nmc_set_schedule_factored", "nmc_replicas_create", "nmc_replicas_reset", "nmc_replicas_destroy",
+           "nmc_set_schedule_device", "nmc_set_schedule_factored", "nmc_replicas_create", "nmc_replicas_reset", "nmc_replicas_restore", "nmc_replicas_destroy",
            "nmc_replicas_run", "nmc_replicas_read", "nmc_replicas_read_device", "nmc_anneal",
            "nmc_threshold_table", "nmc_selftest_wait_timeout", "nmc_batch_run",
            "nmc_batch_max_vars", "nmc_server_create", "nmc_server_destroy",
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
             "nmc_set_schedule_factored": ([P, i32, i32, P, P], C.c_int),
             "nmc_replicas_create": ([P, i32, i32, u64, P, P], C.c_int),
             "nmc_replicas_reset": ([P, i32, u64, P], C.c_int),
+            "nmc_replicas_restore": ([P, i32, P], C.c_int),
             "nmc_replicas_destroy": ([P, i32], C.c_int),
             "nmc_replicas_run": ([P, i32, i32, i32], C.c_int),
             "nmc_replicas_read": ([P, i32, P], C.c_int),
@@ -287,6 +288,17 @@ class Context:
                 raise ValueError("init must be [replicas, n_units]")
         self._check(self._lib.nmc_replicas_reset(self._h, int(rs), int(seed) & (2**64 - 1),
                                                  _ptr(init)))
+
+    def replicas_restore(self, rs: int, checkpoint: dict):
+        """Restores states and best states saved by replicas_read (checkpoint resume)."""
+        inst, R = self._rs[rs]
+        dt = np.uint8 if self._kinds[inst] == KIND_KSAT else np.int16
+        st = np.ascontiguousarray(checkpoint["states"], dtype=dt)
+        bs = np.ascontiguousarray(checkpoint["best_states"], dtype=dt)
+        if st.shape != (R, self._units[inst]) or bs.shape != st.shape:
+            raise ValueError("checkpoint arrays must be [replicas, n_units]")
+        res = Result(_ptr(st), None, None, _ptr(bs))
+        self._check(self._lib.nmc_replicas_restore(self._h, int(rs), C.byref(res)))
 
     def replicas_destroy(self, rs: int):
         self._check(self._lib.nmc_replicas_destroy(self._h, int(rs)))

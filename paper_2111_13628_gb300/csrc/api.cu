@@ -891,6 +891,41 @@ int nmc_replicas_reset(nmc_ctx *ctx, int32_t rs, uint64_t seed, const void *init
   return init_replicas(ctx, *I, *S, init_states);
 }
 
+int nmc_replicas_restore(nmc_ctx *ctx, int32_t rs, const nmc_result *in) {
+  if (!ctx) return NMC_EINVAL;
+  if (!in || !in->states || !in->best_states)
+    return fail(ctx, NMC_EINVAL, "restore needs states and best_states");
+  ReplicaSet *S = find_set(ctx, rs);
+  if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
+  Instance *I = find_inst(ctx, S->inst);
+  if (!I) return fail(ctx, NMC_ESTATE, "instance was unloaded");
+  int rc = check_init(ctx, *I, S->R, in->states);
+  if (rc == NMC_OK) rc = check_init(ctx, *I, S->R, in->best_states);
+  if (rc != NMC_OK) return rc;
+  DeviceGuard g(ctx->device);
+  const size_t bytes = static_cast<size_t>(S->R) * I->n_units * (I->kind == NMC_KIND_KSAT ? 1 : 2);
+  void *dev = nullptr;
+  NMC_CUDA(cudaMallocAsync(&dev, 2 * bytes, ctx->stream), "allocate restore staging");
+  char *bdev = static_cast<char *>(dev), *sdev = bdev + bytes;
+  cudaError_t e = cudaMemcpyAsync(bdev, in->best_states, bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sdev, in->states, bytes, cudaMemcpyHostToDevice, ctx->stream);
+  // the best states first (their energies become the best energies), then the current states
+  if (I->kind == NMC_KIND_KSAT) {
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->ks.imp, 0, sizeof(uint32_t) * S->ks.W, ctx->stream);
+    if (e == cudaSuccess) e = ksat_init_states(I->ks, S->ks, S->seed, reinterpret_cast<uint8_t *>(bdev), ctx->stream, true);
+    if (e == cudaSuccess) e = ksat_energies(I->ks, S->ks, ctx->stream, true);
+    if (e == cudaSuccess) e = ksat_init_states(I->ks, S->ks, S->seed, reinterpret_cast<uint8_t *>(sdev), ctx->stream, false);
+    if (e == cudaSuccess) e = ksat_energies(I->ks, S->ks, ctx->stream, false);
+  } else {
+    if (e == cudaSuccess) e = qap_init_states(I->qp, S->qp, S->seed, reinterpret_cast<int16_t *>(bdev), ctx->stream, true);
+    if (e == cudaSuccess) e = qap_init_states(I->qp, S->qp, S->seed, reinterpret_cast<int16_t *>(sdev), ctx->stream, false);
+  }
+  cudaFreeAsync(dev, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "restore replicas");
+  return NMC_OK;
+}
+
 int nmc_replicas_destroy(nmc_ctx *ctx, int32_t rs) {
   if (!ctx) return NMC_EINVAL;
   ReplicaSet *S = find_set(ctx, rs);

@@ -597,7 +597,7 @@ __global__ void wait_selftest_kernel(GridBarrier *gb, unsigned expected,
 // ---- initial states, energies, unpacking ---------------------------------------------------
 __global__ void ksat_init_kernel(uint32_t *S, uint32_t *best, const int32_t *orig,
                                  const uint8_t *init, int32_t n, int32_t W, int32_t R,
-                                 uint32_t k0, uint32_t k1) {
+                                 uint32_t k0, uint32_t k1, bool write_best) {
   const long long total = (long long)(n + 1) * W;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -623,7 +623,7 @@ __global__ void ksat_init_kernel(uint32_t *S, uint32_t *best, const int32_t *ori
     }
     S[(size_t)(2 * v) * W + w] = x;
     S[(size_t)(2 * v + 1) * W + w] = ~x;
-    best[(size_t)v * W + w] = x;
+    if (write_best) best[(size_t)v * W + w] = x;
   }
 }
 
@@ -805,15 +805,15 @@ int grid_for(long long work, int threads) {
 void set_sweep_shape(int warps_per_variable) { g_fast_p = warps_per_variable; }
 
 cudaError_t ksat_init_states(const KsatDevice &I, KsatReplicas &Rp, uint64_t seed,
-                             const uint8_t *init_dev, cudaStream_t st) {
+                             const uint8_t *init_dev, cudaStream_t st, bool set_best) {
   const long long work = (long long)(I.n + 1) * Rp.W;
   ksat_init_kernel<<<grid_for(work, 256), 256, 0, st>>>(Rp.S, Rp.best, I.orig, init_dev, I.n,
                                                         Rp.W, Rp.R, (uint32_t)seed,
-                                                        (uint32_t)(seed >> 32));
+                                                        (uint32_t)(seed >> 32), set_best);
   return cudaGetLastError();
 }
 
-cudaError_t ksat_energies(const KsatDevice &I, KsatReplicas &Rp, cudaStream_t st) {
+cudaError_t ksat_energies(const KsatDevice &I, KsatReplicas &Rp, cudaStream_t st, bool set_best) {
   cudaError_t err = cudaMemsetAsync(Rp.energy, 0, sizeof(int32_t) * 32 * Rp.W, st);
   if (err != cudaSuccess) return err;
   if (I.m > 0) {
@@ -824,6 +824,7 @@ cudaError_t ksat_energies(const KsatDevice &I, KsatReplicas &Rp, cudaStream_t st
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
+  if (!set_best) return cudaSuccess;
   return cudaMemcpyAsync(Rp.best_energy, Rp.energy, sizeof(int32_t) * 32 * Rp.W,
                          cudaMemcpyDeviceToDevice, st);
 }

@@ -92,9 +92,12 @@ struct BatchItem {
 };
 
 // ---- k-SAT launchers (ksat.cu); all asynchronous on `st` -------------------------------
+// Initial states (Philox, or init_dev [R][n] 0/1 bytes) and, with set_best, best = state.
 cudaError_t ksat_init_states(const KsatDevice &I, KsatReplicas &Rp, uint64_t seed,
-                             const uint8_t *init_dev, cudaStream_t st);
-cudaError_t ksat_energies(const KsatDevice &I, KsatReplicas &Rp, cudaStream_t st);
+                             const uint8_t *init_dev, cudaStream_t st, bool set_best = true);
+// Energies from scratch and, with set_best, best energies = energies.
+cudaError_t ksat_energies(const KsatDevice &I, KsatReplicas &Rp, cudaStream_t st,
+                          bool set_best = true);
 cudaError_t ksat_sweeps(const KsatDevice &I, KsatReplicas &Rp, const uint32_t *bq,
                         const uint32_t *tab, int32_t tab_len, int32_t t0, int32_t t1,
                         uint64_t seed, int device, cudaStream_t st);
@@ -176,8 +179,10 @@ QapArgs qap_block_args(const QapDevice &I, QapReplicas &Rp, const uint32_t *bq, 
 cudaError_t qap_batch(const QapArgs *items_dev, int n_blocks, int npl, int max_n, int tab_len,
                       cudaStream_t st);
 // (older single-set launchers below) ------------------------------------------------------------
+// Initial permutations (Fisher-Yates from Philox, or init_dev [R][n]) with their costs; with
+// set_best the best-so-far is set to them too.
 cudaError_t qap_init_states(const QapDevice &I, QapReplicas &Rp, uint64_t seed,
-                            const int16_t *init_dev, cudaStream_t st);
+                            const int16_t *init_dev, cudaStream_t st, bool set_best = true);
 cudaError_t qap_steps(const QapDevice &I, QapReplicas &Rp, const uint32_t *bq,
                       const uint32_t *tab, int32_t tab_len, int32_t t0, int32_t t1,
                       uint64_t seed, cudaStream_t st);

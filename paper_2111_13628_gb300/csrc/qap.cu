@@ -98,13 +98,14 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
   }
   if (a.init_mode != 0) {
     const long long c = warp_cost<NPL>(Fs, Ds, pw, n, lane);
+    const bool set_best = a.init_mode != 3;
     for (int k = lane; k < n; k += 32) {
       gp[k] = (int16_t)pw[k];
-      a.best_perm[(size_t)r * n + k] = (int16_t)pw[k];
+      if (set_best) a.best_perm[(size_t)r * n + k] = (int16_t)pw[k];
     }
     if (lane == 0) {
       a.energy[r] = c;
-      a.best_energy[r] = c;
+      if (set_best) a.best_energy[r] = c;
     }
     return;
   }
@@ -312,13 +313,13 @@ cudaError_t qap_batch(const QapArgs *items_dev, int n_blocks, int npl, int max_n
 }
 
 cudaError_t qap_init_states(const QapDevice &I, QapReplicas &Rp, uint64_t seed,
-                            const int16_t *init_dev, cudaStream_t st) {
+                            const int16_t *init_dev, cudaStream_t st, bool set_best) {
   QapArgs a = make_args(I, Rp, seed);
   if (init_dev) {
     cudaError_t err = cudaMemcpyAsync(Rp.perm, init_dev, sizeof(int16_t) * (size_t)Rp.R * I.n,
                                       cudaMemcpyDeviceToDevice, st);
     if (err != cudaSuccess) return err;
-    a.init_mode = 2;
+    a.init_mode = set_best ? 2 : 3;
   } else {
     a.init_mode = 1;
   }

@@ -112,3 +112,28 @@ def test_cluster_shapes_agree(ctx, monkeypatch, ctas, lanes):
     ctx.replicas_destroy(a)
     ctx.replicas_destroy(b)
     ctx.unload(inst)
+
+
+def test_batch_mixes_occurrence_widths_and_segments(ctx):
+    """Sets with k <= 4 and k > 4 in one call (two launches), each with its own sweep range."""
+    specs = [(200, 9.6, 4, 64, 7, 19), (150, 2.0, 6, 40, 0, 12), (300, 4.2, 3, 33, 3, 3),
+             (90, 1.2, 8, 96, 5, 30)]
+    sets, data = [], []
+    for i, (n, alpha, k, R, t0, t1) in enumerate(specs):
+        lits = W.random_ksat(n, alpha, k, 60 + i)
+        beta = W.beta_inhomogeneous_linear(n, 30, 0.5, 4.0, 0.3, 0.5, 70 + i)
+        inst = ctx.load_ksat(lits, n)
+        ctx.set_schedule(inst, beta)
+        rs = ctx.replicas_create(inst, R, seed=80 + i)
+        sets.append((inst, rs))
+        data.append((lits, n, beta, R, t0, t1, 80 + i))
+    ctx.batch_run([rs for _, rs in sets], [d[4] for d in data], [d[5] for d in data])
+    for (inst, rs), (lits, n, beta, R, t0, t1, seed) in zip(sets, data):
+        got = ctx.replicas_read(rs)
+        init = O.ksat_anneal(lits, n, beta, 0, 0, seed, replicas=R)
+        want = O.ksat_anneal(lits, n, beta, t0, t1, seed, replicas=R, init=init["states"],
+                             init_best=init["best_states"], init_best_energy=init["best_energies"])
+        for key in KEYS:
+            assert np.array_equal(got[key], want[key]), (n, key)
+        ctx.replicas_destroy(rs)
+        ctx.unload(inst)

@@ -243,3 +243,24 @@ def test_factored_schedule_equals_expanded(ctx):
     got = ctx.anneal(inst, R, 0, T, seed=33)
     ctx.unload(inst)
     _same(got, O.ksat_anneal(lits, n, beta, 0, T, 33, replicas=R))
+
+
+def test_checkpoint_restore_continues_exactly(ctx):
+    wl = W.workload_ksat_small(50)
+    lits, n, beta = wl["lits"], wl["n_vars"], wl["beta"]
+    inst = ctx.load_ksat(lits, n)
+    ctx.set_schedule(inst, beta)
+    a = ctx.replicas_create(inst, 70, seed=5)
+    ctx.replicas_run(a, 0, 20)
+    ckpt = ctx.replicas_read(a)
+    ctx.replicas_destroy(a)
+    b = ctx.replicas_create(inst, 70, seed=5)
+    ctx.replicas_restore(b, ckpt)
+    mid = ctx.replicas_read(b)
+    for key in KEYS:
+        assert np.array_equal(mid[key], ckpt[key]), key
+    ctx.replicas_run(b, 20, 50)
+    got = ctx.replicas_read(b)
+    ctx.replicas_destroy(b)
+    ctx.unload(inst)
+    _same(got, O.ksat_anneal(lits, n, beta, 0, 50, 5, replicas=70))

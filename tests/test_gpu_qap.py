@@ -112,3 +112,22 @@ def test_batched_qap_matches_single_sets_and_oracle(ctx):
         ctx.replicas_destroy(a)
         ctx.replicas_destroy(b)
         ctx.unload(inst)
+
+
+def test_checkpoint_restore_continues_exactly(ctx):
+    n, R, T = 45, 40, 20
+    F, D = W.random_qap(n, 77)
+    beta = W.beta_scaled_linear(n, T, 0.01, 1.0, 0.5, 1.5, 78)
+    inst = ctx.load_qap(F, D)
+    ctx.set_schedule(inst, beta)
+    a = ctx.replicas_create(inst, R, seed=79)
+    ctx.replicas_run(a, 0, 8)
+    ckpt = ctx.replicas_read(a)
+    ctx.replicas_destroy(a)
+    b = ctx.replicas_create(inst, R, seed=79)
+    ctx.replicas_restore(b, ckpt)
+    ctx.replicas_run(b, 8, T)
+    got = ctx.replicas_read(b)
+    ctx.replicas_destroy(b)
+    ctx.unload(inst)
+    _same(got, O.qap_anneal(F, D, beta, 0, T, 79, replicas=R))
