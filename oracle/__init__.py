@@ -61,6 +61,9 @@ def _load():
             lib.orc_ksat_anneal.argtypes = [i32, i32, i32, P, i32, P, i32, P, i32, i32, u64, P, P,
                                             P, i32, P, P, P, P]
             lib.orc_ksat_anneal.restype = C.c_int
+            lib.orc_ksat_pt_anneal.argtypes = [i32, i32, i32, P, i32, P, i32, P, P, i32, i32, i32,
+                                               u64, P, P, P, P, P, P, P]
+            lib.orc_ksat_pt_anneal.restype = C.c_int
             lib.orc_qap_cost.argtypes = [i32, P, P, P]
             lib.orc_qap_cost.restype = i64
             lib.orc_qap_swap_delta.argtypes = [i32, P, P, P, i32, i32]
@@ -84,6 +87,7 @@ TAG_KSAT_INIT = 0x4B494E49
 TAG_KSAT_SWEEP = 0x4B535750
 TAG_QAP_INIT = 0x51494E49
 TAG_QAP_STEP = 0x51535450
+TAG_PT_SWAP = 0x50545357
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:
@@ -170,6 +174,32 @@ def ksat_anneal(lits, n_vars, beta, t0, t1, seed, replicas=None, replica_ids=Non
     if rc != 0:
         raise ValueError("orc_ksat_anneal rejected its arguments")
     return dict(states=out_s, energies=e, best_energies=be, best_states=out_b)
+
+
+def ksat_pt_anneal(lits, n_vars, beta, ladder, t0, t1, sweeps_per_round, seed, slots=None,
+                   init=None, init_best=None, init_best_energy=None):
+    """Replica exchange: R = len(ladder) replicas, replica r at slot slots[r] (default r) with
+    temperature multiplier ladder[slot]; exchange rounds after every sweeps_per_round sweeps.
+    Returns dict(states, energies, best_energies, best_states, slots)."""
+    lits, m, k = _cnf(lits)
+    beta = np.ascontiguousarray(beta, dtype=np.float32)
+    ladder = np.ascontiguousarray(ladder, dtype=np.float32)
+    R = ladder.shape[0]
+    slots = np.arange(R, dtype=np.int32) if slots is None else np.array(slots, dtype=np.int32)
+    init = _c(init, np.uint8)
+    init_best = _c(init_best, np.uint8)
+    init_best_energy = _c(init_best_energy, np.int64)
+    out_s = np.zeros((R, n_vars), dtype=np.uint8)
+    out_b = np.zeros((R, n_vars), dtype=np.uint8)
+    e = np.zeros(R, dtype=np.int64)
+    be = np.zeros(R, dtype=np.int64)
+    rc = _load().orc_ksat_pt_anneal(n_vars, m, k, _p(lits), beta.shape[1], _p(beta), R, _p(ladder),
+                                    _p(slots), int(t0), int(t1), int(sweeps_per_round),
+                                    int(seed) & (2**64 - 1), _p(init), _p(init_best),
+                                    _p(init_best_energy), _p(out_s), _p(e), _p(be), _p(out_b))
+    if rc != 0:
+        raise ValueError("orc_ksat_pt_anneal rejected its arguments")
+    return dict(states=out_s, energies=e, best_energies=be, best_states=out_b, slots=slots)
 
 
 def qap_cost(F, D, p) -> int:

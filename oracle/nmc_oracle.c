@@ -26,6 +26,14 @@
  *    idx = (bq*dE) >> 8, accept iff idx < L and u < Tab[idx], with
  *    Tab[j] = min(2^32-1, floor(2^32 exp(-j/256))) and L the first j with Tab[j] = 0.
  *  Best-so-far: starts at the initial state, replaced after a full sweep on strictly lower E.
+ *  Replica exchange (App. "Adaptive Parallel Tempering": swap probability
+ *    min{1, exp[(beta_i - beta_j)(E_i - E_j)]} for replicas at adjacent temperatures): replica r
+ *    sits at ladder slot s(r) with Q16 temperature lq[s]; its moves use
+ *    min(2^32-1, (lq[s(r)] * bq_v[t]) >> 16). After every S sweeps (sweep t with (t+1) % S == 0,
+ *    round q = (t+1)/S - 1) the pairs of adjacent slots (k, k+1) with k = q mod 2, k+2, ... try to
+ *    exchange their replicas a (at k) and b (at k+1): d = (lq[k] - lq[k+1]) (E_a - E_b) accepts
+ *    when d >= 0, else iff ((-d) >> 8) < L and u < Tab[(-d) >> 8] for u = word 0 of the Philox
+ *    block for counter (k, q, 0, TAG_PT_SWAP).
  *  QAP (Sec. "Quadratic Assignment Problems", Koopmans-Beckmann form without the placement
  *    term): C(p) = sum_ij F_ij D_{p(i)p(j)}, F and D symmetric with zero diagonal. One step is
  *    n swap attempts; attempt a of step t draws Philox counter (a, t, r, TAG_QAP_STEP):
@@ -42,6 +50,7 @@
 #define ORC_TAG_KSAT_SWEEP 0x4B535750u /* "KSWP" */
 #define ORC_TAG_QAP_INIT 0x51494E49u   /* "QINI" */
 #define ORC_TAG_QAP_STEP 0x51535450u   /* "QSTP" */
+#define ORC_TAG_PT_SWAP 0x50545357u    /* "PTSW" */
 #define ORC_TAB_CAP 8192
 
 /* ---------------------------------------------------------------------------------------
@@ -408,6 +417,126 @@ int orc_ksat_anneal(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, int
   free(jobs);
   free(th);
   free(ids);
+  free(bq);
+  free(order);
+  free(colour);
+  cnf_free(&f);
+  return 0;
+}
+
+
+/* ---------------------------------------------------------------------------------------
+ * k-SAT with replica exchange (single-threaded: the exchange rounds couple the replicas).
+ * ------------------------------------------------------------------------------------- */
+/*
+ * Runs sweeps t0..t1-1 of R replicas with exchange rounds every S sweeps. ladder: R floats
+ * (slot temperatures, multiplied into the per-variable schedule). slots: R int32 in/out (the
+ * slot of each replica; a permutation). init/init_best/init_best_e as orc_ksat_anneal (init
+ * NULL = Philox initial states). Returns 0 or -1 on a bad argument.
+ */
+int orc_ksat_pt_anneal(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, int32_t n_steps,
+                       const float *beta, int32_t R, const float *ladder, int32_t *slots,
+                       int32_t t0, int32_t t1, int32_t S, uint64_t seed, const uint8_t *init,
+                       const uint8_t *init_best, const int64_t *init_best_e,
+                       uint8_t *final_states, int64_t *energies, int64_t *best_energies,
+                       uint8_t *best_states) {
+  if (n <= 0 || m < 0 || kmax <= 0 || t0 < 0 || t1 < t0 || t1 > n_steps || R <= 0 || S <= 0)
+    return -1;
+  orc_cnf f;
+  cnf_build(&f, n, m, kmax, lits);
+  orc_table tab;
+  table_init(&tab);
+  int32_t *colour = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t ncol = cnf_colour(&f, colour);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t p = 0;
+  for (int32_t c = 0; c < ncol; ++c)
+    for (int32_t v = 0; v < n; ++v)
+      if (colour[v] == c) order[p++] = v;
+  uint32_t *bq = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n * (size_t)n_steps);
+  for (size_t i = 0; i < (size_t)n * (size_t)n_steps; ++i) bq[i] = orc_quantize_beta(beta[i]);
+  uint32_t *lq = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)R);
+  for (int32_t k = 0; k < R; ++k) lq[k] = orc_quantize_beta(ladder[k]);
+  int32_t *at = (int32_t *)malloc(sizeof(int32_t) * (size_t)R); /* replica at each slot */
+  for (int32_t r = 0; r < R; ++r) at[slots[r]] = r;
+  uint8_t *x = (uint8_t *)malloc((size_t)R * n);
+  uint8_t *best = (uint8_t *)malloc((size_t)R * n);
+  int64_t *e = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+  int64_t *be = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+  for (int32_t r = 0; r < R; ++r) {
+    uint8_t *xr = x + (size_t)r * n;
+    if (init)
+      memcpy(xr, init + (size_t)r * n, (size_t)n);
+    else
+      for (int v = 0; v < n; ++v)
+        xr[v] = (uint8_t)(philox_word((uint32_t)v, 0u, (uint32_t)r >> 2, ORC_TAG_KSAT_INIT, seed, r & 3) & 1u);
+    e[r] = orc_ksat_energy(n, m, kmax, lits, xr);
+    if (init_best) {
+      memcpy(best + (size_t)r * n, init_best + (size_t)r * n, (size_t)n);
+      be[r] = init_best_e[r];
+    } else {
+      memcpy(best + (size_t)r * n, xr, (size_t)n);
+      be[r] = e[r];
+    }
+  }
+  for (int32_t t = t0; t < t1; ++t) {
+    for (int32_t r = 0; r < R; ++r) {
+      uint8_t *xr = x + (size_t)r * n;
+      const uint64_t mult = lq[slots[r]];
+      for (int32_t q = 0; q < n; ++q) {
+        const int v = order[q];
+        const int64_t d = cnf_delta(&f, xr, v);
+        int acc;
+        if (d <= 0) {
+          acc = 1;
+        } else {
+          uint64_t b = (mult * (uint64_t)bq[(size_t)v * n_steps + t]) >> 16;
+          if (b > 0xFFFFFFFFull) b = 0xFFFFFFFFull;
+          const uint32_t u = philox_word((uint32_t)v, (uint32_t)t, (uint32_t)r >> 2, ORC_TAG_KSAT_SWEEP, seed, r & 3);
+          acc = accept_uphill(&tab, (uint32_t)b, d, u);
+        }
+        if (acc) {
+          xr[v] ^= 1u;
+          e[r] += d;
+        }
+      }
+      if (e[r] < be[r]) {
+        be[r] = e[r];
+        memcpy(best + (size_t)r * n, xr, (size_t)n);
+      }
+    }
+    if ((t + 1) % S == 0) {
+      const uint32_t round = (uint32_t)((t + 1) / S - 1);
+      for (int32_t k = (int32_t)(round & 1u); k + 1 < R; k += 2) {
+        const int32_t a = at[k], b = at[k + 1];
+        const int64_t d = ((int64_t)lq[k] - (int64_t)lq[k + 1]) * (e[a] - e[b]);
+        int acc = 1;
+        if (d < 0) {
+          const uint64_t idx = ((uint64_t)(-d)) >> 8;
+          const uint32_t u = philox_word((uint32_t)k, round, 0u, ORC_TAG_PT_SWAP, seed, 0);
+          acc = idx < (uint64_t)tab.len && u < tab.tab[idx];
+        }
+        if (acc) {
+          at[k] = b;
+          at[k + 1] = a;
+          slots[a] = k + 1;
+          slots[b] = k;
+        }
+      }
+    }
+  }
+  if (final_states) memcpy(final_states, x, (size_t)R * n);
+  if (best_states) memcpy(best_states, best, (size_t)R * n);
+  for (int32_t r = 0; r < R; ++r) {
+    if (energies) energies[r] = e[r];
+    if (best_energies) best_energies[r] = be[r];
+  }
+  free(x);
+  free(best);
+  free(e);
+  free(be);
+  free(at);
+  free(lq);
   free(bq);
   free(order);
   free(colour);

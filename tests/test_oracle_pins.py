@@ -426,3 +426,63 @@ def test_qap_homogeneous_chain_samples_boltzmann():
     assert _chi2_pvalue(counts, w / w.sum()) > 1e-4
     w_bad = np.exp(+beta_v * (E - E.min()))
     assert _chi2_pvalue(counts, w_bad / w_bad.sum()) < 1e-6
+
+
+# ---------------------------------------------------------------- replica exchange (PT)
+def test_pt_with_equal_ladder_is_the_plain_chain():
+    """All slot temperatures 1.0: every exchange is accepted (d = 0) and the replicas' own
+    dynamics (Philox streams by replica id) are those of the plain anneal."""
+    wl = W.workload_ksat_small(24)
+    lits, n, beta = wl["lits"], wl["n_vars"], wl["beta"]
+    R = 12
+    pt = O.ksat_pt_anneal(lits, n, beta, np.ones(R, np.float32), 0, 24, 3, seed=4)
+    plain = O.ksat_anneal(lits, n, beta, 0, 24, 4, replicas=R)
+    for key in ("states", "energies", "best_energies", "best_states"):
+        assert np.array_equal(pt[key], plain[key]), key
+    assert sorted(pt["slots"].tolist()) == list(range(R))
+    # 8 rounds of accepted even/odd exchanges move replica 0 to slot 8 (+1 per round while the
+    # pairing allows: a closed-form walk of the first replica)
+    assert pt["slots"][0] == 8
+
+
+def test_pt_segments_and_invariants():
+    n = 60
+    lits = W.random_ksat(n, 4.2, 3, 12)
+    beta = W.beta_constant(n, 30, 1.0)
+    ladder = W.geometric_profile(0.25, 3.0, 10).astype(np.float32)
+    full = O.ksat_pt_anneal(lits, n, beta, ladder, 0, 30, 2, seed=6)
+    a = O.ksat_pt_anneal(lits, n, beta, ladder, 0, 11, 2, seed=6)
+    b = O.ksat_pt_anneal(lits, n, beta, ladder, 11, 30, 2, seed=6, slots=a["slots"],
+                         init=a["states"], init_best=a["best_states"],
+                         init_best_energy=a["best_energies"])
+    for key in ("states", "energies", "best_energies", "best_states", "slots"):
+        assert np.array_equal(b[key], full[key]), key
+    assert np.array_equal(full["energies"], energies_numpy(lits, full["states"]))
+    assert np.all(full["best_energies"] <= full["energies"])
+    assert sorted(full["slots"].tolist()) == list(range(10))
+    assert not np.array_equal(full["slots"], np.arange(10))  # some exchanges happened
+
+
+def test_pt_exchange_keeps_each_slot_boltzmann():
+    """Two replicas at beta 0.5 and 2.0 with an exchange round after every sweep: the joint
+    chain leaves prod_k exp(-beta_k E(x at slot k)) invariant, so the state found at each slot
+    follows the Boltzmann law of that slot's temperature. (Exchanging with the sign of the
+    energy difference reversed would break this.)"""
+    n = 6
+    lits = small_cnf(n, 20, 3, seed=2)
+    ladder = np.array([0.5, 2.0], dtype=np.float32)
+    T = 24
+    beta = W.beta_constant(n, T, 1.0)
+    E = energies_numpy(lits, all_states(n))
+    counts = [np.zeros(2 ** n), np.zeros(2 ** n)]
+    for run in range(2500):
+        res = O.ksat_pt_anneal(lits, n, beta, ladder, 0, T, 1, seed=1000 + run)
+        for r in range(2):
+            k = res["slots"][r]
+            idx = int((res["states"][r].astype(np.int64) << np.arange(n)).sum())
+            counts[k][idx] += 1
+    for k, b in enumerate(ladder):
+        w = np.exp(-float(b) * E)
+        assert _chi2_pvalue(counts[k], w / w.sum()) > 1e-4, k
+    w_swapped = np.exp(-float(ladder[1]) * E)
+    assert _chi2_pvalue(counts[0], w_swapped / w_swapped.sum()) < 1e-6
