@@ -459,6 +459,78 @@ def run_qap_batch(args):
                        "attempts_per_step": attempts}}
 
 
+def run_pt(args):
+    """Replica exchange on random 4-SAT N=5,000, alpha=9.884 (M=49,420, the paper's 4-SAT
+    size): 32 ladders x 32 temperatures (1,024 replicas), geometric ladder beta 0.5 -> 5.0 over
+    a homogeneous schedule, an exchange round every 10 sweeps, 2,000 sweeps per step. Beside
+    it: the same sweeps without exchanges, and the adaptive ladder's construction time."""
+    import torch
+    ctx, stream = _ctx_stream()
+    n, alpha, T, L, G, per = 5000, 9.884, 2000, 32, 32, 10
+    lits = W.random_ksat(n, alpha, 4, 2111)
+    inst = ctx.load_ksat(lits, n)
+    ctx.set_schedule_factored(inst, np.ones(T, np.float32), np.ones(n, np.float32))
+    R = G * L
+    rs = ctx.replicas_create(inst, R, seed=1)
+    ladder = W.geometric_profile(0.5, 5.0, L).astype(np.float32)
+    ctx.set_ladder(rs, ladder)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, steps):
+        tot = 0.0
+        for i in range(args.warmup + steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))  # L2 flush between steps (outside the events)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(i)
+            b.record(stream)
+            ctx.sync()
+            if i >= args.warmup:
+                tot += a.elapsed_time(b)
+        return tot / steps
+
+    def pt_step(i):
+        ctx.replicas_reset(rs, 100 + i)
+        ctx.run_pt(rs, 0, T, per)
+
+    def plain_step(i):
+        ctx.replicas_reset(rs, 100 + i)
+        ctx.replicas_run(rs, 0, T)
+
+    clocks = Clocks(0)
+    clocks.start()
+    ms = timed(pt_step, args.steps)
+    ck = clocks.stop()
+    ms_plain = timed(plain_step, max(2, args.steps // 2))
+    t = time.time()
+    betas, sigmas = ctx.adaptive_ladder(inst, 256, 3, 0.3, 1.1, 1.0, 48, 50, 100)
+    ladder_s = time.time() - t
+    ctx.close()
+    attempts = n * R * T
+    bps = algorithmic_bytes_per_sweep(lits, n, R)
+    peak, src = peaks()
+    achieved = bps * T / (ms / 1e3) / 1e9
+    return {"metric": "Metropolis attempts/s (replica exchange)", "value": attempts / (ms / 1e3),
+            "unit": UNIT, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "u32 (bit-sliced 32 replicas/word)",
+            "data": "synthetic (seeded random 4-SAT)",
+            "config": {"workload": f"pt_4sat_n{n}_m{lits.shape[0]}_{G}x{L}temps_t{T}_round{per}",
+                       "attempts_per_step": attempts, "exchange_rounds": T // per,
+                       "l2": "flushed between steps (512 MB write)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": src,
+                         "note": "whole step (sweep launches + exchange rounds) against the "
+                                 "sweep byte model"},
+            "no_exchange": {"value": attempts / (ms_plain / 1e3), "unit": UNIT,
+                            "ms_per_step": ms_plain},
+            "adaptive_ladder": {"s": ladder_s, "temps": int(len(betas)),
+                                "beta_last": float(betas[-1]), "sigma_last": float(sigmas[-1]),
+                                "config": "256 replicas, beta0 0.3, alpha 1.1, sigma_min 1.0, "
+                                          "50 + 100 sweeps per level"},
+            "clocks": ck}
+
+
 def run_serving(args):
     """Poisson arrivals of random 4-SAT (N log-uniform [500, 50000], alpha U[9.0, 9.8], 32
     replicas) and QAP (n U[32, 192], 256 replicas) requests of 1000..5000 sweeps, each with its
@@ -578,7 +650,8 @@ def main():
     ap.add_argument("--cpu-replicas", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--workload", default="ksat_large",
-                    choices=["ksat_large", "ksat_small", "ksat_batch", "qap_batch", "serving"])
+                    choices=["ksat_large", "ksat_small", "ksat_batch", "qap_batch", "serving",
+                             "pt"])
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--qap-steps", type=int, default=50)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -599,7 +672,7 @@ def main():
         res = run_reference(args, world, rank)
     elif args.workload != "ksat_large":
         fn = {"ksat_small": run_ksat_small, "ksat_batch": run_ksat_batch,
-              "qap_batch": run_qap_batch, "serving": run_serving}[args.workload]
+              "qap_batch": run_qap_batch, "serving": run_serving, "pt": run_pt}[args.workload]
         res = fn(args) if rank == 0 else None
     else:
         res = run_ours(args, world, rank, local)

@@ -171,7 +171,7 @@ int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t
  * that cannot afford the device-wide synchronisation an allocation may cause. It does the
  * same work with the same results as nmc_batch_run on the same arguments, but its work list
  * and counters live in one fixed 1 MiB device array of the library instead of memory the
- * context allocates. Limit: one call takes at most (1 MiB - 256 B) / 112 B = 9360 work items,
+ * context allocates. Limit: one call takes at most (1 MiB - 256 B) / 136 B = 7708 work items,
  * one per 32-replica word of each set (NMC_EINVAL beyond, with a message). The array is
  * reserved on every GPU that loads the library until the process exits. The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, with that device current);
@@ -187,6 +187,56 @@ int nmc_qap_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int
                       const int32_t *t1);
 /* Largest n_vars nmc_batch_run accepts on this context's device. */
 int32_t nmc_batch_max_vars(nmc_ctx *ctx);
+
+/*
+ * Replica exchange (parallel tempering, App. "Adaptive Parallel Tempering": replicas at
+ * adjacent temperatures exchange with probability min{1, exp[(beta_i - beta_j)(E_i - E_j)]}).
+ *
+ * nmc_replicas_set_ladder attaches a temperature ladder to a k-SAT replica set whose R is a
+ * multiple of n_temps: the set becomes G = R / n_temps independent ladders, replica g*n_temps
+ * + i in ladder g. ladder: n_temps floats (host), each finite and in [0, 65535], quantised to
+ * Q16 like the schedule (lq[k]). slots (host, nullable): R int32, the slot of every replica
+ * within its ladder, each ladder's slots a permutation of 0..n_temps-1; NULL puts replica
+ * g*n_temps + i at slot i. A replica at slot k moves at min(2^32-1, (lq[k] bq_v[t]) >> 16)
+ * instead of the schedule's bq_v[t]: the schedule gives the spatial profile, the ladder the
+ * temperature. Replaces an earlier ladder; reset and restore leave the ladder and slots alone.
+ * Needs an instance nmc_batch_run accepts (NMC_EINVAL otherwise).
+ */
+int nmc_replicas_set_ladder(nmc_ctx *ctx, int32_t rs, int32_t n_temps, const float *ladder,
+                            const int32_t *slots);
+/*
+ * Runs sweeps t0..t1-1 of a set with a ladder, asynchronously on the context's stream, with an
+ * exchange round after every sweep t where (t+1) % sweeps_per_round == 0: round
+ * q = (t+1)/sweeps_per_round - 1 tries the slot pairs (k, k+1), k = q mod 2, k+2, ..., of
+ * every ladder g; replicas a (at k) and b (at k+1) exchange slots when
+ * d = (lq[k] - lq[k+1]) (E_a - E_b) >= 0, else when ((-d) >> 8) < L and u < Tab[(-d) >> 8],
+ * u = word 0 of the Philox block for counter (k, q, g, 0x50545357) under the set's seed.
+ * Rounds are absolute like t, so [t0, t1) then [t1, t2) equals [t0, t2).
+ */
+int nmc_replicas_run_pt(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1,
+                        int32_t sweeps_per_round);
+/* Copies the slot of every replica (R int32) of a set with a ladder to host memory
+ * (synchronises). */
+int nmc_replicas_read_slots(nmc_ctx *ctx, int32_t rs, int32_t *slots_out);
+
+/*
+ * Adaptive ladder (App. "Adaptive Parallel Tempering"): beta_0 = beta0; for level i the k-SAT
+ * instance's `replicas` chains (a temporary set seeded by `seed`, Philox initial states, each
+ * level continuing from the previous level's states) run sweeps_eq + sweeps_meas sweeps
+ * (absolute sweeps [i T, (i+1) T), T = sweeps_eq + sweeps_meas) at the homogeneous inverse
+ * temperature beta_i (every variable, float32 then Q16 as a schedule). The end-of-sweep
+ * energies of the last sweeps_meas sweeps of every replica give
+ * sigma_i = sqrt(<E^2> - <E>^2) (exact integer sums, then IEEE double, each operation rounded
+ * separately, a negative variance taken as 0). The ladder stops at level i when
+ * sigma_i <= sigma_min or i + 1 == max_temps, else beta_{i+1} = beta_i + alpha / sigma_i.
+ * betas_out, sigmas_out: max_temps doubles (host); *n_temps_out = levels run. The instance's
+ * own schedule is not used or changed. sigma_min must be >= 0 (so sigma = 0 always stops).
+ * NMC_EINVAL if a beta leaves [0, 65535].
+ */
+int nmc_adaptive_ladder(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t seed, double beta0,
+                        double alpha, double sigma_min, int32_t max_temps, int32_t sweeps_eq,
+                        int32_t sweeps_meas, double *betas_out, double *sigmas_out,
+                        int32_t *n_temps_out);
 
 /*
  * One-shot anneal through host memory: creates a replica set, runs [t0, t1), copies the

@@ -14,6 +14,7 @@ independent Philox implementation); none is "parity unpinned".
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -59,10 +60,10 @@ def _load():
             lib.orc_ksat_colour.argtypes = [i32, i32, i32, P, P]
             lib.orc_ksat_colour.restype = i32
             lib.orc_ksat_anneal.argtypes = [i32, i32, i32, P, i32, P, i32, P, i32, i32, u64, P, P,
-                                            P, i32, P, P, P, P]
+                                            P, i32, P, P, P, P, i32, P, P]
             lib.orc_ksat_anneal.restype = C.c_int
-            lib.orc_ksat_pt_anneal.argtypes = [i32, i32, i32, P, i32, P, i32, P, P, i32, i32, i32,
-                                               u64, P, P, P, P, P, P, P]
+            lib.orc_ksat_pt_anneal.argtypes = [i32, i32, i32, P, i32, P, i32, i32, P, P, i32, i32,
+                                               i32, u64, P, P, P, P, P, P, P]
             lib.orc_ksat_pt_anneal.restype = C.c_int
             lib.orc_qap_cost.argtypes = [i32, P, P, P]
             lib.orc_qap_cost.restype = i64
@@ -146,9 +147,10 @@ def ksat_colour(lits, n_vars: int):
 
 
 def ksat_anneal(lits, n_vars, beta, t0, t1, seed, replicas=None, replica_ids=None, init=None,
-                init_best=None, init_best_energy=None, n_threads=None):
+                init_best=None, init_best_energy=None, n_threads=None, stats_from=None):
     """Runs sweeps t0..t1-1. Returns dict(states uint8[R,N], energies int64[R],
-    best_energies int64[R], best_states uint8[R,N]).
+    best_energies int64[R], best_states uint8[R,N]); with stats_from, also e_sum / e_sq int64[R]:
+    sums of the end-of-sweep energy and its square over sweeps t >= stats_from.
 
     replica_ids selects which replica indices (Philox streams) to run; default 0..replicas-1.
     """
@@ -167,25 +169,36 @@ def ksat_anneal(lits, n_vars, beta, t0, t1, seed, replicas=None, replica_ids=Non
     out_b = np.zeros((nr, n_vars), dtype=np.uint8)
     e = np.zeros(nr, dtype=np.int64)
     be = np.zeros(nr, dtype=np.int64)
+    s1 = s2 = None
+    if stats_from is not None:
+        s1 = np.zeros(nr, dtype=np.int64)
+        s2 = np.zeros(nr, dtype=np.int64)
     rc = _load().orc_ksat_anneal(n_vars, m, k, _p(lits), beta.shape[1], _p(beta), nr, _p(ids),
                                  int(t0), int(t1), int(seed) & (2**64 - 1), _p(init),
                                  _p(init_best), _p(init_best_energy), int(n_threads), _p(out_s),
-                                 _p(e), _p(be), _p(out_b))
+                                 _p(e), _p(be), _p(out_b),
+                                 int(stats_from) if stats_from is not None else 0, _p(s1), _p(s2))
     if rc != 0:
         raise ValueError("orc_ksat_anneal rejected its arguments")
-    return dict(states=out_s, energies=e, best_energies=be, best_states=out_b)
+    out = dict(states=out_s, energies=e, best_energies=be, best_states=out_b)
+    if stats_from is not None:
+        out.update(e_sum=s1, e_sq=s2)
+    return out
 
 
-def ksat_pt_anneal(lits, n_vars, beta, ladder, t0, t1, sweeps_per_round, seed, slots=None,
-                   init=None, init_best=None, init_best_energy=None):
-    """Replica exchange: R = len(ladder) replicas, replica r at slot slots[r] (default r) with
-    temperature multiplier ladder[slot]; exchange rounds after every sweeps_per_round sweeps.
+def ksat_pt_anneal(lits, n_vars, beta, ladder, t0, t1, sweeps_per_round, seed, replicas=None,
+                   slots=None, init=None, init_best=None, init_best_energy=None):
+    """Replica exchange: R = replicas (default len(ladder)) = G ladders of L = len(ladder)
+    slots; replica g*L + i sits at slot slots[r] (default i) of ladder g, with temperature
+    multiplier ladder[slot]; exchange rounds after every sweeps_per_round sweeps.
     Returns dict(states, energies, best_energies, best_states, slots)."""
     lits, m, k = _cnf(lits)
     beta = np.ascontiguousarray(beta, dtype=np.float32)
     ladder = np.ascontiguousarray(ladder, dtype=np.float32)
-    R = ladder.shape[0]
-    slots = np.arange(R, dtype=np.int32) if slots is None else np.array(slots, dtype=np.int32)
+    L = ladder.shape[0]
+    R = L if replicas is None else int(replicas)
+    slots = (np.arange(R, dtype=np.int32) % L if slots is None
+             else np.array(slots, dtype=np.int32))
     init = _c(init, np.uint8)
     init_best = _c(init_best, np.uint8)
     init_best_energy = _c(init_best_energy, np.int64)
@@ -193,13 +206,47 @@ def ksat_pt_anneal(lits, n_vars, beta, ladder, t0, t1, sweeps_per_round, seed, s
     out_b = np.zeros((R, n_vars), dtype=np.uint8)
     e = np.zeros(R, dtype=np.int64)
     be = np.zeros(R, dtype=np.int64)
-    rc = _load().orc_ksat_pt_anneal(n_vars, m, k, _p(lits), beta.shape[1], _p(beta), R, _p(ladder),
-                                    _p(slots), int(t0), int(t1), int(sweeps_per_round),
+    rc = _load().orc_ksat_pt_anneal(n_vars, m, k, _p(lits), beta.shape[1], _p(beta), R, L,
+                                    _p(ladder), _p(slots), int(t0), int(t1), int(sweeps_per_round),
                                     int(seed) & (2**64 - 1), _p(init), _p(init_best),
                                     _p(init_best_energy), _p(out_s), _p(e), _p(be), _p(out_b))
     if rc != 0:
         raise ValueError("orc_ksat_pt_anneal rejected its arguments")
     return dict(states=out_s, energies=e, best_energies=be, best_states=out_b, slots=slots)
+
+
+def adaptive_ladder(lits, n_vars, replicas, seed, beta0, alpha, sigma_min, max_temps,
+                    sweeps_eq, sweeps_meas):
+    """Adaptive inverse-temperature ladder (App. "Adaptive Parallel Tempering").
+
+    Level i runs the replicas (Philox initial states under `seed` at level 0, then each level
+    continuing from the previous one) over sweeps [i T, (i+1) T), T = sweeps_eq + sweeps_meas, at
+    the homogeneous beta_i (float32, every variable); sigma_i^2 = <E^2> - <E>^2 over the
+    end-of-sweep energies of the last sweeps_meas sweeps of all replicas. Stops when
+    sigma_i <= sigma_min or after max_temps levels; else beta_{i+1} = beta_i + alpha / sigma_i.
+    Returns (betas, sigmas) as float64 arrays.
+    """
+    T = int(sweeps_eq) + int(sweeps_meas)
+    betas, sigmas = [], []
+    beta = float(beta0)
+    state = dict(init=None, init_best=None, init_best_energy=None)
+    for i in range(int(max_temps)):
+        t0, t1 = i * T, (i + 1) * T
+        sched = np.full((n_vars, t1), np.float32(beta), dtype=np.float32)
+        res = ksat_anneal(lits, n_vars, sched, t0, t1, seed, replicas=replicas,
+                          stats_from=t0 + int(sweeps_eq), **state)
+        state = dict(init=res["states"], init_best=res["best_states"],
+                     init_best_energy=res["best_energies"])
+        samples = float(int(replicas) * int(sweeps_meas))
+        mean = float(int(res["e_sum"].sum())) / samples
+        var = float(int(res["e_sq"].sum())) / samples - mean * mean
+        sigma = math.sqrt(max(var, 0.0))
+        betas.append(beta)
+        sigmas.append(sigma)
+        if sigma <= sigma_min:
+            break
+        beta = beta + alpha / sigma
+    return np.array(betas, dtype=np.float64), np.array(sigmas, dtype=np.float64)
 
 
 def qap_cost(F, D, p) -> int:

@@ -27,13 +27,17 @@
  *    Tab[j] = min(2^32-1, floor(2^32 exp(-j/256))) and L the first j with Tab[j] = 0.
  *  Best-so-far: starts at the initial state, replaced after a full sweep on strictly lower E.
  *  Replica exchange (App. "Adaptive Parallel Tempering": swap probability
- *    min{1, exp[(beta_i - beta_j)(E_i - E_j)]} for replicas at adjacent temperatures): replica r
- *    sits at ladder slot s(r) with Q16 temperature lq[s]; its moves use
- *    min(2^32-1, (lq[s(r)] * bq_v[t]) >> 16). After every S sweeps (sweep t with (t+1) % S == 0,
- *    round q = (t+1)/S - 1) the pairs of adjacent slots (k, k+1) with k = q mod 2, k+2, ... try to
- *    exchange their replicas a (at k) and b (at k+1): d = (lq[k] - lq[k+1]) (E_a - E_b) accepts
- *    when d >= 0, else iff ((-d) >> 8) < L and u < Tab[(-d) >> 8] for u = word 0 of the Philox
- *    block for counter (k, q, 0, TAG_PT_SWAP).
+ *    min{1, exp[(beta_i - beta_j)(E_i - E_j)]} for replicas at adjacent temperatures): G ladders
+ *    of L slots, replica g*L + i in ladder g; replica r sits at slot s(r) of its ladder, with Q16
+ *    temperature lq[s]; its moves use min(2^32-1, (lq[s(r)] * bq_v[t]) >> 16). After every S
+ *    sweeps (sweep t with (t+1) % S == 0, round q = (t+1)/S - 1) the pairs of adjacent slots
+ *    (k, k+1) with k = q mod 2, k+2, ... of every ladder try to exchange their replicas a (at k)
+ *    and b (at k+1): d = (lq[k] - lq[k+1]) (E_a - E_b) accepts when d >= 0, else iff
+ *    ((-d) >> 8) < L and u < Tab[(-d) >> 8] for u = word 0 of the Philox block for counter
+ *    (k, q, g, TAG_PT_SWAP).
+ *  Energy statistics (the adaptive ladder of the same appendix measures the energy variance at
+ *    each temperature): sums of E and E^2 of every replica over the end-of-sweep energies of
+ *    the sweeps t >= stats_t0.
  *  QAP (Sec. "Quadratic Assignment Problems", Koopmans-Beckmann form without the placement
  *    term): C(p) = sum_ij F_ij D_{p(i)p(j)}, F and D symmetric with zero diagonal. One step is
  *    n swap attempts; attempt a of step t draws Philox counter (a, t, r, TAG_QAP_STEP):
@@ -298,6 +302,8 @@ typedef struct {
   uint8_t *final_states;
   int64_t *energies, *best_energies;
   uint8_t *best_states;
+  int32_t stats_t0;
+  int64_t *e_sum, *e_sq; /* nr each or NULL */
   int32_t j_begin, j_end;
 } ksat_job;
 
@@ -342,6 +348,10 @@ static void ksat_one_replica(const ksat_job *J, int32_t j) {
       best_e = e;
       memcpy(best, x, (size_t)n);
     }
+    if (J->e_sum && t >= J->stats_t0) {
+      J->e_sum[j] += e;
+      J->e_sq[j] += e * e;
+    }
   }
   if (J->final_states) memcpy(J->final_states + (size_t)j * n, x, (size_t)n);
   if (J->energies) J->energies[j] = e;
@@ -361,13 +371,15 @@ static void *ksat_worker(void *arg) {
  * Runs sweeps t0..t1-1 for nr replicas (ids rep_ids, or 0..nr-1 if NULL).
  * beta: n * n_steps float32, row v = schedule of variable v. init: nr*n uint8 (NULL = Philox
  * initial state). init_best/init_best_e continue a chain's best-so-far (both NULL = fresh).
+ * e_sum/e_sq (nr each, zeroed here, or NULL): energy statistics of sweeps t >= stats_t0.
  * Outputs may be NULL. Returns 0, or -1 on a bad argument.
  */
 int orc_ksat_anneal(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, int32_t n_steps,
                     const float *beta, int32_t nr, const int32_t *rep_ids, int32_t t0, int32_t t1,
                     uint64_t seed, const uint8_t *init, const uint8_t *init_best,
                     const int64_t *init_best_e, int32_t n_threads, uint8_t *final_states,
-                    int64_t *energies, int64_t *best_energies, uint8_t *best_states) {
+                    int64_t *energies, int64_t *best_energies, uint8_t *best_states,
+                    int32_t stats_t0, int64_t *e_sum, int64_t *e_sq) {
   if (n <= 0 || m < 0 || kmax <= 0 || t0 < 0 || t1 < t0 || t1 > n_steps || nr < 0) return -1;
   orc_cnf f;
   cnf_build(&f, n, m, kmax, lits);
@@ -387,6 +399,12 @@ int orc_ksat_anneal(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, int
 
   if (n_threads < 1) n_threads = 1;
   if (n_threads > nr) n_threads = nr > 0 ? nr : 1;
+  if (e_sum && e_sq) {
+    memset(e_sum, 0, sizeof(int64_t) * (size_t)nr);
+    memset(e_sq, 0, sizeof(int64_t) * (size_t)nr);
+  } else {
+    e_sum = e_sq = NULL;
+  }
   ksat_job *jobs = (ksat_job *)calloc((size_t)n_threads, sizeof(ksat_job));
   pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
   for (int w = 0; w < n_threads; ++w) {
@@ -408,6 +426,9 @@ int orc_ksat_anneal(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, int
     J->energies = energies;
     J->best_energies = best_energies;
     J->best_states = best_states;
+    J->stats_t0 = stats_t0;
+    J->e_sum = e_sum;
+    J->e_sq = e_sq;
     J->j_begin = (int32_t)((int64_t)nr * w / n_threads);
     J->j_end = (int32_t)((int64_t)nr * (w + 1) / n_threads);
   }
@@ -429,19 +450,22 @@ int orc_ksat_anneal(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, int
  * k-SAT with replica exchange (single-threaded: the exchange rounds couple the replicas).
  * ------------------------------------------------------------------------------------- */
 /*
- * Runs sweeps t0..t1-1 of R replicas with exchange rounds every S sweeps. ladder: R floats
- * (slot temperatures, multiplied into the per-variable schedule). slots: R int32 in/out (the
- * slot of each replica; a permutation). init/init_best/init_best_e as orc_ksat_anneal (init
- * NULL = Philox initial states). Returns 0 or -1 on a bad argument.
+ * Runs sweeps t0..t1-1 of R = G * L replicas with exchange rounds every S sweeps. ladder: L
+ * floats (slot temperatures, multiplied into the per-variable schedule). slots: R int32 in/out
+ * (the slot of each replica within its ladder; a permutation of 0..L-1 per ladder).
+ * init/init_best/init_best_e as orc_ksat_anneal (init NULL = Philox initial states). Returns 0
+ * or -1 on a bad argument.
  */
 int orc_ksat_pt_anneal(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, int32_t n_steps,
-                       const float *beta, int32_t R, const float *ladder, int32_t *slots,
-                       int32_t t0, int32_t t1, int32_t S, uint64_t seed, const uint8_t *init,
-                       const uint8_t *init_best, const int64_t *init_best_e,
+                       const float *beta, int32_t R, int32_t L, const float *ladder,
+                       int32_t *slots, int32_t t0, int32_t t1, int32_t S, uint64_t seed,
+                       const uint8_t *init, const uint8_t *init_best, const int64_t *init_best_e,
                        uint8_t *final_states, int64_t *energies, int64_t *best_energies,
                        uint8_t *best_states) {
-  if (n <= 0 || m < 0 || kmax <= 0 || t0 < 0 || t1 < t0 || t1 > n_steps || R <= 0 || S <= 0)
+  if (n <= 0 || m < 0 || kmax <= 0 || t0 < 0 || t1 < t0 || t1 > n_steps || R <= 0 || S <= 0 ||
+      L <= 0 || R % L != 0)
     return -1;
+  const int32_t G = R / L;
   orc_cnf f;
   cnf_build(&f, n, m, kmax, lits);
   orc_table tab;
@@ -455,10 +479,10 @@ int orc_ksat_pt_anneal(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, 
       if (colour[v] == c) order[p++] = v;
   uint32_t *bq = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n * (size_t)n_steps);
   for (size_t i = 0; i < (size_t)n * (size_t)n_steps; ++i) bq[i] = orc_quantize_beta(beta[i]);
-  uint32_t *lq = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)R);
-  for (int32_t k = 0; k < R; ++k) lq[k] = orc_quantize_beta(ladder[k]);
-  int32_t *at = (int32_t *)malloc(sizeof(int32_t) * (size_t)R); /* replica at each slot */
-  for (int32_t r = 0; r < R; ++r) at[slots[r]] = r;
+  uint32_t *lq = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)L);
+  for (int32_t k = 0; k < L; ++k) lq[k] = orc_quantize_beta(ladder[k]);
+  int32_t *at = (int32_t *)malloc(sizeof(int32_t) * (size_t)R); /* at[g*L + k]: replica at slot k */
+  for (int32_t r = 0; r < R; ++r) at[(r / L) * L + slots[r]] = r;
   uint8_t *x = (uint8_t *)malloc((size_t)R * n);
   uint8_t *best = (uint8_t *)malloc((size_t)R * n);
   int64_t *e = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
@@ -507,20 +531,23 @@ int orc_ksat_pt_anneal(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, 
     }
     if ((t + 1) % S == 0) {
       const uint32_t round = (uint32_t)((t + 1) / S - 1);
-      for (int32_t k = (int32_t)(round & 1u); k + 1 < R; k += 2) {
-        const int32_t a = at[k], b = at[k + 1];
-        const int64_t d = ((int64_t)lq[k] - (int64_t)lq[k + 1]) * (e[a] - e[b]);
-        int acc = 1;
-        if (d < 0) {
-          const uint64_t idx = ((uint64_t)(-d)) >> 8;
-          const uint32_t u = philox_word((uint32_t)k, round, 0u, ORC_TAG_PT_SWAP, seed, 0);
-          acc = idx < (uint64_t)tab.len && u < tab.tab[idx];
-        }
-        if (acc) {
-          at[k] = b;
-          at[k + 1] = a;
-          slots[a] = k + 1;
-          slots[b] = k;
+      for (int32_t g = 0; g < G; ++g) {
+        int32_t *atg = at + (size_t)g * L;
+        for (int32_t k = (int32_t)(round & 1u); k + 1 < L; k += 2) {
+          const int32_t a = atg[k], b = atg[k + 1];
+          const int64_t d = ((int64_t)lq[k] - (int64_t)lq[k + 1]) * (e[a] - e[b]);
+          int acc = 1;
+          if (d < 0) {
+            const uint64_t idx = ((uint64_t)(-d)) >> 8;
+            const uint32_t u = philox_word((uint32_t)k, round, (uint32_t)g, ORC_TAG_PT_SWAP, seed, 0);
+            acc = idx < (uint64_t)tab.len && u < tab.tab[idx];
+          }
+          if (acc) {
+            atg[k] = b;
+            atg[k + 1] = a;
+            slots[a] = k + 1;
+            slots[b] = k;
+          }
         }
       }
     }

@@ -57,7 +57,9 @@ SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_
            "nmc_batch_max_vars", "nmc_server_create", "nmc_server_destroy",
            "nmc_server_submit_ksat", "nmc_server_submit_qap", "nmc_server_poll",
            "nmc_server_result", "nmc_server_cancel", "nmc_server_stats",
-           "nmc_server_last_error", "nmc_batch_run_noalloc", "nmc_qap_batch_run"]
+           "nmc_server_last_error", "nmc_batch_run_noalloc", "nmc_qap_batch_run",
+           "nmc_replicas_set_ladder", "nmc_replicas_run_pt", "nmc_replicas_read_slots",
+           "nmc_adaptive_ladder"]
 
 
 def library_path() -> str:
@@ -111,6 +113,11 @@ def load(build_if_missing: bool = True):
             "nmc_server_cancel": ([P, C.c_int64], C.c_int),
             "nmc_server_stats": ([P, P, P, P, P, P, P], C.c_int),
             "nmc_server_last_error": ([P], C.c_char_p),
+            "nmc_replicas_set_ladder": ([P, i32, i32, P, P], C.c_int),
+            "nmc_replicas_run_pt": ([P, i32, i32, i32, i32], C.c_int),
+            "nmc_replicas_read_slots": ([P, i32, P], C.c_int),
+            "nmc_adaptive_ladder": ([P, i32, i32, u64, C.c_double, C.c_double, C.c_double, i32,
+                                     i32, i32, P, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -306,6 +313,43 @@ class Context:
 
     def replicas_run(self, rs: int, t0: int, t1: int):
         self._check(self._lib.nmc_replicas_run(self._h, int(rs), int(t0), int(t1)))
+
+    # -- replica exchange
+    def set_ladder(self, rs: int, ladder, slots=None):
+        """Attaches a temperature ladder (n_temps floats) to a k-SAT replica set of R = G *
+        n_temps replicas; slots: [R] int32 slot of every replica in its ladder (None: identity)."""
+        ladder = np.ascontiguousarray(ladder, dtype=np.float32)
+        _, R = self._rs[rs]
+        if slots is not None:
+            slots = np.ascontiguousarray(slots, dtype=np.int32)
+            if slots.shape != (R,):
+                raise ValueError("slots must have one entry per replica")
+        self._check(self._lib.nmc_replicas_set_ladder(self._h, int(rs), ladder.shape[0],
+                                                      _ptr(ladder), _ptr(slots)))
+
+    def run_pt(self, rs: int, t0: int, t1: int, sweeps_per_round: int):
+        """Sweeps t0..t1-1 with an exchange round after every sweeps_per_round sweeps."""
+        self._check(self._lib.nmc_replicas_run_pt(self._h, int(rs), int(t0), int(t1),
+                                                  int(sweeps_per_round)))
+
+    def read_slots(self, rs: int):
+        _, R = self._rs[rs]
+        out = np.zeros(R, dtype=np.int32)
+        self._check(self._lib.nmc_replicas_read_slots(self._h, int(rs), _ptr(out)))
+        return out
+
+    def adaptive_ladder(self, inst: int, replicas: int, seed: int, beta0: float, alpha: float,
+                        sigma_min: float, max_temps: int, sweeps_eq: int, sweeps_meas: int):
+        """(betas float64[L], sigmas float64[L]) of the adaptive ladder."""
+        betas = np.zeros(max_temps, dtype=np.float64)
+        sigmas = np.zeros(max_temps, dtype=np.float64)
+        nt = C.c_int32()
+        self._check(self._lib.nmc_adaptive_ladder(self._h, int(inst), int(replicas),
+                                                  int(seed) & (2**64 - 1), float(beta0),
+                                                  float(alpha), float(sigma_min), int(max_temps),
+                                                  int(sweeps_eq), int(sweeps_meas), _ptr(betas),
+                                                  _ptr(sigmas), C.byref(nt)))
+        return betas[:nt.value].copy(), sigmas[:nt.value].copy()
 
     def _alloc_out(self, inst, R, host=True):
         n = self._units[inst]

@@ -34,6 +34,12 @@ struct ReplicaSet {
   uint64_t seed = 0;
   KsatReplicas ks{};
   QapReplicas qp{};
+  // temperature ladder (k-SAT replica exchange); pt_L = 0 without one
+  int32_t pt_L = 0;
+  uint32_t *pt_lq = nullptr;    // pt_L Q16 inverse temperatures of the slots
+  int32_t *pt_slot = nullptr;   // R: slot of every replica within its ladder
+  int32_t *pt_at = nullptr;     // R: replica at slot k of ladder g (index g*pt_L + k)
+  uint32_t *pt_mult = nullptr;  // 32W: Q16 multiplier of every replica (1.0 for padding)
 };
 
 const char *kStaticNoCtx = "nmc: no context";
@@ -145,6 +151,11 @@ void free_set(ReplicaSet &S) {
   dev_free(S.qp.best_perm);
   dev_free(S.qp.energy);
   dev_free(S.qp.best_energy);
+  dev_free(S.pt_lq);
+  dev_free(S.pt_slot);
+  dev_free(S.pt_at);
+  dev_free(S.pt_mult);
+  S.pt_L = 0;
 }
 
 Instance *find_inst(nmc_ctx *ctx, int32_t id) {
@@ -252,7 +263,7 @@ int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t
     if (t1[i] == t0[i]) continue;
     const int q = I->ks.kq == 1 ? 0 : 1;
     for (int32_t w = 0; w < S->ks.W; ++w) {
-      BatchItem B;
+      BatchItem B{};
       B.occ_t = I->ks.occ_t;
       B.grp_base = I->ks.grp_base;
       B.cgrp = I->ks.cgrp;
@@ -289,8 +300,12 @@ int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t
     plan->off[q] = plan->items.size();
     plan->cnt[q] = static_cast<int>(idx.size());
     for (size_t k : idx) plan->items.push_back(by_kq[q][k]);
+    // CTAs per item: spread few items over the SMs (word vectors replicated per cluster)
     int cs = 1;
-    while (cs < 8 && static_cast<long long>(plan->cnt[q]) * cs * 2 <= sms) cs *= 2;
+    if (const char *env = getenv("NMC_BATCH_CTAS")) cs = atoi(env);
+    else
+      while (cs < 8 && static_cast<long long>(plan->cnt[q]) * cs * 2 <= sms) cs *= 2;
+    if (cs != 1 && cs != 2 && cs != 4 && cs != 8) cs = 1;
     plan->cs[q] = cs;
   }
   plan->device = ctx->device;
@@ -301,6 +316,92 @@ int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t
 }
 
 }  // namespace nmc
+
+namespace {
+
+// Makes room for `total` work items in the context's device work list (waiting for earlier
+// launches that may still read it) and allocates the two work counters.
+int reserve_items(nmc_ctx *ctx, size_t total) {
+  if (total > ctx->items_cap) {
+    NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    dev_free(ctx->items);
+    ctx->items_cap = 0;
+    NMC_CUDA(dev_alloc(&ctx->items, total), "allocate batch work list");
+    ctx->items_cap = total;
+  }
+  if (!ctx->next_item) NMC_CUDA(dev_alloc(&ctx->next_item, 2), "allocate batch counters");
+  return NMC_OK;
+}
+
+// Uploads a work list and launches it: items [off[q], off[q] + cnt[q]) have occurrence width
+// q + 1. pt selects the kernels with temperature multipliers and energy statistics.
+int launch_items(nmc_ctx *ctx, const std::vector<BatchItem> &items, const size_t off[2],
+                 const int cnt[2], const int max_n[2], const int cs[2], bool pt) {
+  if (items.empty()) return NMC_OK;
+  const int rc = reserve_items(ctx, items.size());
+  if (rc != NMC_OK) return rc;
+  // cudaMemcpyAsync stages pageable host memory before it returns
+  NMC_CUDA(cudaMemcpyAsync(ctx->items, items.data(), sizeof(BatchItem) * items.size(),
+                           cudaMemcpyHostToDevice, ctx->stream),
+           "upload batch work list");
+  for (int q = 0; q < 2; ++q) {
+    if (!cnt[q]) continue;
+    NMC_CUDA(ksat_batch(ctx->items + off[q], cnt[q], q + 1, cs[q], max_n[q], ctx->next_item + q,
+                        ctx->tab, ctx->tab_len, ctx->device, ctx->stream, pt),
+             "launch batched sweep");
+  }
+  return NMC_OK;
+}
+
+// The work item of word w of k-SAT set S for sweeps [t0, t1).
+BatchItem ksat_item(const Instance &I, const ReplicaSet &S, int32_t w, int32_t t0, int32_t t1) {
+  BatchItem B{};
+  B.occ_t = I.ks.occ_t;
+  B.grp_base = I.ks.grp_base;
+  B.cgrp = I.ks.cgrp;
+  B.col_ptr = I.ks.col_ptr;
+  B.orig = I.ks.orig;
+  B.bq = I.bq;
+  B.S = S.ks.S;
+  B.best = S.ks.best;
+  B.energy = S.ks.energy;
+  B.best_energy = S.ks.best_energy;
+  B.n = I.ks.n;
+  B.n_colours = I.ks.n_colours;
+  B.W = S.ks.W;
+  B.w = w;
+  B.t0 = t0;
+  B.t1 = t1;
+  B.k0 = static_cast<uint32_t>(S.seed);
+  B.k1 = static_cast<uint32_t>(S.seed >> 32);
+  return B;
+}
+
+// CTAs per work item for a launch of `cnt` items (as batch_plan chooses).
+int ctas_per_item(nmc_ctx *ctx, long long cnt) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  int cs = 1;
+  if (const char *env = getenv("NMC_BATCH_CTAS")) cs = atoi(env);
+  else
+    while (cs < 8 && cnt * cs * 2 <= sms) cs *= 2;
+  if (cs != 1 && cs != 2 && cs != 4 && cs != 8) cs = 1;
+  return cs;
+}
+
+// The checks every batched-kernel path makes on a k-SAT instance.
+int check_batchable(nmc_ctx *ctx, const Instance &I) {
+  if (I.kind != NMC_KIND_KSAT) return fail(ctx, NMC_EINVAL, "needs a k-SAT instance");
+  if (I.ks.nb > 7) return fail(ctx, NMC_EINVAL, "needs every variable in <= 127 clauses");
+  if (static_cast<size_t>(I.ks.n) > batch_max_vars(ctx->tab_len, ctx->device))
+    return fail(ctx, NMC_EINVAL, "instance too large for the batched kernel");
+  return NMC_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1092,94 +1193,238 @@ int32_t nmc_batch_max_vars(nmc_ctx *ctx) {
 int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
                   const int32_t *t1) {
   if (!ctx) return NMC_EINVAL;
-  if (n_sets < 0 || (n_sets > 0 && (!rs || !t0 || !t1)))
-    return fail(ctx, NMC_EINVAL, "bad batch arrays");
   DeviceGuard g(ctx->device);
-  const size_t max_vars = batch_max_vars(ctx->tab_len, ctx->device);
-  std::vector<BatchItem> by_kq[2];
-  int max_n[2] = {0, 0};
-  std::vector<long long> cost[2];
-  std::map<int32_t, int> seen;
-  for (int32_t i = 0; i < n_sets; ++i) {
-    ReplicaSet *S = find_set(ctx, rs[i]);
-    if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set in batch");
-    if (seen[rs[i]]++) return fail(ctx, NMC_EINVAL, "replica set repeated in batch");
-    Instance *I = find_inst(ctx, S->inst);
-    if (!I || I->kind != NMC_KIND_KSAT) return fail(ctx, NMC_EINVAL, "batch sets must be k-SAT");
-    if (t0[i] < 0 || t1[i] < t0[i]) return fail(ctx, NMC_EINVAL, "need 0 <= t0 <= t1");
-    if (t1[i] > t0[i] && (!I->bq || t1[i] > I->n_steps))
-      return fail(ctx, NMC_ESTATE, "schedule missing or shorter than t1");
-    if (I->ks.nb > 7) return fail(ctx, NMC_EINVAL, "batched sets need every variable in <= 127 clauses");
-    if (static_cast<size_t>(I->ks.n) > max_vars)
-      return fail(ctx, NMC_EINVAL, "instance too large for the batched kernel");
-    if (t1[i] == t0[i]) continue;
-    const int q = I->ks.kq == 1 ? 0 : 1;
-    for (int32_t w = 0; w < S->ks.W; ++w) {
-      BatchItem B;
-      B.occ_t = I->ks.occ_t;
-      B.grp_base = I->ks.grp_base;
-      B.cgrp = I->ks.cgrp;
-      B.col_ptr = I->ks.col_ptr;
-      B.orig = I->ks.orig;
-      B.bq = I->bq;
-      B.S = S->ks.S;
-      B.best = S->ks.best;
-      B.energy = S->ks.energy;
-      B.best_energy = S->ks.best_energy;
-      B.n = I->ks.n;
-      B.n_colours = I->ks.n_colours;
-      B.W = S->ks.W;
-      B.w = w;
-      B.t0 = t0[i];
-      B.t1 = t1[i];
-      B.k0 = static_cast<uint32_t>(S->seed);
-      B.k1 = static_cast<uint32_t>(S->seed >> 32);
-      by_kq[q].push_back(B);
-      cost[q].push_back(static_cast<long long>(I->ks.n_occ + I->ks.n) * (t1[i] - t0[i]));
-      if (I->ks.n > max_n[q]) max_n[q] = I->ks.n;
+  BatchPlan plan;
+  const int rc = batch_plan(ctx, n_sets, rs, t0, t1, &plan);
+  if (rc != NMC_OK) return rc;
+  return launch_items(ctx, plan.items, plan.off, plan.cnt, plan.max_n, plan.cs, false);
+}
+
+int nmc_replicas_set_ladder(nmc_ctx *ctx, int32_t rs, int32_t n_temps, const float *ladder,
+                            const int32_t *slots) {
+  if (!ctx) return NMC_EINVAL;
+  ReplicaSet *S = find_set(ctx, rs);
+  if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
+  Instance *I = find_inst(ctx, S->inst);
+  if (!I) return fail(ctx, NMC_ESTATE, "instance was unloaded");
+  int rc = check_batchable(ctx, *I);
+  if (rc != NMC_OK) return rc;
+  if (n_temps < 1 || !ladder || S->R % n_temps != 0)
+    return fail(ctx, NMC_EINVAL, "need a ladder of n_temps >= 1 temperatures dividing R");
+  const int32_t R = S->R, L = n_temps, G = R / L, W = S->ks.W;
+  std::vector<uint32_t> lq(L);
+  for (int32_t k = 0; k < L; ++k) {
+    const float b = ladder[k];
+    if (!(b >= 0.0f && b <= 65535.0f))
+      return fail(ctx, NMC_EINVAL, "ladder temperatures must be finite and in [0, 65535]");
+    lq[k] = static_cast<uint32_t>(std::nearbyint(static_cast<double>(b) * 65536.0));
+  }
+  std::vector<int32_t> slot(R), at(R);
+  std::vector<uint32_t> mult(32 * static_cast<size_t>(W), 65536u);
+  std::vector<char> seen(L);
+  for (int32_t g = 0; g < G; ++g) {
+    std::fill(seen.begin(), seen.end(), 0);
+    for (int32_t i = 0; i < L; ++i) {
+      const int32_t r = g * L + i;
+      const int32_t k = slots ? slots[r] : i;
+      if (k < 0 || k >= L || seen[k])
+        return fail(ctx, NMC_EINVAL, "each ladder's slots must be a permutation of 0..n_temps-1");
+      seen[k] = 1;
+      slot[r] = k;
+      at[static_cast<size_t>(g) * L + k] = r;
+      mult[r] = lq[k];
     }
   }
-  const size_t total = by_kq[0].size() + by_kq[1].size();
-  if (total == 0) return NMC_OK;
-  if (total > ctx->items_cap) {
-    NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
-    dev_free(ctx->items);
-    ctx->items_cap = 0;
-    NMC_CUDA(dev_alloc(&ctx->items, total), "allocate batch work list");
-    ctx->items_cap = total;
+  DeviceGuard dg(ctx->device);
+  // earlier launches may still read the old arrays
+  NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  if (S->pt_L != L) {
+    dev_free(S->pt_lq);
+    S->pt_L = 0;
+    NMC_CUDA(dev_alloc(&S->pt_lq, L), "allocate ladder");
   }
-  if (!ctx->next_item) NMC_CUDA(dev_alloc(&ctx->next_item, 2), "allocate batch counters");
-  // longest items first, so that the tail of the launch is short
-  std::vector<BatchItem> order;
-  order.reserve(total);
-  size_t off[2] = {0, 0};
-  for (int q = 0; q < 2; ++q) {
-    std::vector<size_t> idx(by_kq[q].size());
-    for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return cost[q][a] > cost[q][b]; });
-    off[q] = order.size();
-    for (size_t k : idx) order.push_back(by_kq[q][k]);
-  }
-  NMC_CUDA(cudaMemcpyAsync(ctx->items, order.data(), sizeof(BatchItem) * total, cudaMemcpyHostToDevice,
-                           ctx->stream),
-           "upload batch work list");
-  int sms = 0;
-  NMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "query SMs");
-  for (int q = 0; q < 2; ++q) {
-    const int cnt = static_cast<int>(by_kq[q].size());
-    if (!cnt) continue;
-    // CTAs per item: spread few items over the SMs (word vectors replicated per cluster)
-    int cs = 1;
-    if (const char *env = getenv("NMC_BATCH_CTAS")) cs = atoi(env);
-    else
-      while (cs < 8 && static_cast<long long>(cnt) * cs * 2 <= sms) cs *= 2;
-    if (cs != 1 && cs != 2 && cs != 4 && cs != 8) cs = 1;
-    NMC_CUDA(ksat_batch(ctx->items + off[q], cnt, q + 1, cs, max_n[q], ctx->next_item + q,
-                        ctx->tab, ctx->tab_len, ctx->device, ctx->stream),
-             "launch batched sweep");
-  }
-  // the host vector is staged by cudaMemcpyAsync from pageable memory before it returns
+  if (!S->pt_slot) NMC_CUDA(dev_alloc(&S->pt_slot, R), "allocate ladder slots");
+  if (!S->pt_at) NMC_CUDA(dev_alloc(&S->pt_at, R), "allocate ladder slots");
+  if (!S->pt_mult) NMC_CUDA(dev_alloc(&S->pt_mult, mult.size()), "allocate ladder multipliers");
+  NMC_CUDA(cudaMemcpyAsync(S->pt_lq, lq.data(), sizeof(uint32_t) * L, cudaMemcpyHostToDevice, ctx->stream), "upload ladder");
+  NMC_CUDA(cudaMemcpyAsync(S->pt_slot, slot.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, ctx->stream), "upload slots");
+  NMC_CUDA(cudaMemcpyAsync(S->pt_at, at.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, ctx->stream), "upload slots");
+  NMC_CUDA(cudaMemcpyAsync(S->pt_mult, mult.data(), sizeof(uint32_t) * mult.size(), cudaMemcpyHostToDevice, ctx->stream), "upload multipliers");
+  NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  S->pt_L = L;
   return NMC_OK;
+}
+
+int nmc_replicas_run_pt(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1,
+                        int32_t sweeps_per_round) {
+  if (!ctx) return NMC_EINVAL;
+  ReplicaSet *S = find_set(ctx, rs);
+  if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
+  Instance *I = find_inst(ctx, S->inst);
+  if (!I) return fail(ctx, NMC_ESTATE, "instance was unloaded");
+  int rc = check_batchable(ctx, *I);
+  if (rc != NMC_OK) return rc;
+  if (S->pt_L < 1) return fail(ctx, NMC_ESTATE, "no ladder attached (nmc_replicas_set_ladder)");
+  if (sweeps_per_round < 1) return fail(ctx, NMC_EINVAL, "sweeps_per_round must be >= 1");
+  if (t0 < 0 || t1 < t0) return fail(ctx, NMC_EINVAL, "need 0 <= t0 <= t1");
+  if (t1 > t0 && (!I->bq || t1 > I->n_steps))
+    return fail(ctx, NMC_ESTATE, "schedule missing or shorter than t1");
+  if (t1 == t0) return NMC_OK;
+  DeviceGuard dg(ctx->device);
+  const int32_t W = S->ks.W, L = S->pt_L, G = S->R / L, per = sweeps_per_round;
+  const int kq = I->ks.kq;
+  const int cs = ctas_per_item(ctx, W);
+  // segments end at t1 or after sweep t with (t+1) % per == 0, where an exchange round follows;
+  // their work items are uploaded in chunks
+  const int64_t max_chunk_items = std::max<int64_t>(W, 1 << 18);
+  std::vector<BatchItem> items;
+  std::vector<std::pair<int32_t, int32_t>> seg;
+  int32_t t = t0;
+  while (t < t1) {
+    items.clear();
+    seg.clear();
+    while (t < t1 && static_cast<int64_t>(seg.size() + 1) * W <= max_chunk_items) {
+      const int64_t te = std::min<int64_t>(t1, (static_cast<int64_t>(t) / per + 1) * per);
+      seg.push_back({t, static_cast<int32_t>(te)});
+      for (int32_t w = 0; w < W; ++w) {
+        BatchItem B = ksat_item(*I, *S, w, t, static_cast<int32_t>(te));
+        B.mult = S->pt_mult;
+        items.push_back(B);
+      }
+      t = static_cast<int32_t>(te);
+    }
+    rc = reserve_items(ctx, items.size());
+    if (rc != NMC_OK) return rc;
+    NMC_CUDA(cudaMemcpyAsync(ctx->items, items.data(), sizeof(BatchItem) * items.size(),
+                             cudaMemcpyHostToDevice, ctx->stream),
+             "upload work list");
+    for (size_t i = 0; i < seg.size(); ++i) {
+      NMC_CUDA(ksat_batch(ctx->items + i * W, W, kq, cs, I->ks.n, ctx->next_item, ctx->tab,
+                          ctx->tab_len, ctx->device, ctx->stream, true),
+               "launch sweeps");
+      const int32_t te = seg[i].second;
+      if (te % per == 0)
+        NMC_CUDA(pt_exchange(S->pt_lq, L, G, S->ks.energy, S->pt_slot, S->pt_at, S->pt_mult,
+                             ctx->tab, ctx->tab_len, static_cast<uint32_t>(te / per - 1),
+                             static_cast<uint32_t>(S->seed), static_cast<uint32_t>(S->seed >> 32),
+                             ctx->stream),
+                 "launch exchange round");
+    }
+  }
+  return NMC_OK;
+}
+
+int nmc_replicas_read_slots(nmc_ctx *ctx, int32_t rs, int32_t *slots_out) {
+  if (!ctx) return NMC_EINVAL;
+  if (!slots_out) return fail(ctx, NMC_EINVAL, "slots_out is NULL");
+  ReplicaSet *S = find_set(ctx, rs);
+  if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
+  if (S->pt_L < 1) return fail(ctx, NMC_ESTATE, "no ladder attached (nmc_replicas_set_ladder)");
+  DeviceGuard dg(ctx->device);
+  NMC_CUDA(cudaMemcpyAsync(slots_out, S->pt_slot, sizeof(int32_t) * S->R, cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "read slots");
+  NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  return NMC_OK;
+}
+
+int nmc_adaptive_ladder(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t seed, double beta0,
+                        double alpha, double sigma_min, int32_t max_temps, int32_t sweeps_eq,
+                        int32_t sweeps_meas, double *betas_out, double *sigmas_out,
+                        int32_t *n_temps_out) {
+  if (!ctx) return NMC_EINVAL;
+  Instance *I = find_inst(ctx, inst);
+  if (!I) return fail(ctx, NMC_EINVAL, "unknown instance");
+  int rc = check_batchable(ctx, *I);
+  if (rc != NMC_OK) return rc;
+  if (!betas_out || !sigmas_out || !n_temps_out) return fail(ctx, NMC_EINVAL, "NULL output");
+  if (max_temps < 1 || sweeps_eq < 0 || sweeps_meas < 1)
+    return fail(ctx, NMC_EINVAL, "need max_temps >= 1, sweeps_eq >= 0, sweeps_meas >= 1");
+  if (!std::isfinite(alpha) || !std::isfinite(sigma_min) || !std::isfinite(beta0) || sigma_min < 0.0)
+    return fail(ctx, NMC_EINVAL, "beta0 and alpha must be finite, sigma_min finite and >= 0");
+  const int64_t T = static_cast<int64_t>(sweeps_eq) + sweeps_meas;
+  if (T * max_temps > 0x7FFFFFFF) return fail(ctx, NMC_EINVAL, "too many sweeps in total");
+  // the energy sums stay exact: m^2 * replicas * sweeps_meas < 2^62
+  const double mm = static_cast<double>(I->ks.m);
+  if (mm * mm * replicas * sweeps_meas >= 4.6e18)
+    return fail(ctx, NMC_EINVAL, "energy sums could overflow: fewer replicas or sweeps");
+  *n_temps_out = 0;
+  int32_t rs = 0;
+  rc = nmc_replicas_create(ctx, inst, replicas, seed, nullptr, &rs);
+  if (rc != NMC_OK) return rc;
+  ReplicaSet *S = find_set(ctx, rs);
+  DeviceGuard dg(ctx->device);
+  const int32_t n = I->ks.n, W = S->ks.W;
+  uint32_t *bq = nullptr, *mult = nullptr;
+  long long *stats = nullptr;
+  double *out_dev = nullptr;
+  cudaError_t e = cudaSuccess;
+  const std::vector<uint32_t> ones(32 * static_cast<size_t>(W), 65536u);
+  if ((e = dev_alloc(&bq, static_cast<size_t>(n) * T)) != cudaSuccess ||
+      (e = dev_alloc(&mult, ones.size())) != cudaSuccess ||
+      (e = dev_alloc(&stats, 64 * static_cast<size_t>(W))) != cudaSuccess ||
+      (e = dev_alloc(&out_dev, 2)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(mult, ones.data(), sizeof(uint32_t) * ones.size(), cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess)
+    rc = cuda_fail(ctx, e, "allocate ladder scratch");
+  double beta = beta0;
+  for (int32_t i = 0; rc == NMC_OK && i < max_temps; ++i) {
+    const float bf = static_cast<float>(beta);
+    if (!(bf >= 0.0f && bf <= 65535.0f)) {
+      rc = fail(ctx, NMC_EINVAL, "a ladder temperature left [0, 65535]");
+      break;
+    }
+    const int32_t ts = static_cast<int32_t>(i * T), te = static_cast<int32_t>(ts + T);
+    std::vector<BatchItem> items;
+    for (int32_t w = 0; w < W; ++w) {
+      BatchItem B = ksat_item(*I, *S, w, ts, te);
+      // the level's schedule holds sweeps [ts, te) only: the item's base pointer is moved back
+      // by ts steps so that the kernel's index t * n + v lands in it (no access before bq)
+      B.bq = reinterpret_cast<const uint32_t *>(reinterpret_cast<uintptr_t>(bq) -
+                                                sizeof(uint32_t) * static_cast<size_t>(ts) * n);
+      B.mult = mult;
+      B.stats = stats;
+      B.stats_t0 = ts + sweeps_eq;
+      items.push_back(B);
+    }
+    const int q = I->ks.kq == 1 ? 0 : 1;
+    size_t off[2] = {0, 0};
+    int cnt[2] = {0, 0}, max_n[2] = {0, 0}, cs[2] = {1, 1};
+    cnt[q] = W;
+    max_n[q] = n;
+    cs[q] = ctas_per_item(ctx, W);
+    if ((e = fill_schedule(bq, static_cast<size_t>(n) * T, beta, ctx->flag, ctx->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(stats, 0, sizeof(long long) * 64 * W, ctx->stream)) != cudaSuccess) {
+      rc = cuda_fail(ctx, e, "prepare ladder level");
+      break;
+    }
+    rc = launch_items(ctx, items, off, cnt, max_n, cs, true);
+    if (rc != NMC_OK) break;
+    double out[2] = {0.0, 0.0};
+    if ((e = ladder_step(stats, S->R, W, static_cast<long long>(S->R) * sweeps_meas, beta, alpha,
+                         out_dev, ctx->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(out, out_dev, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+      rc = cuda_fail(ctx, e, "ladder level");
+      break;
+    }
+    betas_out[i] = beta;
+    sigmas_out[i] = out[0];
+    *n_temps_out = i + 1;
+    if (out[0] <= sigma_min) break;
+    beta = out[1];
+  }
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(bq);
+  dev_free(mult);
+  dev_free(stats);
+  dev_free(out_dev);
+  const std::string keep = ctx->err;
+  const int rc2 = nmc_replicas_destroy(ctx, rs);
+  if (rc != NMC_OK) {
+    ctx->err = keep;
+    return rc;
+  }
+  return rc2;
 }
 
 int nmc_anneal(nmc_ctx *ctx, int32_t inst, int32_t replicas, int32_t t0, int32_t t1,

@@ -95,12 +95,13 @@ __device__ __forceinline__ uint32_t lit_word(const uint32_t *xs, int l) {
   return xs[l >> 1] ^ (0u - (uint32_t)(l & 1));
 }
 
-// v = c0 + off is a variable of colour class c (starting at new id c0).
-template <int KQ>
+// v = c0 + off is a variable of colour class c (starting at new id c0). With PT, replica j
+// of the word moves at min(2^32-1, (mult_s[j] * bq) >> 16) instead of bq.
+template <int KQ, bool PT>
 __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint32_t *xs,
-                                                  const uint32_t *tab_s, int tab_len, int c,
-                                                  int c0, int v, int t,
-                                                  uint32_t (&acc)[kAccPlanes]) {
+                                                  const uint32_t *tab_s, int tab_len,
+                                                  const uint32_t *mult_s, int c, int c0, int v,
+                                                  int t, uint32_t (&acc)[kAccPlanes]) {
   constexpr int NB = 7;
   const uint32_t x = xs[v];
   const uint32_t bqv = __ldg(B.bq + (size_t)t * B.n + v);
@@ -183,7 +184,14 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
         de[j] = (int)(signed char)(unsigned char)(xm >> (8 * (4 * h + j)));
         th[j] = 0u;
         if (de[j] > 0) {
-          const uint32_t idx = bq_hi * (uint32_t)de[j] + ((bq_lo * (uint32_t)de[j]) >> 8);
+          uint32_t hi = bq_hi, lo = bq_lo;
+          if (PT) {
+            const unsigned long long be = ((unsigned long long)mult_s[4 * g + j] * bqv) >> 16;
+            const uint32_t b = be > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)be;
+            hi = b >> 8;  // below 2^24, so hi dE stays below 2^31
+            lo = b & 255u;
+          }
+          const uint32_t idx = hi * (uint32_t)de[j] + ((lo * (uint32_t)de[j]) >> 8);
           th[j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
         }
         need |= th[j] != 0u;
@@ -237,7 +245,9 @@ __device__ __forceinline__ T *rank_ptr(T *p, int r) {
 // CS = CTAs per item. With CS > 1 every CTA of the cluster keeps a full copy of the item's
 // word vector; each CTA updates its share of every colour class and stores the new words
 // into all CS copies (distributed shared memory), then the cluster barrier publishes them.
-template <int KQ, int CS>
+// PT: every item carries per-replica temperature multipliers and, optionally, accumulates the
+// end-of-sweep energies of sweeps t >= stats_t0 (sums of E and E^2 per replica).
+template <int KQ, int CS, bool PT>
 __global__ void __launch_bounds__(kBatchThreads, 1)
     ksat_batch_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
                       const uint32_t *tab, int tab_len, int xs_words) {
@@ -245,6 +255,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   uint32_t *xs = smem;                               // word vector first (byte offsets in lists)
   uint32_t *tab_s = smem + ((xs_words + 31) & ~31);  // then the acceptance table
   __shared__ int e_s[32], be_s[32], ep_s[32];
+  __shared__ uint32_t mult_s[32];
   __shared__ uint32_t imp_s;
   __shared__ int item_s;
   __shared__ BatchItem item_b;  // the current item, read from shared memory where needed
@@ -265,11 +276,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     if (threadIdx.x == 0) xs[n] = 0u;
     if (threadIdx.x < 32) {
       ep_s[threadIdx.x] = 0;
+      if (PT) mult_s[threadIdx.x] = B.mult[32 * w + threadIdx.x];
       if (rank == 0) {
         e_s[threadIdx.x] = B.energy[32 * w + threadIdx.x];
         be_s[threadIdx.x] = B.best_energy[32 * w + threadIdx.x];
       }
     }
+    long long s1 = 0, s2 = 0;  // energy statistics of this lane's replica (rank 0, warp 0)
     group_sync<CS>();
     for (int t = B.t0; t < B.t1; ++t) {
       uint32_t acc[kAccPlanes];
@@ -280,7 +293,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
         const int part = ((c1 - c0 + CS - 1) / CS + 31) & ~31;  // whole 32-variable groups
         const int v0 = c0 + rank * part, v1 = min(c1, v0 + part);
         for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-          const uint32_t xn = attempt_batch<KQ>(B, xs, tab_s, tab_len, c, c0, v, t, acc);
+          const uint32_t xn = attempt_batch<KQ, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, v, t, acc);
           if (CS == 1) {
             xs[v] = xn;
           } else {
@@ -311,6 +324,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 #pragma unroll
         for (int r = 0; r < CS; ++r) sum += rank_ptr<CS>(ep_s, r)[lane];
         e_s[lane] = sum;
+        if (PT && B.stats && t >= B.stats_t0) {
+          s1 += sum;
+          s2 += (long long)sum * sum;
+        }
         const bool better = sum < be_s[lane];
         if (better) be_s[lane] = sum;
         const unsigned m = __ballot_sync(0xFFFFFFFFu, better);
@@ -338,6 +355,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     if (rank == 0 && threadIdx.x < 32) {
       B.energy[32 * w + threadIdx.x] = e_s[threadIdx.x];
       B.best_energy[32 * w + threadIdx.x] = be_s[threadIdx.x];
+      if (PT && B.stats) {  // one item per word in a launch: plain read-modify-write
+        B.stats[32 * w + threadIdx.x] += s1;
+        B.stats[32 * (B.W + w) + threadIdx.x] += s2;
+      }
     }
     group_sync<CS>();
   }
@@ -364,10 +385,11 @@ __device__ __forceinline__ void add_planes(uint32_t (&c)[NB], const uint32_t (&p
   }
 }
 
-template <int KQ, int TL>
+template <int KQ, int TL, bool PT>
 __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint32_t *xs,
-                                                 const uint32_t *tab_s, int tab_len, int c,
-                                                 int c0, int v, bool active, int t, int tl,
+                                                 const uint32_t *tab_s, int tab_len,
+                                                 const uint32_t *mult_s, int c, int c0, int v,
+                                                 bool active, int t, int tl,
                                                  int (&acc)[32 / TL]) {
   constexpr int NB = 7;
   const uint32_t x = active ? xs[v] : 0u;
@@ -457,7 +479,14 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
       de[j] = val;
       th[j] = 0u;
       if (val > 0) {
-        const uint32_t idx = bq_hi * (uint32_t)val + ((bq_lo * (uint32_t)val) >> 8);
+        uint32_t hi = bq_hi, lo = bq_lo;
+        if (PT) {
+          const unsigned long long be = ((unsigned long long)mult_s[r] * bqv) >> 16;
+          const uint32_t b = be > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)be;
+          hi = b >> 8;
+          lo = b & 255u;
+        }
+        const uint32_t idx = hi * (uint32_t)val + ((lo * (uint32_t)val) >> 8);
         th[j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
       }
       need |= th[j] != 0u;
@@ -478,7 +507,7 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
   return x ^ flip;
 }
 
-template <int KQ, int CS, int TL>
+template <int KQ, int CS, int TL, bool PT>
 __global__ void __launch_bounds__(kBatchThreads, 1)
     ksat_team_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
                      const uint32_t *tab, int tab_len, int xs_words) {
@@ -486,6 +515,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   uint32_t *xs = smem;                               // word vector first (byte offsets in lists)
   uint32_t *tab_s = smem + ((xs_words + 31) & ~31);  // then the acceptance table
   __shared__ int e_s[32], be_s[32], ep_s[32];
+  __shared__ uint32_t mult_s[32];
   __shared__ uint32_t imp_s;
   __shared__ int item_s;
   __shared__ BatchItem item_b;
@@ -509,11 +539,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     if (threadIdx.x == 0) xs[n] = 0u;
     if (threadIdx.x < 32) {
       ep_s[threadIdx.x] = 0;
+      if (PT) mult_s[threadIdx.x] = B.mult[32 * w + threadIdx.x];
       if (rank == 0) {
         e_s[threadIdx.x] = B.energy[32 * w + threadIdx.x];
         be_s[threadIdx.x] = B.best_energy[32 * w + threadIdx.x];
       }
     }
+    long long s1 = 0, s2 = 0;  // energy statistics of this lane's replica (rank 0, warp 0)
     group_sync<CS>();
     for (int t = B.t0; t < B.t1; ++t) {
       int acc[32 / TL];
@@ -527,7 +559,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
         for (int vw = v0 + warp * (32 / TL); vw < v1; vw += nteams) {
           const int v = vw + (lane / TL);
           const bool active = v < v1;
-          const uint32_t xn = attempt_team<KQ, TL>(B, xs, tab_s, tab_len, c, c0, v, active, t, tl, acc);
+          const uint32_t xn =
+              attempt_team<KQ, TL, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, v, active, t, tl, acc);
           if (active && tl == 0) {
             if (CS == 1) {
               xs[v] = xn;
@@ -549,6 +582,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 #pragma unroll
         for (int r = 0; r < CS; ++r) sum += rank_ptr<CS>(ep_s, r)[lane];
         e_s[lane] = sum;
+        if (PT && B.stats && t >= B.stats_t0) {
+          s1 += sum;
+          s2 += (long long)sum * sum;
+        }
         const bool better = sum < be_s[lane];
         if (better) be_s[lane] = sum;
         const unsigned m = __ballot_sync(0xFFFFFFFFu, better);
@@ -576,6 +613,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     if (rank == 0 && threadIdx.x < 32) {
       B.energy[32 * w + threadIdx.x] = e_s[threadIdx.x];
       B.best_energy[32 * w + threadIdx.x] = be_s[threadIdx.x];
+      if (PT && B.stats) {  // one item per word in a launch: plain read-modify-write
+        B.stats[32 * w + threadIdx.x] += s1;
+        B.stats[32 * (B.W + w) + threadIdx.x] += s2;
+      }
     }
     group_sync<CS>();
   }
@@ -584,13 +625,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 
 // The launch shape of each kernel instance is queried once per (device, shared-memory size):
 // occupancy and cluster queries are slow host calls.
-template <int KQ, int CS, int TL>
+template <int KQ, int CS, int TL, bool PT = false>
 cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
                          const uint32_t *tab, int tab_len, int max_n, int device,
                          cudaStream_t st) {
   const int xs_words = max_n + 1;
   const size_t smem = sizeof(uint32_t) * (((size_t)xs_words + 31) / 32 * 32 + (size_t)tab_len + 1);
-  auto kern = TL == 1 ? ksat_batch_kernel<KQ, CS> : ksat_team_kernel<KQ, CS, (TL > 1 ? TL : 4)>;
+  auto kern = TL == 1 ? ksat_batch_kernel<KQ, CS, PT> : ksat_team_kernel<KQ, CS, (TL > 1 ? TL : 4), PT>;
   static std::mutex mu;
   static std::map<std::pair<int, size_t>, int> shapes;  // (device, smem) -> resident clusters
   static std::map<int, size_t> smem_set;                // device -> largest smem attribute set
@@ -670,7 +711,14 @@ int batch_lanes(int cs, int max_n) {
 
 template <int KQ, int CS>
 cudaError_t dispatch_lanes(const BatchItem *items, int n_items, int *next_item, const uint32_t *tab,
-                           int tab_len, int max_n, int device, cudaStream_t st) {
+                           int tab_len, int max_n, int device, cudaStream_t st, bool pt) {
+  if (pt) {
+    switch (batch_lanes(CS, max_n)) {
+      case 4: return launch_batch<KQ, CS, 4, true>(items, n_items, next_item, tab, tab_len, max_n, device, st);
+      case 8: return launch_batch<KQ, CS, 8, true>(items, n_items, next_item, tab, tab_len, max_n, device, st);
+      default: return launch_batch<KQ, CS, 1, true>(items, n_items, next_item, tab, tab_len, max_n, device, st);
+    }
+  }
   switch (batch_lanes(CS, max_n)) {
     case 4: return launch_batch<KQ, CS, 4>(items, n_items, next_item, tab, tab_len, max_n, device, st);
     case 8: return launch_batch<KQ, CS, 8>(items, n_items, next_item, tab, tab_len, max_n, device, st);
@@ -680,12 +728,13 @@ cudaError_t dispatch_lanes(const BatchItem *items, int n_items, int *next_item, 
 
 template <int KQ>
 cudaError_t dispatch_batch(int cs, const BatchItem *items, int n_items, int *next_item,
-                           const uint32_t *tab, int tab_len, int max_n, int device, cudaStream_t st) {
+                           const uint32_t *tab, int tab_len, int max_n, int device, cudaStream_t st,
+                           bool pt) {
   switch (cs) {
-    case 8: return dispatch_lanes<KQ, 8>(items, n_items, next_item, tab, tab_len, max_n, device, st);
-    case 4: return dispatch_lanes<KQ, 4>(items, n_items, next_item, tab, tab_len, max_n, device, st);
-    case 2: return dispatch_lanes<KQ, 2>(items, n_items, next_item, tab, tab_len, max_n, device, st);
-    default: return dispatch_lanes<KQ, 1>(items, n_items, next_item, tab, tab_len, max_n, device, st);
+    case 8: return dispatch_lanes<KQ, 8>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt);
+    case 4: return dispatch_lanes<KQ, 4>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt);
+    case 2: return dispatch_lanes<KQ, 2>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt);
+    default: return dispatch_lanes<KQ, 1>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt);
   }
 }
 
@@ -699,7 +748,7 @@ cudaError_t dispatch_batch(int cs, const BatchItem *items, int n_items, int *nex
 constexpr size_t kNoAllocBytes = 1u << 20;  // 1 MiB on every GPU that loads the library
 constexpr size_t kNoAllocHeader = 256;      // two int counters, padded to the item alignment
 constexpr size_t kNoAllocItems = (kNoAllocBytes - kNoAllocHeader) / sizeof(BatchItem);
-static_assert(sizeof(BatchItem) == 112 && kNoAllocItems == 9360, "limit stated in nmc.h");
+static_assert(sizeof(BatchItem) == 136 && kNoAllocItems == 7708, "limit stated in nmc.h");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -784,10 +833,10 @@ size_t batch_max_vars(int tab_len, int device) {
 
 cudaError_t ksat_batch(const BatchItem *items_dev, int n_items, int kq, int cs, int max_n,
                        int *next_item, const uint32_t *tab, int tab_len, int device,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool pt) {
   if (n_items <= 0) return cudaSuccess;
-  if (kq == 1) return dispatch_batch<1>(cs, items_dev, n_items, next_item, tab, tab_len, max_n, device, st);
-  return dispatch_batch<2>(cs, items_dev, n_items, next_item, tab, tab_len, max_n, device, st);
+  if (kq == 1) return dispatch_batch<1>(cs, items_dev, n_items, next_item, tab, tab_len, max_n, device, st, pt);
+  return dispatch_batch<2>(cs, items_dev, n_items, next_item, tab, tab_len, max_n, device, st, pt);
 }
 
 }  // namespace nmc

@@ -16,6 +16,7 @@ constexpr uint32_t kTagKsatInit = 0x4B494E49u;
 constexpr uint32_t kTagKsatSweep = 0x4B535750u;
 constexpr uint32_t kTagQapInit = 0x51494E49u;
 constexpr uint32_t kTagQapStep = 0x51535450u;
+constexpr uint32_t kTagPtSwap = 0x50545357u;
 
 constexpr int kTabCap = 8192;    // capacity of the acceptance-threshold table
 constexpr int kMaxReplicas = 4096;
@@ -89,6 +90,11 @@ struct BatchItem {
   int32_t *best_energy;
   int32_t n, n_colours, W, w, t0, t1;
   uint32_t k0, k1;
+  // Replica exchange and energy statistics (kernels instantiated for them only):
+  const uint32_t *mult;  // 32W Q16 temperature multipliers of the replicas, or null
+  long long *stats;      // 64W: per-replica sums of E (first 32W) and E^2 (next 32W), or null
+  int32_t stats_t0;      // sweeps t >= stats_t0 add their end-of-sweep energies to stats
+  int32_t pad_;
 };
 
 // ---- k-SAT launchers (ksat.cu); all asynchronous on `st` -------------------------------
@@ -119,10 +125,11 @@ cudaError_t quantize_schedule(const float *beta, int32_t n_units, int32_t n_step
 // Largest n whose word vector fits the batched kernel's shared memory on `device`.
 size_t batch_max_vars(int tab_len, int device);
 // Runs n_items items (all of one occurrence width kq) in one launch with cs CTAs (1, 2, 4, 8)
-// per item; next_item is a device int.
+// per item; next_item is a device int. With pt, every item carries temperature multipliers
+// (mult) and may carry energy statistics.
 cudaError_t ksat_batch(const BatchItem *items_dev, int n_items, int kq, int cs, int max_n,
                        int *next_item, const uint32_t *tab, int tab_len, int device,
-                       cudaStream_t st);
+                       cudaStream_t st, bool pt = false);
 
 // A validated batched launch, ready to be placed into device memory: the work items in launch
 // order (occurrence width 1 first, then 2), with their counts, shapes and the context's
@@ -157,6 +164,21 @@ struct HostKsat {
 int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t *lits,
                  HostKsat *out);
 int upload_ksat(nmc_ctx *ctx, HostKsat &h, int32_t *inst_out);
+
+// ---- replica exchange and the adaptive ladder (pt.cu) ----------------------------------
+// One exchange round q of G ladders of L slots (replica g*L + i belongs to ladder g): the
+// pairs of slots (k, k+1), k = q mod 2, k+2, ..., of every ladder exchange their replicas on
+// the Metropolis test of (lq[k] - lq[k+1]) (E_a - E_b); slot, at and mult follow the swaps.
+cudaError_t pt_exchange(const uint32_t *lq, int32_t L, int32_t G, const int32_t *energy,
+                        int32_t *slot, int32_t *at, uint32_t *mult, const uint32_t *tab,
+                        int32_t tab_len, uint32_t round, uint32_t k0, uint32_t k1,
+                        cudaStream_t st);
+// bq[i] = Q16(float(beta)) for i < count (a constant schedule).
+cudaError_t fill_schedule(uint32_t *bq, size_t count, double beta, int32_t *bad, cudaStream_t st);
+// From per-replica energy sums over `samples` sweeps of R replicas: sigma = sqrt(<E^2> - <E>^2)
+// (IEEE double, no contraction); out[0] = sigma, out[1] = beta + alpha / sigma.
+cudaError_t ladder_step(const long long *stats, int32_t R, int32_t W, long long samples,
+                        double beta, double alpha, double *out, cudaStream_t st);
 
 // ---- QAP launchers (qap.cu) ------------------------------------------------------------
 // Arguments of one QAP launch (or, in a batched launch, of one CTA: one block of 32 replicas).

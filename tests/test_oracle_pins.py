@@ -434,15 +434,25 @@ def test_pt_with_equal_ladder_is_the_plain_chain():
     dynamics (Philox streams by replica id) are those of the plain anneal."""
     wl = W.workload_ksat_small(24)
     lits, n, beta = wl["lits"], wl["n_vars"], wl["beta"]
-    R = 12
-    pt = O.ksat_pt_anneal(lits, n, beta, np.ones(R, np.float32), 0, 24, 3, seed=4)
-    plain = O.ksat_anneal(lits, n, beta, 0, 24, 4, replicas=R)
+    L, G = 12, 3
+    pt = O.ksat_pt_anneal(lits, n, beta, np.ones(L, np.float32), 0, 24, 3, seed=4,
+                          replicas=G * L)
+    plain = O.ksat_anneal(lits, n, beta, 0, 24, 4, replicas=G * L)
     for key in ("states", "energies", "best_energies", "best_states"):
         assert np.array_equal(pt[key], plain[key]), key
-    assert sorted(pt["slots"].tolist()) == list(range(R))
-    # 8 rounds of accepted even/odd exchanges move replica 0 to slot 8 (+1 per round while the
-    # pairing allows: a closed-form walk of the first replica)
-    assert pt["slots"][0] == 8
+    # every ladder exchanges within itself: its slots stay a permutation of 0..L-1, and with
+    # every exchange accepted the slots follow the closed-form walk of the even/odd pairing:
+    # after 8 rounds the replica that started at slot 0 of each ladder sits at slot 8
+    for g in range(G):
+        assert sorted(pt["slots"][g * L:(g + 1) * L].tolist()) == list(range(L))
+        assert pt["slots"][g * L] == 8
+    walk = np.arange(L)
+    for q in range(8):
+        for k in range(q & 1, L - 1, 2):
+            a, b = np.where(walk == k)[0][0], np.where(walk == k + 1)[0][0]
+            walk[a], walk[b] = k + 1, k
+    for g in range(G):
+        assert np.array_equal(pt["slots"][g * L:(g + 1) * L], walk)
 
 
 def test_pt_segments_and_invariants():
@@ -475,9 +485,9 @@ def test_pt_exchange_keeps_each_slot_boltzmann():
     beta = W.beta_constant(n, T, 1.0)
     E = energies_numpy(lits, all_states(n))
     counts = [np.zeros(2 ** n), np.zeros(2 ** n)]
-    for run in range(2500):
-        res = O.ksat_pt_anneal(lits, n, beta, ladder, 0, T, 1, seed=1000 + run)
-        for r in range(2):
+    for run in range(1250):  # two ladders per run
+        res = O.ksat_pt_anneal(lits, n, beta, ladder, 0, T, 1, seed=1000 + run, replicas=4)
+        for r in range(4):
             k = res["slots"][r]
             idx = int((res["states"][r].astype(np.int64) << np.arange(n)).sum())
             counts[k][idx] += 1
@@ -486,3 +496,76 @@ def test_pt_exchange_keeps_each_slot_boltzmann():
         assert _chi2_pvalue(counts[k], w / w.sum()) > 1e-4, k
     w_swapped = np.exp(-float(ladder[1]) * E)
     assert _chi2_pvalue(counts[0], w_swapped / w_swapped.sum()) < 1e-6
+
+
+# ---------------------------------------------------------------- energy statistics, ladder
+def test_energy_statistics_match_the_recorded_trajectory():
+    """The sums of E and E^2 over sweeps >= stats_from equal those of the trajectory recorded
+    one sweep at a time, with every energy recounted by the independent evaluator."""
+    wl = W.workload_ksat_small(30)
+    lits, n, beta, R = wl["lits"], wl["n_vars"], wl["beta"], 10
+    res = O.ksat_anneal(lits, n, beta, 3, 30, 9, replicas=R, stats_from=12)
+    s1 = np.zeros(R, np.int64)
+    s2 = np.zeros(R, np.int64)
+    state = dict(init=None)
+    x = None
+    for t in range(3, 30):
+        if x is None:
+            step = O.ksat_anneal(lits, n, beta, 3, 4, 9, replicas=R)
+        else:
+            step = O.ksat_anneal(lits, n, beta, t, t + 1, 9, replicas=R, init=x)
+        x = step["states"]
+        if t >= 12:
+            e = energies_numpy(lits, x)
+            s1 += e
+            s2 += e * e
+    assert np.array_equal(res["states"], x)
+    assert np.array_equal(res["e_sum"], s1) and np.array_equal(res["e_sq"], s2)
+
+
+def test_adaptive_ladder_follows_its_definition():
+    """Each sigma is the standard deviation of the recorded energies of its level (recounted
+    independently, two-pass variance), each step is beta + alpha / sigma, and the ladder stops
+    at the first sigma <= sigma_min."""
+    n = 60
+    lits = W.random_ksat(n, 4.2, 3, 21)
+    R, eq, meas = 8, 4, 6
+    betas, sigmas = O.adaptive_ladder(lits, n, R, 5, 0.2, 1.1, 0.9, 12, eq, meas)
+    T = eq + meas
+    x = None
+    for i, b in enumerate(betas):
+        sched = np.full((n, (i + 1) * T), np.float32(b), np.float32)
+        es = []
+        for t in range(i * T, (i + 1) * T):
+            step = (O.ksat_anneal(lits, n, sched, t, t + 1, 5, replicas=R) if x is None else
+                    O.ksat_anneal(lits, n, sched, t, t + 1, 5, replicas=R, init=x))
+            x = step["states"]
+            if t >= i * T + eq:
+                es.append(energies_numpy(lits, x))
+        sig = float(np.std(np.concatenate(es)))
+        assert abs(sig - sigmas[i]) <= 1e-9 * max(1.0, sig), i
+        if i + 1 < len(betas):
+            assert betas[i + 1] == b + 1.1 / sigmas[i]
+            assert sigmas[i] > 0.9
+    assert sigmas[-1] <= 0.9 or len(betas) == 12
+    assert np.all(np.diff(betas) > 0)
+    # max_temps bounds the ladder; a large sigma_min stops it at once
+    b1, s1 = O.adaptive_ladder(lits, n, R, 5, 0.2, 1.1, 1e9, 12, eq, meas)
+    assert len(b1) == 1 and b1[0] == np.float64(0.2)
+    b3, _ = O.adaptive_ladder(lits, n, R, 5, 0.2, 1.1, 0.0, 3, eq, meas)
+    assert len(b3) == 3 and np.array_equal(b3, betas[:3])
+
+
+def test_adaptive_ladder_measures_the_equilibrium_fluctuation():
+    """On a 7-variable formula the sweeps mix fast, so each level's sigma estimates the exact
+    canonical standard deviation of E at that level's beta (enumeration of all 2^7 states)."""
+    n = 7
+    lits = small_cnf(n, 24, 3, seed=8)
+    E = energies_numpy(lits, all_states(n)).astype(np.float64)
+    betas, sigmas = O.adaptive_ladder(lits, n, 256, 3, 0.1, 0.8, 0.05, 5, 20, 60)
+    assert len(betas) >= 3
+    for b, sg in zip(betas, sigmas):
+        w = np.exp(-float(np.float32(b)) * E)
+        w /= w.sum()
+        exact = math.sqrt(float((w * E * E).sum() - (w * E).sum() ** 2))
+        assert abs(sg - exact) <= 0.06 * exact + 0.01, (b, sg, exact)

@@ -56,11 +56,12 @@ def test_noalloc_rejects_more_items_than_its_array_holds():
     n = 20
     inst = ctx.load_ksat(W.random_ksat(n, 4.2, 3, 1), n)
     ctx.set_schedule(inst, W.beta_constant(n, 2, 1.0))
-    sets = [ctx.replicas_create(inst, 4096, seed=s) for s in range(74)]  # 74 x 128 = 9472 words
-    rc = _noalloc(ctx, sets, [0] * 74, [1] * 74)
+    # the array holds (1 MiB - 256 B) / 136 B = 7708 items (32-replica words)
+    sets = [ctx.replicas_create(inst, 4096, seed=s) for s in range(61)]  # 61 x 128 = 7808 words
+    rc = _noalloc(ctx, sets, [0] * 61, [1] * 61)
     assert rc == nmc.NMC_EINVAL
     assert b"scratch" in ctx._lib.nmc_last_error(ctx._h)
-    assert _noalloc(ctx, sets[:73], [0] * 73, [1] * 73) == nmc.NMC_OK  # 9344 words fit
+    assert _noalloc(ctx, sets[:60], [0] * 60, [1] * 60) == nmc.NMC_OK  # 7680 words fit
     ctx.sync()
     for s in sets:
         ctx.replicas_destroy(s)
