@@ -104,8 +104,11 @@ int nmc_ksat_colouring(nmc_ctx *ctx, int32_t inst, int32_t *colour_out, int32_t 
 /*
  * Sets the inverse-temperature profile beta[unit][step] of an instance (units = variables or
  * facilities): n_units * n_steps float32, row-major (row = one unit's schedule), host memory.
- * Every value must be finite and in [0, 65535] (checked on the device; else NMC_EINVAL). The
+ * Every value must be in [0, 65535] or +infinity (checked on the device; else NMC_EINVAL). The
  * profile is quantised to Q16 and stored step-major on the device. Replaces any earlier one.
+ * beta = +infinity holds the unit fixed at that step (the two chains of Algorithm 1 each sample
+ * one subset with the other fixed, Fig. 2 caption): a held k-SAT variable is not attempted, a
+ * QAP swap that involves a held facility is rejected; no other draw or unit is affected.
  */
 int nmc_set_schedule(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const float *beta);
 /* As nmc_set_schedule, with beta in device memory (read on the context's stream). */
@@ -218,6 +221,22 @@ int nmc_replicas_run_pt(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1,
 /* Copies the slot of every replica (R int32) of a set with a ladder to host memory
  * (synchronises). */
 int nmc_replicas_read_slots(nmc_ctx *ctx, int32_t rs, int32_t *slots_out);
+
+/*
+ * Collective move (the nonlocal flip of a whole backbone, Fig. 1(c) caption; Sec.
+ * "Nonequilibrium Nonlocal Monte Carlo"): every replica r of a k-SAT set proposes flipping all
+ * variables of its mask at once, x' = x xor m_r, and accepts with the Metropolis rule at inverse
+ * temperature beta[r] on dE = E(x') - E(x): dE <= 0 accepts; otherwise bq = Q16(beta[r]) and it
+ * accepts iff ((bq dE) >> 8) < L and u < Tab[(bq dE) >> 8], u = word r&3 of the Philox block for
+ * counter (move_id, 0, r>>2, 0x434C5354) under the set's seed. Energies follow; the best-so-far
+ * is replaced on strictly lower energy. mask: host uint8 [mask_rows][n_vars], 0/1, original
+ * variable order; mask_rows = 1 (the same mask for every replica) or R. beta: R host floats,
+ * finite and in [0, 65535]. Runs asynchronously on the context's stream; with accepted_out
+ * (host, R bytes, nullable) it synchronises and reports which replicas moved. Callers pass a
+ * different move_id for every move they want drawn independently.
+ */
+int nmc_replicas_cluster_flip(nmc_ctx *ctx, int32_t rs, int32_t mask_rows, const uint8_t *mask,
+                              const float *beta, uint32_t move_id, uint8_t *accepted_out);
 
 /*
  * Adaptive ladder (App. "Adaptive Parallel Tempering"): beta_0 = beta0; for level i the k-SAT

@@ -65,6 +65,9 @@ def _load():
             lib.orc_ksat_pt_anneal.argtypes = [i32, i32, i32, P, i32, P, i32, i32, P, P, i32, i32,
                                                i32, u64, P, P, P, P, P, P, P]
             lib.orc_ksat_pt_anneal.restype = C.c_int
+            lib.orc_ksat_cluster_flip.argtypes = [i32, i32, i32, P, i32, P, P, P, P, i32, P, P,
+                                                  u32, u64, P]
+            lib.orc_ksat_cluster_flip.restype = C.c_int
             lib.orc_qap_cost.argtypes = [i32, P, P, P]
             lib.orc_qap_cost.restype = i64
             lib.orc_qap_swap_delta.argtypes = [i32, P, P, P, i32, i32]
@@ -89,6 +92,7 @@ TAG_KSAT_SWEEP = 0x4B535750
 TAG_QAP_INIT = 0x51494E49
 TAG_QAP_STEP = 0x51535450
 TAG_PT_SWAP = 0x50545357
+TAG_CLUSTER = 0x434C5354
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:
@@ -213,6 +217,28 @@ def ksat_pt_anneal(lits, n_vars, beta, ladder, t0, t1, sweeps_per_round, seed, r
     if rc != 0:
         raise ValueError("orc_ksat_pt_anneal rejected its arguments")
     return dict(states=out_s, energies=e, best_energies=be, best_states=out_b, slots=slots)
+
+
+def ksat_cluster_flip(lits, n_vars, chain, mask, beta, move_id, seed):
+    """Collective move of every replica of `chain` (a dict as ksat_anneal returns: states,
+    energies, best_states, best_energies): replica r proposes x xor mask_r (mask [1 or R, N] 0/1)
+    and accepts by the Metropolis rule at beta[r]. Returns a new dict of the same form plus
+    `accepted` uint8[R]."""
+    lits, m, k = _cnf(lits)
+    st = np.array(chain["states"], dtype=np.uint8, order="C")
+    bs = np.array(chain["best_states"], dtype=np.uint8, order="C")
+    e = np.array(chain["energies"], dtype=np.int64)
+    be = np.array(chain["best_energies"], dtype=np.int64)
+    R = st.shape[0]
+    mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1, n_vars)
+    beta = np.ascontiguousarray(np.broadcast_to(np.asarray(beta, dtype=np.float32), (R,)))
+    acc = np.zeros(R, dtype=np.uint8)
+    rc = _load().orc_ksat_cluster_flip(n_vars, m, k, _p(lits), R, _p(st), _p(e), _p(bs), _p(be),
+                                       mask.shape[0], _p(mask), _p(beta), int(move_id) & 0xFFFFFFFF,
+                                       int(seed) & (2**64 - 1), _p(acc))
+    if rc != 0:
+        raise ValueError("orc_ksat_cluster_flip rejected its arguments")
+    return dict(states=st, energies=e, best_energies=be, best_states=bs, accepted=acc)
 
 
 def adaptive_ladder(lits, n_vars, replicas, seed, beta0, alpha, sigma_min, max_temps,

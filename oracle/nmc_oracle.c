@@ -35,6 +35,14 @@
  *    and b (at k+1): d = (lq[k] - lq[k+1]) (E_a - E_b) accepts when d >= 0, else iff
  *    ((-d) >> 8) < L and u < Tab[(-d) >> 8] for u = word 0 of the Philox block for counter
  *    (k, q, g, TAG_PT_SWAP).
+ *  Frozen units (the two chains of Algorithm 1 sample one subset with the other held fixed,
+ *    Fig. 2 caption): beta_v[t] = +infinity holds unit v fixed at step t. A frozen k-SAT variable
+ *    is not attempted; a QAP swap that involves a frozen facility is rejected (its Philox block is
+ *    still drawn, so nothing else shifts).
+ *  Collective move (the nonlocal backbone flip of Fig. 1(c)): replica r proposes x' = x xor m_r
+ *    and accepts when dE = E(x') - E(x) <= 0, else iff ((bq dE) >> 8) < L and u < Tab[...] with
+ *    bq = Q16(beta_r) and u = word r&3 of the Philox block for counter
+ *    (move_id, 0, r>>2, TAG_CLUSTER); the best-so-far follows on strictly lower E.
  *  Energy statistics (the adaptive ladder of the same appendix measures the energy variance at
  *    each temperature): sums of E and E^2 of every replica over the end-of-sweep energies of
  *    the sweeps t >= stats_t0.
@@ -55,6 +63,8 @@
 #define ORC_TAG_QAP_INIT 0x51494E49u   /* "QINI" */
 #define ORC_TAG_QAP_STEP 0x51535450u   /* "QSTP" */
 #define ORC_TAG_PT_SWAP 0x50545357u    /* "PTSW" */
+#define ORC_TAG_CLUSTER 0x434C5354u    /* "CLST" */
+#define ORC_FROZEN 0xFFFFFFFFu         /* Q16 value of beta = +infinity: the unit is held */
 #define ORC_TAB_CAP 8192
 
 /* ---------------------------------------------------------------------------------------
@@ -120,9 +130,10 @@ int orc_threshold_table(uint32_t *tab, int cap) {
   return -1;
 }
 
-/* beta in Q16: nearest integer to beta * 65536, ties to even. beta must be finite, >= 0 and
- * <= 65535 (the library rejects anything else). */
+/* beta in Q16: nearest integer to beta * 65536, ties to even. beta must be +infinity (frozen:
+ * ORC_FROZEN), or finite, >= 0 and <= 65535 (the library rejects anything else). */
 uint32_t orc_quantize_beta(float beta) {
+  if (isinf(beta) && beta > 0) return ORC_FROZEN;
   double v = (double)beta * 65536.0;
   return (uint32_t)nearbyint(v);
 }
@@ -331,13 +342,15 @@ static void ksat_one_replica(const ksat_job *J, int32_t j) {
   for (int32_t t = J->t0; t < J->t1; ++t) {
     for (int32_t p = 0; p < n; ++p) {
       int v = J->order[p];
+      const uint32_t bqv = J->bq[(size_t)v * J->n_steps + t];
+      if (bqv == ORC_FROZEN) continue;
       int64_t d = cnf_delta(f, x, v);
       int acc;
       if (d <= 0) {
         acc = 1;
       } else {
         uint32_t u = philox_word((uint32_t)v, (uint32_t)t, r >> 2, ORC_TAG_KSAT_SWEEP, J->seed, r & 3);
-        acc = accept_uphill(J->tab, J->bq[(size_t)v * J->n_steps + t], d, u);
+        acc = accept_uphill(J->tab, bqv, d, u);
       }
       if (acc) {
         x[v] ^= 1u;
@@ -509,6 +522,7 @@ int orc_ksat_pt_anneal(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, 
       const uint64_t mult = lq[slots[r]];
       for (int32_t q = 0; q < n; ++q) {
         const int v = order[q];
+        if (bq[(size_t)v * n_steps + t] == ORC_FROZEN) continue;
         const int64_t d = cnf_delta(&f, xr, v);
         int acc;
         if (d <= 0) {
@@ -650,6 +664,9 @@ static void qap_one_replica(const qap_job *J, int32_t j) {
         int32_t fr = (int32_t)(((uint64_t)u[0] * (uint64_t)n) >> 32);
         int32_t fs = (int32_t)(((uint64_t)u[1] * (uint64_t)(n - 1)) >> 32);
         if (fs >= fr) fs += 1;
+        if (J->bq[(size_t)fr * J->n_steps + t] == ORC_FROZEN ||
+            J->bq[(size_t)fs * J->n_steps + t] == ORC_FROZEN)
+          continue;
         int64_t d = orc_qap_swap_delta(n, J->F, J->D, p, fr, fs);
         int acc;
         if (d <= 0) {
@@ -733,5 +750,49 @@ int orc_qap_anneal(int32_t n, const int32_t *F, const int32_t *D, int32_t n_step
   free(th);
   free(ids);
   free(bq);
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Collective (cluster) move on R k-SAT replicas.
+ * ------------------------------------------------------------------------------------- */
+/*
+ * states: R*n uint8 in/out; energies, best_energies: R int64 in/out; best_states: R*n in/out.
+ * mask: mask_rows*n uint8 (mask_rows 1: one mask for all replicas, or R). beta: R floats.
+ * accepted: R uint8 out (nullable). Returns 0 or -1 on a bad argument.
+ */
+int orc_ksat_cluster_flip(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, int32_t R,
+                          uint8_t *states, int64_t *energies, uint8_t *best_states,
+                          int64_t *best_energies, int32_t mask_rows, const uint8_t *mask,
+                          const float *beta, uint32_t move_id, uint64_t seed, uint8_t *accepted) {
+  if (n <= 0 || m < 0 || kmax <= 0 || R <= 0 || (mask_rows != 1 && mask_rows != R)) return -1;
+  orc_table tab;
+  table_init(&tab);
+  uint8_t *y = (uint8_t *)malloc((size_t)n);
+  for (int32_t r = 0; r < R; ++r) {
+    uint8_t *x = states + (size_t)r * n;
+    const uint8_t *mr = mask + (size_t)(mask_rows == 1 ? 0 : r) * n;
+    for (int32_t v = 0; v < n; ++v) y[v] = (uint8_t)(x[v] ^ (mr[v] & 1u));
+    const int64_t e0 = orc_ksat_energy(n, m, kmax, lits, x);
+    const int64_t e1 = orc_ksat_energy(n, m, kmax, lits, y);
+    const int64_t d = e1 - e0;
+    int acc = 1;
+    if (d > 0) {
+      const uint32_t u = philox_word(move_id, 0u, (uint32_t)r >> 2, ORC_TAG_CLUSTER, seed, r & 3);
+      acc = accept_uphill(&tab, orc_quantize_beta(beta[r]), d, u);
+    }
+    if (acc) {
+      memcpy(x, y, (size_t)n);
+      energies[r] = e1;
+      if (e1 < best_energies[r]) {
+        best_energies[r] = e1;
+        memcpy(best_states + (size_t)r * n, x, (size_t)n);
+      }
+    } else {
+      energies[r] = e0;
+    }
+    if (accepted) accepted[r] = (uint8_t)acc;
+  }
+  free(y);
   return 0;
 }

@@ -59,7 +59,7 @@ SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_
            "nmc_server_result", "nmc_server_cancel", "nmc_server_stats",
            "nmc_server_last_error", "nmc_batch_run_noalloc", "nmc_qap_batch_run",
            "nmc_replicas_set_ladder", "nmc_replicas_run_pt", "nmc_replicas_read_slots",
-           "nmc_adaptive_ladder"]
+           "nmc_adaptive_ladder", "nmc_replicas_cluster_flip"]
 
 
 def library_path() -> str:
@@ -118,6 +118,7 @@ def load(build_if_missing: bool = True):
             "nmc_replicas_read_slots": ([P, i32, P], C.c_int),
             "nmc_adaptive_ladder": ([P, i32, i32, u64, C.c_double, C.c_double, C.c_double, i32,
                                      i32, i32, P, P, P], C.c_int),
+            "nmc_replicas_cluster_flip": ([P, i32, i32, P, P, C.c_uint32, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -336,6 +337,20 @@ class Context:
         _, R = self._rs[rs]
         out = np.zeros(R, dtype=np.int32)
         self._check(self._lib.nmc_replicas_read_slots(self._h, int(rs), _ptr(out)))
+        return out
+
+    def cluster_flip(self, rs: int, mask, beta, move_id: int, accepted: bool = False):
+        """Collective move: replica r proposes flipping the variables of mask[r] (mask [1 or R,
+        n_vars] 0/1) and accepts at beta[r] (scalar or R floats). With accepted=True, returns
+        the uint8[R] acceptance flags (synchronises)."""
+        inst, R = self._rs[rs]
+        n = self._units[inst]
+        mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1, n)
+        beta = np.ascontiguousarray(np.broadcast_to(np.asarray(beta, dtype=np.float32), (R,)))
+        out = np.zeros(R, dtype=np.uint8) if accepted else None
+        self._check(self._lib.nmc_replicas_cluster_flip(self._h, int(rs), mask.shape[0], _ptr(mask),
+                                                        _ptr(beta), int(move_id) & 0xFFFFFFFF,
+                                                        _ptr(out)))
         return out
 
     def adaptive_ladder(self, inst: int, replicas: int, seed: int, beta0: float, alpha: float,

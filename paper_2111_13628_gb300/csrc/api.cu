@@ -860,7 +860,7 @@ static int set_schedule_impl(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const 
   }
   if (bad) {
     cudaFree(bq);
-    return fail(ctx, NMC_EINVAL, "beta must be finite and in [0, 65535]");
+    return fail(ctx, NMC_EINVAL, "beta must be in [0, 65535] or +infinity (held)");
   }
   dev_free(I->bq);
   I->bq = bq;
@@ -900,7 +900,7 @@ int nmc_set_schedule_factored(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const
   }
   if (bad) {
     cudaFree(bq);
-    return fail(ctx, NMC_EINVAL, "beta must be finite and in [0, 65535]");
+    return fail(ctx, NMC_EINVAL, "beta must be in [0, 65535] or +infinity (held)");
   }
   dev_free(I->bq);
   I->bq = bq;
@@ -1325,6 +1325,47 @@ int nmc_replicas_read_slots(nmc_ctx *ctx, int32_t rs, int32_t *slots_out) {
                            ctx->stream),
            "read slots");
   NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  return NMC_OK;
+}
+
+int nmc_replicas_cluster_flip(nmc_ctx *ctx, int32_t rs, int32_t mask_rows, const uint8_t *mask,
+                              const float *beta, uint32_t move_id, uint8_t *accepted_out) {
+  if (!ctx) return NMC_EINVAL;
+  ReplicaSet *S = find_set(ctx, rs);
+  if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
+  Instance *I = find_inst(ctx, S->inst);
+  if (!I) return fail(ctx, NMC_ESTATE, "instance was unloaded");
+  if (I->kind != NMC_KIND_KSAT) return fail(ctx, NMC_EINVAL, "collective moves need a k-SAT set");
+  if (!mask || !beta || (mask_rows != 1 && mask_rows != S->R))
+    return fail(ctx, NMC_EINVAL, "need a mask of 1 or R rows and R temperatures");
+  const int32_t n = I->ks.n, R = S->R, W = S->ks.W;
+  const size_t mask_bytes = static_cast<size_t>(mask_rows) * n;
+  for (size_t i = 0; i < mask_bytes; ++i)
+    if (mask[i] > 1) return fail(ctx, NMC_EINVAL, "mask entries must be 0 or 1");
+  for (int32_t r = 0; r < R; ++r)
+    if (!(beta[r] >= 0.0f && beta[r] <= 65535.0f))
+      return fail(ctx, NMC_EINVAL, "beta must be finite and in [0, 65535]");
+  DeviceGuard dg(ctx->device);
+  // staging: mask bytes, beta, accepted flags, then the kernels' scratch (256-byte sections)
+  auto up = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+  const size_t off_beta = up(mask_bytes), off_acc = off_beta + up(sizeof(float) * R);
+  const size_t off_scr = off_acc + up(static_cast<size_t>(R));
+  const size_t total = off_scr + cluster_scratch_bytes(n, W);
+  char *dev = nullptr;
+  NMC_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&dev), total, ctx->stream), "allocate move scratch");
+  cudaError_t e = cudaMemcpyAsync(dev, mask, mask_bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dev + off_beta, beta, sizeof(float) * R, cudaMemcpyHostToDevice, ctx->stream);
+  uint8_t *acc_dev = accepted_out ? reinterpret_cast<uint8_t *>(dev + off_acc) : nullptr;
+  if (e == cudaSuccess)
+    e = ksat_cluster_flip(I->ks, S->ks, reinterpret_cast<const uint8_t *>(dev), mask_rows,
+                          reinterpret_cast<const float *>(dev + off_beta), move_id, S->seed,
+                          ctx->tab, ctx->tab_len, dev + off_scr, acc_dev, ctx->stream);
+  if (e == cudaSuccess && accepted_out)
+    e = cudaMemcpyAsync(accepted_out, acc_dev, static_cast<size_t>(R), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(dev, ctx->stream);
+  if (e == cudaSuccess && accepted_out) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "collective move");
   return NMC_OK;
 }
 

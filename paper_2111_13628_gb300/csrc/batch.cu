@@ -18,6 +18,7 @@
 
 #include "nmc.h"
 #include "nmc_internal.h"
+#include "bits.cuh"
 #include "philox.cuh"
 
 namespace cg = cooperative_groups;
@@ -27,10 +28,6 @@ namespace nmc {
 namespace {
 
 constexpr int kBatchThreads = 640;
-
-__device__ __forceinline__ uint32_t maj3b(uint32_t a, uint32_t b, uint32_t c) {
-  return (a & b) | (a & c) | (b & c);
-}
 
 template <int NB>
 __device__ __forceinline__ void csa4(uint32_t (&c)[NB], uint32_t a0, uint32_t a1, uint32_t a2,
@@ -49,27 +46,6 @@ __device__ __forceinline__ void csa4(uint32_t (&c)[NB], uint32_t a0, uint32_t a1
     c[j] ^= carry;
     carry = t;
   }
-}
-
-// Transposes the 8x8 bit matrix held as 8 bytes (byte j = row j) so that byte i holds
-// column i: with row j = bit plane j of 8 replicas, byte i becomes replica i's value.
-__device__ __forceinline__ unsigned long long transpose8(unsigned long long x) {
-  unsigned long long t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
-  x = x ^ t ^ (t << 7);
-  t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
-  x = x ^ t ^ (t << 14);
-  t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
-  x = x ^ t ^ (t << 28);
-  return x;
-}
-
-// Gathers byte q of each of the 8 planes p[0..7] into one 64-bit word (byte j from plane j).
-__device__ __forceinline__ unsigned long long gather_bytes(const uint32_t *p, int q) {
-  const uint32_t sel = (uint32_t)q | ((uint32_t)(4 + q) << 4);
-  const uint32_t t01 = __byte_perm(p[0], p[1], sel), t23 = __byte_perm(p[2], p[3], sel);
-  const uint32_t t45 = __byte_perm(p[4], p[5], sel), t67 = __byte_perm(p[6], p[7], sel);
-  return (unsigned long long)__byte_perm(t01, t23, 0x5410) |
-         ((unsigned long long)__byte_perm(t45, t67, 0x5410) << 32);
 }
 
 constexpr int kAccPlanes = 16;  // per-thread energy accumulator: 16-bit two's complement
@@ -105,6 +81,7 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
   constexpr int NB = 7;
   const uint32_t x = xs[v];
   const uint32_t bqv = __ldg(B.bq + (size_t)t * B.n + v);
+  if (bqv == kFrozenQ16) return x;  // held at this step: no attempt
   uint32_t bc[NB], mc[NB];
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
@@ -394,6 +371,8 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
   constexpr int NB = 7;
   const uint32_t x = active ? xs[v] : 0u;
   const uint32_t bqv = active ? __ldg(B.bq + (size_t)t * B.n + v) : 0u;
+  // a held variable takes no attempt; the team still joins the shuffles below
+  const bool frozen = bqv == kFrozenQ16;
   uint32_t bc[NB], mc[NB];
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
@@ -402,7 +381,7 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
   }
   int len = 0;
   const int4 *ent = nullptr;
-  if (active) {
+  if (active && !frozen) {
     const int off = v - c0;
     const int g = __ldg(B.cgrp + c) + (off >> 5), ln = off & 31;
     const int gb = __ldg(B.grp_base + g);
@@ -502,6 +481,7 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
       }
     }
   }
+  if (frozen) flip = 0u;  // zero counters read as dE = 0: cancel those flips
 #pragma unroll
   for (int sft = 1; sft < TL; sft <<= 1) flip |= __shfl_xor_sync(0xFFFFFFFFu, flip, sft);
   return x ^ flip;

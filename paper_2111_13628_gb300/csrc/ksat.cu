@@ -155,13 +155,14 @@ __device__ __forceinline__ void attempt(const SweepArgs &a, const uint32_t *__re
   const uint32_t *Sw = a.S + w;
   const uint32_t x = __ldcg(Sw + (size_t)(2 * v) * W);
   const uint32_t bqv = __ldg(a.bq + (size_t)t * a.n + v);
+  const bool frozen = bqv == kFrozenQ16;  // held: no attempt (the pending best copy still runs)
   uint32_t bc[NB], mc[NB];
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
     bc[j] = 0u;
     mc[j] = 0u;
   }
-  const int e0 = __ldg(a.occ_ptr + v), e1 = __ldg(a.occ_ptr + v + 1);
+  const int e0 = __ldg(a.occ_ptr + v), e1 = frozen ? e0 : __ldg(a.occ_ptr + v + 1);
   for (int e = e0; e < e1; e += 4) {
     uint32_t bb[4], mm[4];
 #pragma unroll
@@ -212,6 +213,7 @@ __device__ __forceinline__ void attempt(const SweepArgs &a, const uint32_t *__re
       }
     }
   }
+  if (frozen) flip = 0u;  // zero counters read as dE = 0: cancel those flips
   const uint32_t xn = x ^ flip;
   __stcg(a.S + (size_t)(2 * v) * W + w, xn);
   __stcg(a.S + (size_t)(2 * v + 1) * W + w, ~xn);
@@ -338,8 +340,9 @@ __device__ __forceinline__ void fast_attempt(const SweepArgs &a, const FastSmem 
   const int e0 = __ldg(a.occ_ptr + v), e1 = __ldg(a.occ_ptr + v + 1);
   const uint32_t x = __ldcg(Sw + (size_t)(2 * v) * W);
   const uint32_t bqv = __ldg(a.bq + (size_t)t * a.n + v);
-  // this warp's share of the occurrences, a multiple of 4
-  const int quads = (e1 - e0) >> 2;
+  const bool frozen = bqv == kFrozenQ16;  // uniform over the team (one variable)
+  // this warp's share of the occurrences, a multiple of 4 (none when the variable is held)
+  const int quads = frozen ? 0 : (e1 - e0) >> 2;
   const int per = (quads + P - 1) / P;
   const int lo = e0 + 4 * min(quads, p * per);
   const int hi = e0 + 4 * min(quads, (p + 1) * per);
@@ -470,6 +473,7 @@ __device__ __forceinline__ void fast_attempt(const SweepArgs &a, const FastSmem 
       }
     }
   }
+  if (frozen) flip = 0u;  // zero counters read as dE = 0: cancel those flips
   if (P > 1) {
     uint32_t *fl = sm.flip + (size_t)team_in_cta * P * 32;
     fl[p * 32 + lane] = flip;
@@ -685,7 +689,9 @@ __global__ void quantize_kernel(const float *beta, int32_t n_units, int32_t n_st
     if (v < n_units && t < n_steps) {
       const int u = orig ? orig[v] : v;
       const float b = beta[(size_t)u * n_steps + t];
-      if (!(b >= 0.0f && b <= 65535.0f)) {  // also rejects NaN
+      if (isinf(b) && b > 0.0f) {
+        q = kFrozenQ16;
+      } else if (!(b >= 0.0f && b <= 65535.0f)) {  // also rejects NaN
         atomicExch(bad, 1);
       } else {
         q = __float2uint_rn(b * 65536.0f);  // exact product, ties to even
@@ -712,7 +718,9 @@ __global__ void quantize_factored_kernel(const float *base, const float *factor,
     const int u = orig ? orig[v] : v;
     const float b = __fmul_rn(base[t], factor[u]);
     uint32_t q = 0u;
-    if (!(b >= 0.0f && b <= 65535.0f)) {
+    if (isinf(b) && b > 0.0f) {
+      q = kFrozenQ16;
+    } else if (!(b >= 0.0f && b <= 65535.0f)) {
       atomicExch(bad, 1);
     } else {
       q = __float2uint_rn(b * 65536.0f);

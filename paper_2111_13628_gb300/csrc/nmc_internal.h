@@ -17,6 +17,10 @@ constexpr uint32_t kTagKsatSweep = 0x4B535750u;
 constexpr uint32_t kTagQapInit = 0x51494E49u;
 constexpr uint32_t kTagQapStep = 0x51535450u;
 constexpr uint32_t kTagPtSwap = 0x50545357u;
+constexpr uint32_t kTagCluster = 0x434C5354u;
+// Q16 schedule entry of beta = +infinity: the unit is held fixed at that step (a frozen
+// variable is not attempted; a QAP swap involving a frozen facility is rejected).
+constexpr uint32_t kFrozenQ16 = 0xFFFFFFFFu;
 
 constexpr int kTabCap = 8192;    // capacity of the acceptance-threshold table
 constexpr int kMaxReplicas = 4096;
@@ -179,6 +183,17 @@ cudaError_t fill_schedule(uint32_t *bq, size_t count, double beta, int32_t *bad,
 // (IEEE double, no contraction); out[0] = sigma, out[1] = beta + alpha / sigma.
 cudaError_t ladder_step(const long long *stats, int32_t R, int32_t W, long long samples,
                         double beta, double alpha, double *out, cudaStream_t st);
+
+// ---- collective move (cluster.cu) --------------------------------------------------------
+// Device scratch one ksat_cluster_flip needs for an instance of n variables and W words.
+size_t cluster_scratch_bytes(int32_t n, int32_t W);
+// Replica r proposes flipping the variables of its mask (mask_dev: uint8 [rows][n], original
+// order, rows 1 or R) and accepts by the Metropolis rule at beta_dev[r] (validated, R floats);
+// energies, best energies, states and best states follow. acc_dev (nullable): R bytes out.
+cudaError_t ksat_cluster_flip(const KsatDevice &I, KsatReplicas &Rp, const uint8_t *mask_dev,
+                              int32_t rows, const float *beta_dev, uint32_t move_id,
+                              uint64_t seed, const uint32_t *tab, int32_t tab_len, void *scratch,
+                              uint8_t *acc_dev, cudaStream_t st);
 
 // ---- QAP launchers (qap.cu) ------------------------------------------------------------
 // Arguments of one QAP launch (or, in a batched launch, of one CTA: one block of 32 replicas).

@@ -125,7 +125,7 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
       for (int a0 = 0; a0 < n; a0 += 32) {
         // lane j draws attempt a0+j
         const int at = a0 + lane;
-        int fr = 0, fs = 0;
+        int fr = 0, fs = 0, frz = 0;
         uint32_t u2 = 0u, bqs = 0u;
         if (at < n) {
           const uint4 u =
@@ -134,10 +134,13 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
           fs = (int)(((unsigned long long)u.y * (unsigned)nm1) >> 32);
           fs += fs >= fr;
           u2 = u.z;
-          bqs = (uint32_t)(((unsigned long long)__ldg(bqt + fr) + __ldg(bqt + fs)) >> 1);
+          const uint32_t br = __ldg(bqt + fr), bs = __ldg(bqt + fs);
+          frz = (br == kFrozenQ16 || bs == kFrozenQ16) ? 1 : 0;  // a held facility: reject
+          bqs = (uint32_t)(((unsigned long long)br + bs) >> 1);
         }
         const int cnt = (n - a0) < 32 ? (n - a0) : 32;
         for (int j = 0; j < cnt; ++j) {
+          if (__shfl_sync(0xFFFFFFFFu, frz, j)) continue;  // uniform over the warp
           const int rr = __shfl_sync(0xFFFFFFFFu, fr, j);
           const int ss = __shfl_sync(0xFFFFFFFFu, fs, j);
           const int pr = __shfl_sync(0xFFFFFFFFu, pick<NPL>(p, rr >> 5), rr & 31);

@@ -159,7 +159,7 @@ def test_rejects_bad_input(ctx):
         assert e.value.code == nmc.NMC_EINVAL
     lits = W.random_ksat(20, 4.2, 3, 1)
     inst = ctx.load_ksat(lits, 20)
-    for v in (np.nan, -1.0, 70000.0, np.inf):
+    for v in (np.nan, -1.0, 70000.0, -np.inf):  # +inf is valid: the variable is held
         beta = W.beta_constant(20, 4, 1.0)
         beta[3, 2] = v
         with pytest.raises(nmc.NmcError) as e:

@@ -569,3 +569,146 @@ def test_adaptive_ladder_measures_the_equilibrium_fluctuation():
         w /= w.sum()
         exact = math.sqrt(float((w * E * E).sum() - (w * E).sum() ** 2))
         assert abs(sg - exact) <= 0.06 * exact + 0.01, (b, sg, exact)
+
+
+# ---------------------------------------------------------------- frozen units, cluster moves
+def _state_index(X):
+    X = np.asarray(X, dtype=np.int64)
+    return (X << np.arange(X.shape[1])).sum(axis=1)
+
+
+def test_frozen_variables_hold_and_the_rest_is_conditionally_boltzmann():
+    """beta = +inf holds a variable; the others then sample the Boltzmann law conditioned on the
+    held values (each chain of the two-chain scheme is detailed-balanced on its own subset)."""
+    n = 7
+    lits = small_cnf(n, 26, 3, seed=12)
+    frozen = {1: 1, 4: 0}
+    R, T, b = 3000, 30, 0.9
+    rng = np.random.default_rng(4)
+    init = rng.integers(0, 2, size=(R, n), dtype=np.uint8)
+    for v, val in frozen.items():
+        init[:, v] = val
+    beta = W.beta_constant(n, T, b)
+    for v in frozen:
+        beta[v, :] = np.inf
+    res = O.ksat_anneal(lits, n, beta, 0, T, 7, replicas=R, init=init)
+    for v, val in frozen.items():
+        assert np.all(res["states"][:, v] == val)
+    X = all_states(n)
+    keep = np.all([X[:, v] == val for v, val in frozen.items()], axis=0)
+    E = energies_numpy(lits, X[keep]).astype(np.float64)
+    pos = {int(i): j for j, i in enumerate(_state_index(X[keep]))}
+    counts = np.zeros(len(E))
+    for i in _state_index(res["states"]):
+        counts[pos[int(i)]] += 1
+    w = np.exp(-np.float64(np.float32(b)) * E)
+    assert _chi2_pvalue(counts, w / w.sum()) > 1e-4
+    assert np.array_equal(res["energies"], energies_numpy(lits, res["states"]))
+
+
+def test_fully_frozen_schedule_changes_nothing():
+    wl = W.workload_ksat_small(12)
+    beta = np.full_like(wl["beta"], np.inf)
+    a = O.ksat_anneal(wl["lits"], wl["n_vars"], beta, 0, 12, 3, replicas=9)
+    b = O.ksat_anneal(wl["lits"], wl["n_vars"], beta, 0, 0, 3, replicas=9)
+    for key in ("states", "energies", "best_energies", "best_states"):
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_frozen_qap_facility_holds_and_the_rest_is_conditionally_boltzmann():
+    n = 5
+    F, D = W.random_qap(n, 77, max_entry=9)
+    R, T, b = 3000, 40, 0.08
+    beta = W.beta_constant(n, T, b)
+    beta[2, :] = np.inf
+    rng = np.random.default_rng(3)
+    init = np.zeros((R, n), dtype=np.int16)
+    for r in range(R):
+        rest = rng.permutation([0, 1, 3, 4])
+        init[r] = [rest[0], rest[1], 2, rest[2], rest[3]]
+    res = O.qap_anneal(F, D, beta, 0, T, 5, replicas=R, init=init)
+    assert np.all(res["perms"][:, 2] == 2)
+    perms = [p for p in itertools.permutations(range(n)) if p[2] == 2]
+    pos = {p: j for j, p in enumerate(perms)}
+    E = np.array([_qap_cost_numpy(F, D, np.array(p)) for p in perms], dtype=np.float64)
+    counts = np.zeros(len(perms))
+    for p in res["perms"]:
+        counts[pos[tuple(int(x) for x in p)]] += 1
+    w = np.exp(-np.float64(np.float32(b)) * (E - E.min()))
+    assert _chi2_pvalue(counts, w / w.sum()) > 1e-4
+
+
+def _chain_of(lits, n, states):
+    e = energies_numpy(lits, states)
+    return dict(states=states.copy(), energies=e, best_states=states.copy(), best_energies=e.copy())
+
+
+def test_cluster_flip_limits():
+    """beta 0 accepts every proposal; beta 65535 accepts exactly the non-increasing ones; the
+    best-so-far is the minimum of the energies seen."""
+    n = 40
+    lits = W.random_ksat(n, 4.2, 3, 31)
+    rng = np.random.default_rng(5)
+    X = rng.integers(0, 2, size=(64, n), dtype=np.uint8)
+    M = rng.integers(0, 2, size=(64, n), dtype=np.uint8)
+    ch = _chain_of(lits, n, X)
+    hot = O.ksat_cluster_flip(lits, n, ch, M, 0.0, 1, 9)
+    assert np.all(hot["accepted"] == 1)
+    assert np.array_equal(hot["states"], X ^ M)
+    assert np.array_equal(hot["energies"], energies_numpy(lits, X ^ M))
+    assert np.array_equal(hot["best_energies"], np.minimum(ch["energies"], hot["energies"]))
+    cold = O.ksat_cluster_flip(lits, n, ch, M, 65535.0, 1, 9)
+    down = energies_numpy(lits, X ^ M) <= ch["energies"]
+    assert np.array_equal(cold["accepted"].astype(bool), down)
+    want = np.where(down[:, None], X ^ M, X)
+    assert np.array_equal(cold["states"], want)
+    # one shared mask row acts on every replica
+    one = O.ksat_cluster_flip(lits, n, ch, M[:1], 0.0, 1, 9)
+    assert np.array_equal(one["states"], X ^ M[:1])
+
+
+def test_cluster_flip_accepts_with_the_boltzmann_factor():
+    """A proposal with energy change dE > 0 at beta = 0.5 (on the table's grid) is accepted with
+    frequency exp(-0.5 dE) over independent draws (replicas and move ids)."""
+    n = 30
+    lits = W.random_ksat(n, 4.2, 3, 8)
+    rng = np.random.default_rng(1)
+    while True:
+        x = rng.integers(0, 2, size=n, dtype=np.uint8)
+        m = rng.integers(0, 2, size=n, dtype=np.uint8)
+        dE = int(energies_numpy(lits, (x ^ m)[None])[0] - energies_numpy(lits, x[None])[0])
+        if 1 <= dE <= 4:
+            break
+    R = 4096
+    ch = _chain_of(lits, n, np.repeat(x[None], R, axis=0))
+    hits = 0
+    for mid in range(5):
+        hits += int(O.ksat_cluster_flip(lits, n, ch, m, 0.5, mid, 3)["accepted"].sum())
+    p = math.exp(-0.5 * dE)
+    tot = 5 * R
+    z = (hits - tot * p) / math.sqrt(tot * p * (1 - p))
+    assert abs(z) < 4.5, (dE, hits / tot, p)
+
+
+def test_cluster_moves_keep_the_boltzmann_law():
+    """Sweeps interleaved with collective flips of a fixed half of the variables (a symmetric
+    proposal) at one beta: the final states follow the Boltzmann law."""
+    n = 6
+    lits = small_cnf(n, 20, 3, seed=4)
+    R, rounds, b = 3000, 12, 0.8
+    beta = W.beta_constant(n, rounds, b)
+    mask = np.array([1, 0, 1, 1, 0, 0], dtype=np.uint8)
+    ch = None
+    for t in range(rounds):
+        if ch is None:
+            ch = O.ksat_anneal(lits, n, beta, 0, 1, 21, replicas=R)
+        else:
+            ch = O.ksat_anneal(lits, n, beta, t, t + 1, 21, replicas=R, init=ch["states"],
+                               init_best=ch["best_states"], init_best_energy=ch["best_energies"])
+        ch = O.ksat_cluster_flip(lits, n, ch, mask, b, t, 21)
+    E = energies_numpy(lits, all_states(n)).astype(np.float64)
+    counts = np.bincount(_state_index(ch["states"]), minlength=2 ** n)
+    w = np.exp(-np.float64(np.float32(b)) * E)
+    assert _chi2_pvalue(counts, w / w.sum()) > 1e-4
+    w_bad = np.exp(+np.float64(np.float32(b)) * E)
+    assert _chi2_pvalue(counts, w_bad / w_bad.sum()) < 1e-6
