@@ -239,6 +239,56 @@ int nmc_replicas_cluster_flip(nmc_ctx *ctx, int32_t rs, int32_t mask_rows, const
                               const float *beta, uint32_t move_id, uint8_t *accepted_out);
 
 /*
+ * Learning stage for k-SAT: loopy belief propagation on the surrogate Hamiltonian around S seed
+ * states (Sec. "4-SAT Problems Near Computational Phase Transitions"; App. "Loopy Belief
+ * propagation for k-local Hamiltonians over conjugate normal form"), double precision.
+ * Spins r = 2x - 1; sigma_ai = +1 for a positive literal of variable i in clause a, -1 for a
+ * negated one. Messages: h_{i->a} = sigma_ai (lambda eps_i s*_i + sum_{b != a} sigma_bi u_{b->i}),
+ * u_{a->i} = -1/2 ln[1 - (1 - e^{-2 beta}) prod_{j in a, j != i} (1 - tanh h_{j->a}) / 2]. They
+ * start from h = sigma lambda_0 eps s* and the u of those h; an iteration recomputes every h
+ * from the previous u, then every u; a lambda converges when max |u_new - u_old| < tol. lambda
+ * runs through `lambdas` without re-initialising; when one fails to converge in max_iter
+ * iterations, the messages of the previous converged lambda are restored and that seed stops.
+ * Outputs from the final messages (lambda = the last converged one, else lambda_0):
+ * <r_i> = tanh(lambda eps_i s*_i + sum_a sigma_ai u_{a->i}); clause correlations
+ * <prod_{i in a} r_i> under mu_a(r) ~ omega_a(r) prod_i (1 + sigma_ai r_i tanh h_{i->a}) / 2
+ * with omega_a = e^{-2 beta} on the violating configuration (the full sum over the clause's
+ * configurations); p = (1/N) sum s*_i <r_i>, q1 = (1/N) sum <r_i>^2.
+ * x_star: host uint8 [S][N] 0/1 (original variable order); eps: host double [N], NULL = the
+ * number of clauses of each variable; lambdas: host double [n_lambda]. Outputs (host):
+ * marg_out [S][N] (required); corr_out [S][M], iters_out [S][n_lambda] (iterations run at each
+ * lambda, 0 where not reached), deltas_out [S][n_lambda] (last max |du|), n_done_out [S]
+ * (lambdas that converged), overlap_out [S][2] (p, q1): each nullable. Synchronises.
+ */
+int nmc_cnf_lbp(nmc_ctx *ctx, int32_t inst, int32_t n_seeds, const uint8_t *x_star,
+                const double *eps, double beta, int32_t n_lambda, const double *lambdas,
+                double tol, int32_t max_iter, double *marg_out, double *corr_out,
+                int32_t *iters_out, double *deltas_out, int32_t *n_done_out,
+                double *overlap_out);
+/*
+ * Backbones (Sec. "Generating backbones of rigid variables") from clause correlations corr
+ * (host double [S][M], each in [-1, 1]): effective factor couplings J~_a = atanh|corr_a| / beta;
+ * factors with J~ > seed_thr are nuclei; clusters grow through every factor with J~ > cutoff
+ * (or > seed_thr) touching them. labels_out (host int32 [S][N], original order): the cluster's
+ * smallest variable id, -1 outside every cluster; n_clusters_out (host [S], nullable).
+ * beta > 0. Synchronises.
+ */
+int nmc_cnf_backbone(nmc_ctx *ctx, int32_t inst, int32_t n_seeds, const double *corr,
+                     double beta, double seed_thr, double cutoff, int32_t *labels_out,
+                     int32_t *n_clusters_out);
+/*
+ * The sampling stage's schedule of Algorithm 1 built on the device from backbone labels (host
+ * int32 [N], original order, -1 = not in a backbone): cycles x (t_hot sweeps with the backbone
+ * at beta = base / heat (float) and every other variable held (+inf), t_cold sweeps with the
+ * backbone held and the rest at base, t_unlearn homogeneous sweeps at base). Replaces the
+ * instance's schedule (n_steps = cycles (t_hot + t_cold + t_unlearn)). base and base / heat in
+ * [0, 65535], heat > 0.
+ */
+int nmc_set_schedule_backbone(nmc_ctx *ctx, int32_t inst, const int32_t *labels, int32_t cycles,
+                              int32_t t_hot, int32_t t_cold, int32_t t_unlearn, float base,
+                              float heat);
+
+/*
  * Adaptive ladder (App. "Adaptive Parallel Tempering"): beta_0 = beta0; for level i the k-SAT
  * instance's `replicas` chains (a temporary set seeded by `seed`, Philox initial states, each
  * level continuing from the previous level's states) run sweeps_eq + sweeps_meas sweeps

@@ -23,16 +23,18 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nmc_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "lbp_oracle.c")]
 _LIB = os.path.join(_HERE, "libnmc_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compiles nmc_oracle.c with gcc (plain -O2, no fast-math) into libnmc_oracle.so."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compiles the oracle's C files with gcc (plain -O2, no fast-math) into libnmc_oracle.so."""
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC,
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, *_SRCS,
                                "-lm", "-lpthread"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -68,6 +70,12 @@ def _load():
             lib.orc_ksat_cluster_flip.argtypes = [i32, i32, i32, P, i32, P, P, P, P, i32, P, P,
                                                   u32, u64, P]
             lib.orc_ksat_cluster_flip.restype = C.c_int
+            dbl = C.c_double
+            lib.orc_cnf_lbp.argtypes = [i32, i32, i32, P, P, P, dbl, i32, P, dbl, i32, P, P, P, P,
+                                        P, P, P]
+            lib.orc_cnf_lbp.restype = C.c_int
+            lib.orc_cnf_backbone.argtypes = [i32, i32, i32, P, P, dbl, dbl, dbl, P]
+            lib.orc_cnf_backbone.restype = i32
             lib.orc_qap_cost.argtypes = [i32, P, P, P]
             lib.orc_qap_cost.restype = i64
             lib.orc_qap_swap_delta.argtypes = [i32, P, P, P, i32, i32]
@@ -273,6 +281,64 @@ def adaptive_ladder(lits, n_vars, replicas, seed, beta0, alpha, sigma_min, max_t
             break
         beta = beta + alpha / sigma
     return np.array(betas, dtype=np.float64), np.array(sigmas, dtype=np.float64)
+
+
+def clause_degrees(lits, n_vars):
+    """eps_i of the surrogate Hamiltonian for a CNF formula: the number of clauses containing
+    variable i (the largest energy change a flip of i can cause)."""
+    lits = np.asarray(lits)
+    v = np.abs(lits[lits != 0]) - 1
+    return np.bincount(v, minlength=n_vars).astype(np.float64)
+
+
+def cnf_lbp(lits, n_vars, x_star, beta, lambdas, tol, max_iter, eps=None):
+    """Loopy BP on the surrogate Hamiltonian of a CNF formula around the seed x_star (0/1),
+    with lambda continuation over `lambdas`. Returns dict(marg float64[N], corr float64[M],
+    iters int32[L], deltas float64[L], n_done, p, q1, lam)."""
+    lits, m, k = _cnf(lits)
+    x = np.ascontiguousarray(x_star, dtype=np.uint8)
+    eps = clause_degrees(lits, n_vars) if eps is None else np.ascontiguousarray(eps, np.float64)
+    lam = np.ascontiguousarray(np.atleast_1d(lambdas), dtype=np.float64)
+    marg = np.zeros(n_vars)
+    corr = np.zeros(m)
+    iters = np.zeros(lam.size, dtype=np.int32)
+    deltas = np.zeros(lam.size)
+    nd = C.c_int32()
+    ov = np.zeros(2)
+    lo = C.c_double()
+    rc = _load().orc_cnf_lbp(n_vars, m, k, _p(lits), _p(x), _p(eps), float(beta), lam.size,
+                             _p(lam), float(tol), int(max_iter), _p(marg), _p(corr), _p(iters),
+                             _p(deltas), C.byref(nd), _p(ov), C.byref(lo))
+    if rc != 0:
+        raise ValueError("orc_cnf_lbp rejected its arguments")
+    return dict(marg=marg, corr=corr, iters=iters, deltas=deltas, n_done=nd.value, p=ov[0],
+                q1=ov[1], lam=lo.value)
+
+
+def cnf_backbone(lits, n_vars, corr, beta, seed_thr, cutoff):
+    """Backbone labels (int32[N], -1 outside every cluster) and the number of clusters."""
+    lits, m, k = _cnf(lits)
+    corr = np.ascontiguousarray(corr, dtype=np.float64)
+    lab = np.zeros(n_vars, dtype=np.int32)
+    nc = _load().orc_cnf_backbone(n_vars, m, k, _p(lits), _p(corr), float(beta), float(seed_thr),
+                                  float(cutoff), _p(lab))
+    return lab, int(nc)
+
+
+def backbone_schedule(labels, base, heat, cycles, t_hot, t_cold, t_unlearn):
+    """The sampling stage's schedule (Algorithm 1) as beta[N][T] float32: every cycle runs
+    t_hot sweeps with the backbone at base/heat and the rest held (+inf), t_cold sweeps with the
+    backbone held and the rest at base, then t_unlearn homogeneous sweeps at base."""
+    labels = np.asarray(labels)
+    bb = labels >= 0
+    hot = np.float32(base) / np.float32(heat)
+    cyc = []
+    for _ in range(int(cycles)):
+        a = np.where(bb[:, None], hot, np.float32(np.inf)) * np.ones((1, t_hot), np.float32)
+        b = np.where(bb[:, None], np.float32(np.inf), np.float32(base)) * np.ones((1, t_cold), np.float32)
+        c = np.full((labels.size, t_unlearn), np.float32(base), np.float32)
+        cyc += [a.astype(np.float32), b.astype(np.float32), c]
+    return np.concatenate(cyc, axis=1) if cyc else np.zeros((labels.size, 0), np.float32)
 
 
 def qap_cost(F, D, p) -> int:

@@ -59,7 +59,8 @@ SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_
            "nmc_server_result", "nmc_server_cancel", "nmc_server_stats",
            "nmc_server_last_error", "nmc_batch_run_noalloc", "nmc_qap_batch_run",
            "nmc_replicas_set_ladder", "nmc_replicas_run_pt", "nmc_replicas_read_slots",
-           "nmc_adaptive_ladder", "nmc_replicas_cluster_flip"]
+           "nmc_adaptive_ladder", "nmc_replicas_cluster_flip", "nmc_cnf_lbp",
+           "nmc_cnf_backbone", "nmc_set_schedule_backbone"]
 
 
 def library_path() -> str:
@@ -119,6 +120,12 @@ def load(build_if_missing: bool = True):
             "nmc_adaptive_ladder": ([P, i32, i32, u64, C.c_double, C.c_double, C.c_double, i32,
                                      i32, i32, P, P, P], C.c_int),
             "nmc_replicas_cluster_flip": ([P, i32, i32, P, P, C.c_uint32, P], C.c_int),
+            "nmc_cnf_lbp": ([P, i32, i32, P, P, C.c_double, i32, P, C.c_double, i32, P, P, P, P,
+                             P, P], C.c_int),
+            "nmc_cnf_backbone": ([P, i32, i32, P, C.c_double, C.c_double, C.c_double, P, P],
+                                 C.c_int),
+            "nmc_set_schedule_backbone": ([P, i32, P, i32, i32, i32, i32, C.c_float, C.c_float],
+                                          C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -151,6 +158,7 @@ class Context:
         self._lib = load()
         self._kinds = {}
         self._units = {}
+        self._clauses = {}
         self._rs = {}
         h = C.c_void_p()
         s = None
@@ -200,6 +208,7 @@ class Context:
                                             _ptr(lits), C.byref(inst)))
         self._kinds[inst.value] = KIND_KSAT
         self._units[inst.value] = int(n_vars)
+        self._clauses[inst.value] = lits.shape[0]
         return inst.value
 
     def load_qap(self, F, D) -> int:
@@ -352,6 +361,56 @@ class Context:
                                                         _ptr(beta), int(move_id) & 0xFFFFFFFF,
                                                         _ptr(out)))
         return out
+
+    # -- learning stage (k-SAT)
+    def cnf_lbp(self, inst: int, x_star, beta: float, lambdas, tol: float, max_iter: int,
+                eps=None) -> dict:
+        """LBP around seeds x_star ([S, N] or [N] 0/1). Returns dict(marg [S,N], corr [S,M],
+        iters [S,L], deltas [S,L], n_done [S], p [S], q1 [S]) (one seed: the rows alone)."""
+        n = self._units[inst]
+        x = np.ascontiguousarray(x_star, dtype=np.uint8)
+        one = x.ndim == 1
+        x = x.reshape(-1, n)
+        S = x.shape[0]
+        lam = np.ascontiguousarray(np.atleast_1d(lambdas), dtype=np.float64)
+        eps = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
+        m = self._clauses[inst]
+        out = dict(marg=np.zeros((S, n)), corr=np.zeros((S, m)),
+                   iters=np.zeros((S, lam.size), np.int32), deltas=np.zeros((S, lam.size)),
+                   n_done=np.zeros(S, np.int32))
+        ov = np.zeros((S, 2))
+        self._check(self._lib.nmc_cnf_lbp(self._h, int(inst), S, _ptr(x), _ptr(eps), float(beta),
+                                          lam.size, _ptr(lam), float(tol), int(max_iter),
+                                          _ptr(out["marg"]), _ptr(out["corr"]),
+                                          _ptr(out["iters"]), _ptr(out["deltas"]),
+                                          _ptr(out["n_done"]), _ptr(ov)))
+        out["p"], out["q1"] = ov[:, 0].copy(), ov[:, 1].copy()
+        if one:
+            out = {k: v[0] for k, v in out.items()}
+        return out
+
+    def cnf_backbone(self, inst: int, corr, beta: float, seed_thr: float, cutoff: float):
+        """(labels int32 [S, N] or [N], n_clusters) from clause correlations [S, M] or [M]."""
+        n, m = self._units[inst], self._clauses[inst]
+        c = np.ascontiguousarray(corr, dtype=np.float64)
+        one = c.ndim == 1
+        c = c.reshape(-1, m)
+        S = c.shape[0]
+        lab = np.zeros((S, n), np.int32)
+        nc = np.zeros(S, np.int32)
+        self._check(self._lib.nmc_cnf_backbone(self._h, int(inst), S, _ptr(c), float(beta),
+                                               float(seed_thr), float(cutoff), _ptr(lab),
+                                               _ptr(nc)))
+        return (lab[0], int(nc[0])) if one else (lab, nc)
+
+    def set_schedule_backbone(self, inst: int, labels, cycles: int, t_hot: int, t_cold: int,
+                              t_unlearn: int, base: float, heat: float):
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        if lab.shape != (self._units[inst],):
+            raise ValueError("labels must have one entry per variable")
+        self._check(self._lib.nmc_set_schedule_backbone(self._h, int(inst), _ptr(lab), int(cycles),
+                                                        int(t_hot), int(t_cold), int(t_unlearn),
+                                                        float(base), float(heat)))
 
     def adaptive_ladder(self, inst: int, replicas: int, seed: int, beta0: float, alpha: float,
                         sigma_min: float, max_temps: int, sweeps_eq: int, sweeps_meas: int):

@@ -26,6 +26,8 @@ struct Instance {
   uint32_t *bq = nullptr;       // [n_steps][n_units] Q16, step-major (new ids for k-SAT)
   int32_t n_steps = 0;
   int users = 0;  // live replica sets
+  int32_t *lbp_vptr = nullptr;   // k-SAT: variable -> clause-slot CSR for LBP (built on first use)
+  int32_t *lbp_vedge = nullptr;
 };
 
 struct ReplicaSet {
@@ -138,6 +140,8 @@ void free_instance(Instance &I) {
   dev_free(I.qp.F);
   dev_free(I.qp.D);
   dev_free(I.bq);
+  dev_free(I.lbp_vptr);
+  dev_free(I.lbp_vedge);
 }
 
 void free_set(ReplicaSet &S) {
@@ -1366,6 +1370,242 @@ int nmc_replicas_cluster_flip(nmc_ctx *ctx, int32_t rs, int32_t mask_rows, const
   cudaFreeAsync(dev, ctx->stream);
   if (e == cudaSuccess && accepted_out) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "collective move");
+  return NMC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Variable -> clause-slot incidence (slots e = a * kmax + q in increasing order) of a k-SAT
+// instance, built from its device clause literals on first use and kept with the instance.
+int ensure_lbp_graph(nmc_ctx *ctx, Instance &I) {
+  if (I.lbp_vptr) return NMC_OK;
+  const int32_t n = I.ks.n;
+  const size_t slots = static_cast<size_t>(I.ks.m) * I.ks.kmax;
+  std::vector<int32_t> cl(slots > 0 ? slots : 1);
+  if (slots > 0)
+    NMC_CUDA(cudaMemcpy(cl.data(), I.ks.clits, sizeof(int32_t) * slots, cudaMemcpyDeviceToHost),
+             "read clause literals");
+  std::vector<int32_t> vptr(static_cast<size_t>(n) + 1, 0), vedge;
+  for (size_t e = 0; e < slots; ++e)
+    if (cl[e] < 2 * n) vptr[(cl[e] >> 1) + 1]++;
+  for (int32_t v = 0; v < n; ++v) vptr[v + 1] += vptr[v];
+  vedge.resize(static_cast<size_t>(vptr[n]) + 1);
+  std::vector<int32_t> fill(vptr.begin(), vptr.end() - 1);
+  for (size_t e = 0; e < slots; ++e)
+    if (cl[e] < 2 * n) vedge[fill[cl[e] >> 1]++] = static_cast<int32_t>(e);
+  int32_t *dp = nullptr, *de = nullptr;
+  cudaError_t e;
+  if ((e = dev_alloc(&dp, vptr.size())) != cudaSuccess || (e = dev_alloc(&de, vedge.size())) != cudaSuccess ||
+      (e = cudaMemcpy(dp, vptr.data(), sizeof(int32_t) * vptr.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(de, vedge.data(), sizeof(int32_t) * vedge.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    dev_free(dp);
+    dev_free(de);
+    return cuda_fail(ctx, e, "build LBP incidence");
+  }
+  I.lbp_vptr = dp;
+  I.lbp_vedge = de;
+  return NMC_OK;
+}
+
+// Device allocations released when the scope ends (after the stream has drained).
+struct DevScratch {
+  std::vector<void *> ptrs;
+  cudaStream_t st = nullptr;
+  ~DevScratch() {
+    if (st) cudaStreamSynchronize(st);
+    for (void *p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t get(T **p, size_t count) {
+    *p = nullptr;
+    const cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int nmc_cnf_lbp(nmc_ctx *ctx, int32_t inst, int32_t n_seeds, const uint8_t *x_star,
+                const double *eps, double beta, int32_t n_lambda, const double *lambdas,
+                double tol, int32_t max_iter, double *marg_out, double *corr_out,
+                int32_t *iters_out, double *deltas_out, int32_t *n_done_out,
+                double *overlap_out) {
+  if (!ctx) return NMC_EINVAL;
+  Instance *I = find_inst(ctx, inst);
+  if (!I || I->kind != NMC_KIND_KSAT) return fail(ctx, NMC_EINVAL, "needs a k-SAT instance");
+  if (n_seeds < 1 || !x_star || !marg_out || n_lambda < 1 || !lambdas || max_iter < 1)
+    return fail(ctx, NMC_EINVAL, "need seeds, lambdas, max_iter >= 1 and marg_out");
+  if (!std::isfinite(beta) || beta < 0.0 || !std::isfinite(tol) || tol < 0.0)
+    return fail(ctx, NMC_EINVAL, "beta and tol must be finite and >= 0");
+  const int32_t n = I->ks.n, m = I->ks.m, K = I->ks.kmax, S = n_seeds;
+  for (size_t i = 0; i < static_cast<size_t>(S) * n; ++i)
+    if (x_star[i] > 1) return fail(ctx, NMC_EINVAL, "seed states must be 0/1");
+  for (int32_t k = 0; k < n_lambda; ++k)
+    if (!std::isfinite(lambdas[k])) return fail(ctx, NMC_EINVAL, "lambdas must be finite");
+  if (eps)
+    for (int32_t i = 0; i < n; ++i)
+      if (!std::isfinite(eps[i])) return fail(ctx, NMC_EINVAL, "eps must be finite");
+  DeviceGuard dg(ctx->device);
+  int rc = ensure_lbp_graph(ctx, *I);
+  if (rc != NMC_OK) return rc;
+  NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  DevScratch d;
+  d.st = ctx->stream;
+  uint8_t *x_in = nullptr, *xs = nullptr;
+  double *eps_in = nullptr, *eps_d = nullptr, *marg = nullptr, *corr = nullptr, *deltas = nullptr,
+         *overlap = nullptr;
+  int32_t *iters = nullptr, *n_done = nullptr;
+  char *scratch = nullptr;
+  const size_t sn = static_cast<size_t>(S) * n;
+  NMC_CUDA(d.get(&x_in, sn), "allocate LBP seeds");
+  NMC_CUDA(d.get(&xs, sn), "allocate LBP seeds");
+  if (eps) NMC_CUDA(d.get(&eps_in, n), "allocate eps");
+  NMC_CUDA(d.get(&eps_d, n), "allocate eps");
+  NMC_CUDA(d.get(&marg, sn), "allocate marginals");
+  NMC_CUDA(d.get(&corr, static_cast<size_t>(S) * m), "allocate correlations");
+  NMC_CUDA(d.get(&iters, static_cast<size_t>(S) * n_lambda), "allocate LBP report");
+  NMC_CUDA(d.get(&deltas, static_cast<size_t>(S) * n_lambda), "allocate LBP report");
+  NMC_CUDA(d.get(&n_done, S), "allocate LBP report");
+  NMC_CUDA(d.get(&overlap, 2 * static_cast<size_t>(S)), "allocate LBP report");
+  NMC_CUDA(d.get(&scratch, lbp_scratch_bytes(n, m, K, S, n_lambda)),
+           "allocate LBP messages");
+  NMC_CUDA(cudaMemcpyAsync(x_in, x_star, sn, cudaMemcpyHostToDevice, ctx->stream), "upload seeds");
+  if (eps)
+    NMC_CUDA(cudaMemcpyAsync(eps_in, eps, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream),
+             "upload eps");
+  NMC_CUDA(lbp_prepare(x_in, eps_in, I->ks.orig, I->lbp_vptr, n, S, xs, eps_d, ctx->stream),
+           "prepare LBP");
+  LbpArgs A{};
+  A.clits = I->ks.clits;
+  A.vptr = I->lbp_vptr;
+  A.vedge = I->lbp_vedge;
+  A.orig = I->ks.orig;
+  A.n = n;
+  A.m = m;
+  A.kmax = K;
+  A.S = S;
+  A.n_lambda = n_lambda;
+  A.max_iter = max_iter;
+  A.eps = eps_d;
+  A.xs = xs;
+  A.lambdas = lambdas;
+  A.beta = beta;
+  A.tol = tol;
+  A.scratch = scratch;
+  A.marg = marg;
+  A.corr = corr;
+  A.iters = iters;
+  A.deltas = deltas;
+  A.n_done = n_done;
+  A.overlap = overlap;
+  const int err = lbp_run(A, ctx->stream);
+  if (err != 0) return cuda_fail(ctx, static_cast<cudaError_t>(err), "LBP");
+  NMC_CUDA(cudaMemcpyAsync(marg_out, marg, sizeof(double) * sn, cudaMemcpyDeviceToHost, ctx->stream), "read marginals");
+  if (corr_out)
+    NMC_CUDA(cudaMemcpyAsync(corr_out, corr, sizeof(double) * S * static_cast<size_t>(m), cudaMemcpyDeviceToHost, ctx->stream), "read correlations");
+  if (iters_out)
+    NMC_CUDA(cudaMemcpyAsync(iters_out, iters, sizeof(int32_t) * S * static_cast<size_t>(n_lambda), cudaMemcpyDeviceToHost, ctx->stream), "read LBP report");
+  if (deltas_out)
+    NMC_CUDA(cudaMemcpyAsync(deltas_out, deltas, sizeof(double) * S * static_cast<size_t>(n_lambda), cudaMemcpyDeviceToHost, ctx->stream), "read LBP report");
+  if (n_done_out)
+    NMC_CUDA(cudaMemcpyAsync(n_done_out, n_done, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, ctx->stream), "read LBP report");
+  if (overlap_out)
+    NMC_CUDA(cudaMemcpyAsync(overlap_out, overlap, sizeof(double) * 2 * S, cudaMemcpyDeviceToHost, ctx->stream), "read LBP report");
+  NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  return NMC_OK;
+}
+
+int nmc_cnf_backbone(nmc_ctx *ctx, int32_t inst, int32_t n_seeds, const double *corr,
+                     double beta, double seed_thr, double cutoff, int32_t *labels_out,
+                     int32_t *n_clusters_out) {
+  if (!ctx) return NMC_EINVAL;
+  Instance *I = find_inst(ctx, inst);
+  if (!I || I->kind != NMC_KIND_KSAT) return fail(ctx, NMC_EINVAL, "needs a k-SAT instance");
+  if (n_seeds < 1 || !corr || !labels_out) return fail(ctx, NMC_EINVAL, "need correlations and labels_out");
+  if (!std::isfinite(beta) || beta <= 0.0 || std::isnan(seed_thr) || std::isnan(cutoff))
+    return fail(ctx, NMC_EINVAL, "beta must be finite and > 0, thresholds not NaN");
+  const int32_t n = I->ks.n, m = I->ks.m, S = n_seeds;
+  for (size_t i = 0; i < static_cast<size_t>(S) * m; ++i)
+    if (!(corr[i] >= -1.0 && corr[i] <= 1.0)) return fail(ctx, NMC_EINVAL, "correlations must be in [-1, 1]");
+  DeviceGuard dg(ctx->device);
+  NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  DevScratch d;
+  d.st = ctx->stream;
+  double *corr_d = nullptr;
+  int32_t *lab = nullptr, *ncl = nullptr;
+  char *scratch = nullptr;
+  NMC_CUDA(d.get(&corr_d, static_cast<size_t>(S) * m), "allocate correlations");
+  NMC_CUDA(d.get(&lab, static_cast<size_t>(S) * n), "allocate labels");
+  NMC_CUDA(d.get(&ncl, S), "allocate labels");
+  NMC_CUDA(d.get(&scratch, backbone_scratch_bytes(n, m, S)), "allocate backbone scratch");
+  NMC_CUDA(cudaMemcpyAsync(corr_d, corr, sizeof(double) * S * static_cast<size_t>(m), cudaMemcpyHostToDevice, ctx->stream), "upload correlations");
+  BackboneArgs A{};
+  A.clits = I->ks.clits;
+  A.orig = I->ks.orig;
+  A.newid = I->ks.newid;
+  A.n = n;
+  A.m = m;
+  A.kmax = I->ks.kmax;
+  A.S = S;
+  A.corr = corr_d;
+  A.beta = beta;
+  A.seed_thr = seed_thr;
+  A.cutoff = cutoff;
+  A.scratch = scratch;
+  A.labels = lab;
+  A.n_clusters = ncl;
+  const int err = backbone_run(A, ctx->stream);
+  if (err != 0) return cuda_fail(ctx, static_cast<cudaError_t>(err), "backbone growth");
+  NMC_CUDA(cudaMemcpyAsync(labels_out, lab, sizeof(int32_t) * S * static_cast<size_t>(n), cudaMemcpyDeviceToHost, ctx->stream), "read labels");
+  if (n_clusters_out)
+    NMC_CUDA(cudaMemcpyAsync(n_clusters_out, ncl, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, ctx->stream), "read labels");
+  NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  return NMC_OK;
+}
+
+int nmc_set_schedule_backbone(nmc_ctx *ctx, int32_t inst, const int32_t *labels, int32_t cycles,
+                              int32_t t_hot, int32_t t_cold, int32_t t_unlearn, float base,
+                              float heat) {
+  if (!ctx) return NMC_EINVAL;
+  Instance *I = find_inst(ctx, inst);
+  if (!I || I->kind != NMC_KIND_KSAT) return fail(ctx, NMC_EINVAL, "needs a k-SAT instance");
+  if (!labels || cycles < 1 || t_hot < 0 || t_cold < 0 || t_unlearn < 0)
+    return fail(ctx, NMC_EINVAL, "need labels, cycles >= 1 and phase lengths >= 0");
+  const int64_t cyc = static_cast<int64_t>(t_hot) + t_cold + t_unlearn;
+  if (cyc < 1 || cyc * cycles > 0x7FFFFFFF) return fail(ctx, NMC_EINVAL, "bad phase lengths");
+  const float hot = base / heat;
+  if (!(base >= 0.0f && base <= 65535.0f) || !(heat > 0.0f) || !std::isfinite(heat) ||
+      !(hot >= 0.0f && hot <= 65535.0f))
+    return fail(ctx, NMC_EINVAL, "base and base/heat must be in [0, 65535], heat > 0");
+  const int32_t n = I->ks.n, n_steps = static_cast<int32_t>(cyc * cycles);
+  DeviceGuard dg(ctx->device);
+  int32_t *lab = nullptr;
+  uint32_t *bq = nullptr;
+  cudaError_t e;
+  if ((e = cudaMallocAsync(reinterpret_cast<void **>(&lab), sizeof(int32_t) * n, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "allocate labels");
+  if ((e = cudaMalloc(&bq, sizeof(uint32_t) * static_cast<size_t>(n) * n_steps)) != cudaSuccess) {
+    cudaFreeAsync(lab, ctx->stream);
+    return cuda_fail(ctx, e, "allocate schedule");
+  }
+  e = cudaMemcpyAsync(lab, labels, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = backbone_schedule(lab, I->ks.orig, n, n_steps, base, heat, t_hot, t_cold, t_unlearn, bq,
+                          ctx->stream);
+  cudaFreeAsync(lab, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    cudaFree(bq);
+    return cuda_fail(ctx, e, "backbone schedule");
+  }
+  dev_free(I->bq);
+  I->bq = bq;
+  I->n_steps = n_steps;
   return NMC_OK;
 }
 

@@ -195,6 +195,46 @@ cudaError_t ksat_cluster_flip(const KsatDevice &I, KsatReplicas &Rp, const uint8
                               uint64_t seed, const uint32_t *tab, int32_t tab_len, void *scratch,
                               uint8_t *acc_dev, cudaStream_t st);
 
+// ---- learning stage: CNF LBP, backbones, two-chain schedule (lbp.cu) ----------------------
+struct LbpArgs {
+  const int32_t *clits, *vptr, *vedge, *orig;  // device: clause literal ids, var -> edge CSR
+  int32_t n, m, kmax, S, n_lambda, max_iter;
+  const double *eps;      // device [n], new order
+  const uint8_t *xs;      // device [n][S] seeds (0/1), new order, seed fastest
+  const double *lambdas;  // host [n_lambda]
+  double beta, tol;
+  void *scratch;          // lbp_scratch_bytes
+  double *marg;           // device out [S][n], original order
+  double *corr;           // device out [S][m]
+  int32_t *iters;         // device out [S][n_lambda]
+  double *deltas;         // device out [S][n_lambda]
+  int32_t *n_done;        // device out [S]
+  double *overlap;        // device out [S][2]: p, q1
+};
+size_t lbp_scratch_bytes(int32_t n, int32_t m, int32_t kmax, int32_t S, int32_t n_lambda);
+cudaError_t lbp_prepare(const uint8_t *x_in, const double *eps_in, const int32_t *orig,
+                        const int32_t *vptr, int32_t n, int32_t S, uint8_t *xs, double *eps,
+                        cudaStream_t st);
+// Runs the continuation; returns 0 or a cudaError_t value. Synchronises the stream once per
+// iteration (to see whether any seed is still iterating).
+int lbp_run(const LbpArgs &A, cudaStream_t st);
+
+struct BackboneArgs {
+  const int32_t *clits, *orig, *newid;
+  int32_t n, m, kmax, S;
+  const double *corr;  // device [S][m]
+  double beta, seed_thr, cutoff;
+  void *scratch;       // backbone_scratch_bytes
+  int32_t *labels;     // device out [S][n], original order
+  int32_t *n_clusters; // device out [S]
+};
+size_t backbone_scratch_bytes(int32_t n, int32_t m, int32_t S);
+int backbone_run(const BackboneArgs &A, cudaStream_t st);
+// lab: device [n] labels in original order (-1 = not in a backbone); bq [n_steps][n] new order.
+cudaError_t backbone_schedule(const int32_t *lab, const int32_t *orig, int32_t n, int32_t n_steps,
+                              float base, float heat, int32_t t_hot, int32_t t_cold,
+                              int32_t t_unlearn, uint32_t *bq, cudaStream_t st);
+
 // ---- QAP launchers (qap.cu) ------------------------------------------------------------
 // Arguments of one QAP launch (or, in a batched launch, of one CTA: one block of 32 replicas).
 struct QapArgs {

@@ -712,3 +712,138 @@ def test_cluster_moves_keep_the_boltzmann_law():
     assert _chi2_pvalue(counts, w / w.sum()) > 1e-4
     w_bad = np.exp(+np.float64(np.float32(b)) * E)
     assert _chi2_pvalue(counts, w_bad / w_bad.sum()) < 1e-6
+
+
+# ---------------------------------------------------------------- CNF LBP and backbones
+def _tree_cnf(seed):
+    """A CNF whose factor graph is a tree: every clause after the first shares exactly one
+    variable with the clauses before it. 13 variables, clauses of 2 to 4 literals."""
+    rng = np.random.default_rng(seed)
+    groups = [[0, 1, 2], [2, 3, 4], [2, 5], [4, 6, 7], [7, 8, 9, 10], [1, 11], [11, 12]]
+    lits = np.zeros((len(groups), 4), np.int32)
+    for a, g in enumerate(groups):
+        lits[a, :len(g)] = (np.array(g) + 1) * rng.choice([-1, 1], size=len(g))
+    return lits, 13
+
+
+def _exact_cnf_marginals(lits, n, x_star, eps, beta, lam):
+    """<r_i> and <prod_{i in a} r_i> under P(r) ~ prod_a omega_a(r) prod_i exp(lam eps_i s*_i r_i)
+    by enumeration of all 2^n states (omega_a = exp(-2 beta) when clause a is violated)."""
+    X = all_states(n)
+    Rs = 2.0 * X - 1.0
+    viol = energies_numpy(lits, X).astype(np.float64)
+    s = 2.0 * np.asarray(x_star, np.float64) - 1.0
+    logw = -2.0 * beta * viol + (Rs * (lam * np.asarray(eps) * s)).sum(axis=1)
+    w = np.exp(logw - logw.max())
+    w /= w.sum()
+    marg = (w[:, None] * Rs).sum(axis=0)
+    corr = []
+    for row in lits:
+        vs = np.abs(row[row != 0]) - 1
+        corr.append(float((w * Rs[:, vs].prod(axis=1)).sum()))
+    return marg, np.array(corr)
+
+
+@pytest.mark.parametrize("seed,beta,lam", [(1, 0.7, 0.3), (2, 2.0, 0.1), (3, 1.2, 0.0),
+                                           (4, 3.0, 0.05)])
+def test_lbp_is_exact_on_a_tree(seed, beta, lam):
+    """Belief propagation is exact on a tree factor graph: the oracle's fixed point gives the
+    enumerated marginals and clause correlations of the surrogate distribution."""
+    lits, n = _tree_cnf(seed)
+    x = np.random.default_rng(seed + 10).integers(0, 2, n).astype(np.uint8)
+    eps = O.clause_degrees(lits, n)
+    r = O.cnf_lbp(lits, n, x, beta, [lam], 1e-15, 200, eps=eps)
+    assert r["n_done"] == 1
+    marg, corr = _exact_cnf_marginals(lits, n, x, eps, beta, lam)
+    assert np.allclose(r["marg"], marg, atol=1e-10, rtol=0)
+    assert np.allclose(r["corr"], corr, atol=1e-10, rtol=0)
+    s = 2.0 * x - 1.0
+    assert abs(r["p"] - float((s * marg).mean())) < 1e-10
+    assert abs(r["q1"] - float((marg ** 2).mean())) < 1e-10
+
+
+def test_lbp_at_zero_beta_leaves_the_bias_alone():
+    n = 60
+    lits = W.random_ksat(n, 4.2, 3, 2)
+    x = np.random.default_rng(3).integers(0, 2, n).astype(np.uint8)
+    eps = O.clause_degrees(lits, n)
+    r = O.cnf_lbp(lits, n, x, 0.0, [0.07], 1e-14, 50, eps=eps)
+    field = 0.07 * eps * (2.0 * x - 1.0)
+    assert np.allclose(r["marg"], np.tanh(field), atol=1e-14, rtol=0)
+    want = [np.prod(np.tanh(field[np.abs(row[row != 0]) - 1])) for row in lits]
+    assert np.allclose(r["corr"], want, atol=1e-14, rtol=0)
+
+
+def test_lbp_continuation_falls_back_to_the_last_converged_lambda():
+    n = 300
+    lits = W.random_ksat(n, 9.6, 4, 6)
+    x = np.random.default_rng(4).integers(0, 2, n).astype(np.uint8)
+    lams = [0.5, 0.2, 0.1, 0.05, 0.02, 0.01, 0.005]
+    full = O.cnf_lbp(lits, n, x, 1.0, lams, 1e-9, 15)
+    k = full["n_done"]
+    assert 0 < k < len(lams), full["iters"]
+    assert full["iters"][k] == 15 and full["deltas"][k] >= 1e-9 and full["lam"] == lams[k - 1]
+    part = O.cnf_lbp(lits, n, x, 1.0, lams[:k], 1e-9, 15)
+    assert part["n_done"] == k
+    for key in ("marg", "corr"):
+        assert np.array_equal(full[key], part[key]), key
+    assert np.all(full["iters"][k + 1:] == 0)
+
+
+def _components_union_find(lits, n, corr, beta, seed_thr, cutoff):
+    parent = list(range(n))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+    jt = np.arctanh(np.abs(corr)) / beta
+    link = (jt > cutoff) | (jt > seed_thr)
+    touched = np.zeros(n, bool)
+    for a, row in enumerate(lits):
+        if not link[a]:
+            continue
+        vs = np.abs(row[row != 0]) - 1
+        touched[vs] = True
+        for v in vs[1:]:
+            ra, rb = find(int(vs[0])), find(int(v))
+            if ra != rb:
+                parent[max(ra, rb)] = min(ra, rb)
+    seeded = set()
+    for a, row in enumerate(lits):
+        if jt[a] > seed_thr:
+            seeded.add(find(int(np.abs(row[row != 0])[0]) - 1))
+    lab = np.full(n, -1, np.int32)
+    for v in range(n):
+        if touched[v] and find(v) in seeded:
+            lab[v] = find(v)
+    return lab
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_backbones_are_the_seeded_components(seed):
+    """Clusters grown seed by seed (the oracle) equal the connected components, under the
+    factors above the cutoff, that hold a seed factor (union-find), labelled by their smallest
+    variable."""
+    n = 400
+    lits = W.random_ksat(n, 4.2, 3, 70 + seed)
+    rng = np.random.default_rng(seed)
+    corr = np.tanh(rng.exponential(0.6, lits.shape[0])) * rng.choice([-1, 1], lits.shape[0])
+    for seed_thr, cutoff in [(1.5, 1.2), (2.0, 0.9), (0.8, 1.0)]:
+        lab, nc = O.cnf_backbone(lits, n, corr, 1.0, seed_thr, cutoff)
+        want = _components_union_find(lits, n, corr, 1.0, seed_thr, cutoff)
+        assert np.array_equal(lab, want)
+        assert nc == len(set(want[want >= 0].tolist()))
+
+
+def test_backbone_schedule_layout():
+    lab = np.array([-1, 3, 3, -1, 0], np.int32)
+    b = O.backbone_schedule(lab, 2.0, 4.0, 2, 3, 2, 1)
+    assert b.shape == (5, 12) and b.dtype == np.float32
+    hot, cold, unl = b[:, 0:3], b[:, 3:5], b[:, 5:6]
+    bb = lab >= 0
+    assert np.all(hot[bb] == np.float32(0.5)) and np.all(np.isinf(hot[~bb]))
+    assert np.all(np.isinf(cold[bb])) and np.all(cold[~bb] == 2.0)
+    assert np.all(unl == 2.0)
+    assert np.array_equal(b[:, :6], b[:, 6:])
