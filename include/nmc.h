@@ -289,6 +289,20 @@ int nmc_set_schedule_backbone(nmc_ctx *ctx, int32_t inst, const int32_t *labels,
                               float heat);
 
 /*
+ * Whitening (Sec. "Whitening procedure for low energy states") of every replica of a k-SAT set,
+ * on its current states (use_best = 0) or its best states (use_best = 1). A variable turns
+ * white when no clause containing it blocks it; a clause blocks v when it is neither satisfied
+ * by another of its variables nor holds another white variable, and, with generalized != 0 (the
+ * paper's extension to low-energy states), when it is moreover satisfied by v itself, so that
+ * violated clauses never report a frozen variable. Whitening runs to its fixed point (the same
+ * for any inspection order); frozen = not white. frozen_count_out: host int32 [R] (required);
+ * frozen_out: host uint8 [R][N] 0/1, original order (nullable); rounds_out (nullable): parallel
+ * rounds run. Synchronises.
+ */
+int nmc_replicas_whitening(nmc_ctx *ctx, int32_t rs, int32_t use_best, int32_t generalized,
+                           int32_t *frozen_count_out, uint8_t *frozen_out, int32_t *rounds_out);
+
+/*
  * Adaptive ladder (App. "Adaptive Parallel Tempering"): beta_0 = beta0; for level i the k-SAT
  * instance's `replicas` chains (a temporary set seeded by `seed`, Philox initial states, each
  * level continuing from the previous level's states) run sweeps_eq + sweeps_meas sweeps

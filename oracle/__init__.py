@@ -76,6 +76,8 @@ def _load():
             lib.orc_cnf_lbp.restype = C.c_int
             lib.orc_cnf_backbone.argtypes = [i32, i32, i32, P, P, dbl, dbl, dbl, P]
             lib.orc_cnf_backbone.restype = i32
+            lib.orc_ksat_whitening.argtypes = [i32, i32, i32, P, P, i32, P]
+            lib.orc_ksat_whitening.restype = i32
             lib.orc_qap_cost.argtypes = [i32, P, P, P]
             lib.orc_qap_cost.restype = i64
             lib.orc_qap_swap_delta.argtypes = [i32, P, P, P, i32, i32]
@@ -281,6 +283,15 @@ def adaptive_ladder(lits, n_vars, replicas, seed, beta0, alpha, sigma_min, max_t
             break
         beta = beta + alpha / sigma
     return np.array(betas, dtype=np.float64), np.array(sigmas, dtype=np.float64)
+
+
+def ksat_whitening(lits, n_vars, x, generalized=True):
+    """(frozen uint8[N], count) of the whitening procedure on assignment x (0/1)."""
+    lits, m, k = _cnf(lits)
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    fr = np.zeros(n_vars, dtype=np.uint8)
+    c = _load().orc_ksat_whitening(n_vars, m, k, _p(lits), _p(x), int(bool(generalized)), _p(fr))
+    return fr, int(c)
 
 
 def clause_degrees(lits, n_vars):

@@ -43,6 +43,7 @@
  *    and accepts when dE = E(x') - E(x) <= 0, else iff ((bq dE) >> 8) < L and u < Tab[...] with
  *    bq = Q16(beta_r) and u = word r&3 of the Philox block for counter
  *    (move_id, 0, r>>2, TAG_CLUSTER); the best-so-far follows on strictly lower E.
+ *  Whitening (Sec. "Whitening procedure for low energy states"): see orc_ksat_whitening.
  *  Energy statistics (the adaptive ladder of the same appendix measures the energy variance at
  *    each temperature): sums of E and E^2 of every replica over the end-of-sweep energies of
  *    the sweeps t >= stats_t0.
@@ -795,4 +796,58 @@ int orc_ksat_cluster_flip(int32_t n, int32_t m, int32_t kmax, const int32_t *lit
   }
   free(y);
   return 0;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Whitening (Sec. "Whitening procedure for low energy states").
+ * ------------------------------------------------------------------------------------- */
+/*
+ * Variables are inspected one at a time, in id order, repeatedly until a whole pass marks
+ * nothing new. Variable v becomes white (star) when no clause containing it blocks it. A clause
+ * blocks v when it is neither satisfied by another of its variables nor holds another white
+ * variable; with `generalized` (the paper's extension to low-energy states) a clause only blocks v
+ * when it is moreover satisfied by v itself, so violated clauses never report a frozen variable.
+ * frozen: n uint8 out (1 = not white at the fixed point). Returns the number of frozen variables.
+ */
+int32_t orc_ksat_whitening(int32_t n, int32_t m, int32_t kmax, const int32_t *lits,
+                           const uint8_t *x, int32_t generalized, uint8_t *frozen) {
+  orc_cnf f;
+  cnf_build(&f, n, m, kmax, lits);
+  uint8_t *star = (uint8_t *)calloc((size_t)n + 1, 1);
+  int changed = 1;
+  while (changed) {
+    changed = 0;
+    for (int32_t v = 0; v < n; ++v) {
+      if (star[v]) continue;
+      int blocked = 0;
+      for (int32_t e = f.inc_ptr[v]; e < f.inc_ptr[v + 1] && !blocked; ++e) {
+        const int64_t a = f.inc[e];
+        int other_true = 0, other_star = 0, own_true = 0;
+        for (int q = 0; q < kmax; ++q) {
+          const int32_t l = lits[a * kmax + q];
+          if (l == 0) continue;
+          const int u = lit_var(l);
+          if (u == v) {
+            own_true = lit_true(l, x);
+          } else {
+            if (lit_true(l, x)) other_true = 1;
+            if (star[u]) other_star = 1;
+          }
+        }
+        if (!other_true && !other_star && (own_true || !generalized)) blocked = 1;
+      }
+      if (!blocked) {
+        star[v] = 1;
+        changed = 1;
+      }
+    }
+  }
+  int32_t cnt = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    frozen[v] = (uint8_t)(star[v] ? 0 : 1);
+    cnt += frozen[v];
+  }
+  free(star);
+  cnf_free(&f);
+  return cnt;
 }

@@ -60,7 +60,7 @@ SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_
            "nmc_server_last_error", "nmc_batch_run_noalloc", "nmc_qap_batch_run",
            "nmc_replicas_set_ladder", "nmc_replicas_run_pt", "nmc_replicas_read_slots",
            "nmc_adaptive_ladder", "nmc_replicas_cluster_flip", "nmc_cnf_lbp",
-           "nmc_cnf_backbone", "nmc_set_schedule_backbone"]
+           "nmc_cnf_backbone", "nmc_set_schedule_backbone", "nmc_replicas_whitening"]
 
 
 def library_path() -> str:
@@ -126,6 +126,7 @@ def load(build_if_missing: bool = True):
                                  C.c_int),
             "nmc_set_schedule_backbone": ([P, i32, P, i32, i32, i32, i32, C.c_float, C.c_float],
                                           C.c_int),
+            "nmc_replicas_whitening": ([P, i32, i32, i32, P, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -411,6 +412,19 @@ class Context:
         self._check(self._lib.nmc_set_schedule_backbone(self._h, int(inst), _ptr(lab), int(cycles),
                                                         int(t_hot), int(t_cold), int(t_unlearn),
                                                         float(base), float(heat)))
+
+    def whitening(self, rs: int, use_best: bool = False, generalized: bool = True,
+                  masks: bool = False):
+        """Frozen-variable counts (int32 [R]) of the whitening procedure; with masks=True also
+        the frozen flags (uint8 [R, N]) and the number of parallel rounds."""
+        inst, R = self._rs[rs]
+        cnt = np.zeros(R, np.int32)
+        fr = np.zeros((R, self._units[inst]), np.uint8) if masks else None
+        rounds = C.c_int32()
+        self._check(self._lib.nmc_replicas_whitening(self._h, int(rs), int(bool(use_best)),
+                                                     int(bool(generalized)), _ptr(cnt), _ptr(fr),
+                                                     C.byref(rounds)))
+        return (cnt, fr, rounds.value) if masks else cnt
 
     def adaptive_ladder(self, inst: int, replicas: int, seed: int, beta0: float, alpha: float,
                         sigma_min: float, max_temps: int, sweeps_eq: int, sweeps_meas: int):

@@ -10,7 +10,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnmc.so")
-SOURCES = ["api.cu", "ksat.cu", "qap.cu", "batch.cu", "pt.cu", "cluster.cu", "lbp.cu", "server.cpp"]
+SOURCES = ["api.cu", "ksat.cu", "qap.cu", "batch.cu", "pt.cu", "cluster.cu", "lbp.cu", "whitening.cu", "server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

@@ -1568,6 +1568,37 @@ int nmc_cnf_backbone(nmc_ctx *ctx, int32_t inst, int32_t n_seeds, const double *
   return NMC_OK;
 }
 
+int nmc_replicas_whitening(nmc_ctx *ctx, int32_t rs, int32_t use_best, int32_t generalized,
+                           int32_t *frozen_count_out, uint8_t *frozen_out, int32_t *rounds_out) {
+  if (!ctx) return NMC_EINVAL;
+  ReplicaSet *S = find_set(ctx, rs);
+  if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
+  Instance *I = find_inst(ctx, S->inst);
+  if (!I) return fail(ctx, NMC_ESTATE, "instance was unloaded");
+  if (I->kind != NMC_KIND_KSAT) return fail(ctx, NMC_EINVAL, "whitening needs a k-SAT set");
+  if (!frozen_count_out) return fail(ctx, NMC_EINVAL, "frozen_count_out is NULL");
+  const int32_t n = I->ks.n, R = S->R, W = S->ks.W;
+  DeviceGuard dg(ctx->device);
+  DevScratch d;
+  d.st = ctx->stream;
+  int32_t *count = nullptr;
+  uint8_t *frozen = nullptr;
+  char *scratch = nullptr;
+  NMC_CUDA(d.get(&count, R), "allocate whitening output");
+  if (frozen_out) NMC_CUDA(d.get(&frozen, static_cast<size_t>(R) * n), "allocate whitening output");
+  NMC_CUDA(d.get(&scratch, whitening_scratch_bytes(n, W)), "allocate whitening scratch");
+  int32_t rounds = 0;
+  const int err = whitening_run(I->ks, use_best ? S->ks.best : S->ks.S, use_best ? 1 : 2, R, W,
+                                generalized ? 1 : 0, scratch, count, frozen, &rounds, ctx->stream);
+  if (err != 0) return cuda_fail(ctx, static_cast<cudaError_t>(err), "whitening");
+  NMC_CUDA(cudaMemcpyAsync(frozen_count_out, count, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, ctx->stream), "read whitening");
+  if (frozen_out)
+    NMC_CUDA(cudaMemcpyAsync(frozen_out, frozen, static_cast<size_t>(R) * n, cudaMemcpyDeviceToHost, ctx->stream), "read whitening");
+  NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  if (rounds_out) *rounds_out = rounds;
+  return NMC_OK;
+}
+
 int nmc_set_schedule_backbone(nmc_ctx *ctx, int32_t inst, const int32_t *labels, int32_t cycles,
                               int32_t t_hot, int32_t t_cold, int32_t t_unlearn, float base,
                               float heat) {

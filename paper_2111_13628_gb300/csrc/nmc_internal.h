@@ -235,6 +235,15 @@ cudaError_t backbone_schedule(const int32_t *lab, const int32_t *orig, int32_t n
                               float base, float heat, int32_t t_hot, int32_t t_cold,
                               int32_t t_unlearn, uint32_t *bq, cudaStream_t st);
 
+// ---- whitening (whitening.cu) ------------------------------------------------------------
+size_t whitening_scratch_bytes(int32_t n, int32_t W);
+// X: state words, variable u's word w at X[u * xrows2 * W + w] (S with xrows2 = 2, best with 1).
+// count: device [R]; frozen: device [R][n] original order (nullable); *rounds: rounds run.
+// Returns 0 or a cudaError_t value; synchronises once per round.
+int whitening_run(const KsatDevice &I, const uint32_t *X, int32_t xrows2, int32_t R, int32_t W,
+                  int generalized, void *scratch, int32_t *count, uint8_t *frozen, int32_t *rounds,
+                  cudaStream_t st);
+
 // ---- QAP launchers (qap.cu) ------------------------------------------------------------
 // Arguments of one QAP launch (or, in a batched launch, of one CTA: one block of 32 replicas).
 struct QapArgs {

@@ -1,0 +1,140 @@
+// Whitening of k-SAT states (Sec. "Whitening procedure for low energy states"), 32 replicas per
+// word. A variable turns white (star) when no clause containing it blocks it; a clause blocks v
+// when it is neither satisfied by another of its variables nor holds another white variable
+// (generalized form: and it is satisfied by v itself, so violated clauses never report a frozen
+// variable). White sets only grow and the blocking test is monotone in them, so the parallel
+// rounds used here (every variable tested against the previous round's white set) reach the same
+// fixed point as inspecting one variable at a time. Frozen = not white at the fixed point.
+//
+// Per (variable v, word w) and occurrence (clause a): own = truth word of v's literal in a, o =
+// OR of the other literals' truth words (rows of the state array S), so = OR of the other
+// variables' white words; block = ~o & ~so (& own when generalized). Padding entries of the
+// occurrence lists read as always-true literals (o = ~0) and never block.
+#include "nmc_internal.h"
+
+namespace nmc {
+
+namespace {
+
+constexpr int kWhiteBlock = 256;
+
+template <int KQ>
+__global__ void white_round_kernel(const int4 *__restrict__ occ, const int32_t *__restrict__ occ_ptr,
+                                   const uint32_t *__restrict__ X, int32_t xrows2, int32_t n,
+                                   int32_t W, const uint32_t *__restrict__ star, uint32_t *star_new,
+                                   int generalized, int32_t *changed) {
+  const long long total = (long long)n * W;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(i / W), w = (int)(i % W);
+    const uint32_t s0 = star[i];
+    if (s0 == 0xFFFFFFFFu) {
+      star_new[i] = s0;
+      continue;
+    }
+    // truth word of literal id l (2u + neg): the state row of u, complemented when negated; the
+    // padding literals 2n (false) and 2n+1 (true) address the constant rows / zero star row n
+    auto lit = [&](int l) -> uint32_t {
+      const int u = l >> 1;
+      const uint32_t xu = u < n ? X[(size_t)u * xrows2 * W + w] : 0u;
+      return (l & 1) ? ~xu : xu;
+    };
+    auto st = [&](int l) -> uint32_t { return (l >> 1) < n ? star[(size_t)(l >> 1) * W + w] : 0u; };
+    const uint32_t x = X[(size_t)v * xrows2 * W + w];
+    uint32_t blocked = 0u;
+    for (int e = occ_ptr[v]; e < occ_ptr[v + 1]; ++e) {
+      const int4 q = occ[(size_t)e * KQ];
+      uint32_t o = lit(q.y) | lit(q.z) | lit(q.w);
+      uint32_t so = st(q.y) | st(q.z) | st(q.w);
+      if (KQ == 2) {
+        const int4 q2 = occ[(size_t)e * KQ + 1];
+        o |= lit(q2.x) | lit(q2.y) | lit(q2.z) | lit(q2.w);
+        so |= st(q2.x) | st(q2.y) | st(q2.z) | st(q2.w);
+      }
+      uint32_t b = ~o & ~so;
+      if (generalized) b &= x ^ (uint32_t)q.x;  // v's own literal is true
+      blocked |= b;
+    }
+    const uint32_t s1 = s0 | ~blocked;
+    star_new[i] = s1;
+    if (s1 != s0) *changed = 1;
+  }
+}
+
+// frozen count of replica 32w + j: variables whose white bit j stays clear.
+__global__ void white_count_kernel(const uint32_t *__restrict__ star, int32_t n, int32_t R, int32_t W,
+                                   int32_t *count) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int w = r >> 5;
+  const uint32_t bit = 1u << (r & 31);
+  int c = 0;
+  for (int v = 0; v < n; ++v) c += (star[(size_t)v * W + w] & bit) ? 0 : 1;
+  count[r] = c;
+}
+
+// frozen[r][orig v] = 1 - white bit.
+__global__ void white_unpack_kernel(const uint32_t *__restrict__ star, const int32_t *__restrict__ orig,
+                                    int32_t n, int32_t R, int32_t W, uint8_t *frozen) {
+  const long long total = (long long)n * R;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / n), v = (int)(i % n);
+    frozen[(size_t)r * n + orig[v]] = (star[(size_t)v * W + (r >> 5)] >> (r & 31)) & 1u ? 0 : 1;
+  }
+}
+
+unsigned white_blocks(long long work) {
+  long long g = (work + kWhiteBlock - 1) / kWhiteBlock;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+size_t whitening_scratch_bytes(int32_t n, int32_t W) {
+  auto up = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+  return 2 * up(sizeof(uint32_t) * (size_t)(n + 1) * W) + up(sizeof(int32_t));
+}
+
+int whitening_run(const KsatDevice &I, const uint32_t *X, int32_t xrows2, int32_t R, int32_t W,
+                  int generalized, void *scratch, int32_t *count, uint8_t *frozen, int32_t *rounds,
+                  cudaStream_t st) {
+  auto up = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+  const int32_t n = I.n;
+  char *p = static_cast<char *>(scratch);
+  uint32_t *a = reinterpret_cast<uint32_t *>(p); p += up(sizeof(uint32_t) * (size_t)(n + 1) * W);
+  uint32_t *b = reinterpret_cast<uint32_t *>(p); p += up(sizeof(uint32_t) * (size_t)(n + 1) * W);
+  int32_t *changed = reinterpret_cast<int32_t *>(p);
+  cudaError_t e;
+  // rows 0..n of both buffers start clear (row n: the padding literals' variable, never white)
+  if ((e = cudaMemsetAsync(a, 0, sizeof(uint32_t) * (size_t)(n + 1) * W, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(b, 0, sizeof(uint32_t) * (size_t)(n + 1) * W, st)) != cudaSuccess)
+    return (int)e;
+  int32_t r = 0;
+  for (; r <= n + 1; ++r) {
+    if ((e = cudaMemsetAsync(changed, 0, sizeof(int32_t), st)) != cudaSuccess) return (int)e;
+    if (I.kq == 1)
+      white_round_kernel<1><<<white_blocks((long long)n * W), kWhiteBlock, 0, st>>>(
+          I.occ, I.occ_ptr, X, xrows2, n, W, a, b, generalized, changed);
+    else
+      white_round_kernel<2><<<white_blocks((long long)n * W), kWhiteBlock, 0, st>>>(
+          I.occ, I.occ_ptr, X, xrows2, n, W, a, b, generalized, changed);
+    if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+    int32_t ch = 0;
+    if ((e = cudaMemcpyAsync(&ch, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return (int)e;
+    uint32_t *t = a;
+    a = b;
+    b = t;
+    if (!ch) break;
+  }
+  *rounds = r + 1;
+  white_count_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(a, n, R, W, count);
+  if (frozen)
+    white_unpack_kernel<<<white_blocks((long long)n * R), kWhiteBlock, 0, st>>>(a, I.orig, n, R, W, frozen);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace nmc

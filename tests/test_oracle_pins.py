@@ -847,3 +847,97 @@ def test_backbone_schedule_layout():
     assert np.all(np.isinf(cold[bb])) and np.all(cold[~bb] == 2.0)
     assert np.all(unl == 2.0)
     assert np.array_equal(b[:, :6], b[:, 6:])
+
+
+# ---------------------------------------------------------------- whitening
+def _blocking(lits, n, x, star, generalized):
+    """blocked[v]: some clause containing v is neither satisfied by another of its variables nor
+    holds another white variable (and, generalized, is satisfied by v) — numpy, per clause."""
+    lits = np.asarray(lits)
+    used = lits != 0
+    var = np.where(used, np.abs(lits) - 1, 0)
+    val = (x[var] == (lits > 0)) & used
+    st = star[var] & used
+    blocked = np.zeros(n, bool)
+    for q in range(lits.shape[1]):
+        others = np.ones(lits.shape[1], bool)
+        others[q] = False
+        other_true = val[:, others].any(axis=1)
+        other_star = st[:, others].any(axis=1)
+        b = used[:, q] & ~other_true & ~other_star
+        if generalized:
+            b &= val[:, q]
+        np.logical_or.at(blocked, var[b, q], True)
+    return blocked
+
+
+@pytest.mark.parametrize("generalized", [True, False])
+def test_whitening_is_the_least_fixed_point(generalized):
+    """The oracle's one-at-a-time result is a fixed point (white = unblocked, frozen = blocked,
+    by an independent evaluator) and equals the parallel-round closure from no white variable."""
+    n = 400
+    lits = W.random_ksat(n, 4.2, 3, 12)
+    beta = W.beta_constant(n, 60, 4.0)
+    X = O.ksat_anneal(lits, n, beta, 0, 60, 2, replicas=6)["states"]
+    for x in X:
+        fr, cnt = O.ksat_whitening(lits, n, x, generalized)
+        star = fr == 0
+        assert cnt == int(fr.sum())
+        blocked = _blocking(lits, n, x, star, generalized)
+        assert np.array_equal(blocked, ~star)
+        s = np.zeros(n, bool)
+        while True:
+            s2 = s | ~_blocking(lits, n, x, s, generalized)
+            if np.array_equal(s2, s):
+                break
+            s = s2
+        assert np.array_equal(s, star)
+
+
+def test_whitening_reports_no_false_frozen_variables():
+    """On solutions of small satisfiable formulas, a variable the procedure calls frozen takes
+    the same value in every solution reachable from the given one by single flips through
+    solutions (its cluster), found by enumerating all 2^14 assignments."""
+    n = 14
+    seen_frozen = 0
+    for seed in range(6):
+        lits = small_cnf(n, 50, 3, seed=100 + seed)
+        X = all_states(n)
+        sol = X[energies_numpy(lits, X) == 0]
+        if len(sol) == 0:
+            continue
+        idx = {int(i): j for j, i in enumerate(_state_index(sol))}
+        for j0 in range(0, len(sol), max(1, len(sol) // 5)):
+            comp, todo = {j0}, [j0]
+            while todo:
+                j = todo.pop()
+                for v in range(n):
+                    y = sol[j].copy()
+                    y[v] ^= 1
+                    k = idx.get(int(_state_index(y[None])[0]))
+                    if k is not None and k not in comp:
+                        comp.add(k)
+                        todo.append(k)
+            cl = sol[sorted(comp)]
+            fr, _ = O.ksat_whitening(lits, n, sol[j0])
+            fr_std, _ = O.ksat_whitening(lits, n, sol[j0], generalized=False)
+            assert np.array_equal(fr, fr_std)  # no violated clause: both forms agree
+            for v in np.nonzero(fr)[0]:
+                assert np.all(cl[:, v] == sol[j0, v]), (seed, j0, v)
+            seen_frozen += int(fr.sum())
+    assert seen_frozen > 0
+
+
+def test_whitening_generalized_whitens_more_on_low_energy_states():
+    n = 300
+    lits = W.random_ksat(n, 9.6, 4, 5)
+    X = O.ksat_anneal(lits, n, W.beta_constant(n, 80, 3.0), 0, 80, 4, replicas=5)["states"]
+    assert energies_numpy(lits, X).min() > 0
+    for x in X:
+        g, cg = O.ksat_whitening(lits, n, x, True)
+        s, cs = O.ksat_whitening(lits, n, x, False)
+        assert np.all(g <= s) and cg <= cs
+    # a unit clause is the only satisfier of its variable: frozen; nothing else is
+    lits2 = np.array([[1, 0, 0], [2, 3, 0]], np.int32)
+    fr, c = O.ksat_whitening(lits2, 3, np.array([1, 1, 1], np.uint8))
+    assert fr.tolist() == [1, 0, 0] and c == 1
