@@ -507,6 +507,13 @@ def run_pt(args):
     betas, sigmas = ctx.adaptive_ladder(inst, 256, 3, 0.3, 1.1, 1.0, 48, 50, 100)
     ladder_s = time.time() - t
     ctx.close()
+    import oracle as O
+    t = time.time()
+    O.ksat_pt_anneal(lits, n, np.ones((n, 20), np.float32), ladder, 0, 20, per, 1, replicas=L)
+    cpu_s = time.time() - t
+    cpu = {"value": n * L * 20 / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"one ladder of {L} replicas x 20 sweeps, exchange every {per} "
+                     f"({cpu_s:.1f} s, single-threaded: the rounds couple the replicas)"}
     attempts = n * R * T
     bps = algorithmic_bytes_per_sweep(lits, n, R)
     peak, src = peaks()
@@ -528,7 +535,148 @@ def run_pt(args):
                                 "beta_last": float(betas[-1]), "sigma_last": float(sigmas[-1]),
                                 "config": "256 replicas, beta0 0.3, alpha 1.1, sigma_min 1.0, "
                                           "50 + 100 sweeps per level"},
-            "clocks": ck}
+            "clocks": ck, "cpu_baseline": cpu}
+
+
+def _timed_events(stream, fn, warmup, steps, flush=None):
+    """Mean CUDA-event time of fn(i) over `steps` calls after `warmup` calls; an optional L2
+    flush runs between calls, outside the events."""
+    import torch
+    tot = 0.0
+    for i in range(warmup + steps):
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn(i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            tot += a.elapsed_time(b)
+    return tot / steps
+
+
+def run_learning(args):
+    """Learning stage on random 4-SAT N=5,000, alpha=9.884 (M=49,420): loopy BP on the surrogate
+    Hamiltonians of 64 seeds at once (seeds = best states of a 200-sweep anneal at beta 3), lambda
+    continuation 0.4 -> 0.025, beta 1, tol 1e-8, at most 100 iterations per lambda; then backbone
+    growth from the correlations. Metric: message updates (edge x seed x iteration) per second."""
+    import torch
+    ctx, stream = _ctx_stream()
+    n, S = 5000, 64
+    lits = W.random_ksat(n, 9.884, 4, 2111)
+    inst = ctx.load_ksat(lits, n)
+    ctx.set_schedule(inst, W.beta_constant(n, 200, 3.0))
+    seeds = ctx.anneal(inst, S, 0, 200, 5)["best_states"]
+    lams = [0.4, 0.2, 0.1, 0.05, 0.025]
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    out = {}
+
+    def lbp(i):
+        out["r"] = ctx.cnf_lbp(inst, seeds, 1.0, lams, 1e-8, 100)
+
+    ms = _timed_events(stream, lbp, args.warmup, args.steps, flush)
+    r = out["r"]
+    edges = int((lits != 0).sum())
+    updates = edges * int(r["iters"].sum())
+    t_bb = _timed_events(stream, lambda i: ctx.cnf_backbone(inst, r["corr"], 1.0, 2.5, 2.0),
+                         1, 3)
+    lab, nc = ctx.cnf_backbone(inst, r["corr"], 1.0, 2.5, 2.0)
+    ctx.close()
+    import oracle as O
+    t = time.time()
+    ro = O.cnf_lbp(lits, n, seeds[0], 1.0, lams, 1e-8, 100)
+    cpu_s = time.time() - t
+    cpu = {"value": edges * int(ro["iters"].sum()) / cpu_s, "unit": "edge-seed updates/s",
+           "cores": 1, "kind": "oracle",
+           "sample": f"seed 0 alone, same lambdas ({int(ro['iters'].sum())} iterations, "
+                     f"{cpu_s:.1f} s)"}
+    bytes_per_update = 40  # u read + h write (variable pass), h read + u read/write (clause pass)
+    peak, src = peaks()
+    achieved = bytes_per_update * updates / (ms / 1e3) / 1e9
+    return {"metric": "LBP message updates/s", "value": updates / (ms / 1e3),
+            "unit": "edge-seed updates/s", "ms_per_step": ms, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic (seeded random 4-SAT; seeds from the engine's anneal)",
+            "config": {"workload": f"lbp_4sat_n{n}_m{lits.shape[0]}_S{S}_lambda5",
+                       "edges": edges, "iterations_total": int(r["iters"].sum()),
+                       "lambdas_converged_mean": float(r["n_done"].mean()),
+                       "l2": "flushed between steps (512 MB write); messages 4 x 101 MB > L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": src,
+                         "note": "40 B per edge-seed update (8 B u + 8 B h, then 8 B h + 16 B u); "
+                                 "includes one 4-byte readback per iteration"},
+            "backbone": {"ms": t_bb, "clusters_seed0": int(nc[0]),
+                         "backbone_vars_seed0": int((lab[0] >= 0).sum()),
+                         "thresholds": "seed 2.5, cutoff 2.0"},
+            "cpu_baseline": cpu}
+
+
+def run_moves(args):
+    """Held-unit (two-chain) sampling, the collective move and whitening on the bench instance
+    (4-SAT N=50,000, M=480,000, 1,024 replicas). Two-chain schedule: a seeded 20% backbone,
+    10 cycles of 20 hot (base 3.0 / heat 4) + 20 cold + 10 unlearning sweeps (500 sweeps). Metric:
+    attempts on the unheld variables per second; beside it the same 500 sweeps with nothing held,
+    one collective flip of the backbone (ms), and whitening of all replicas (ms)."""
+    import torch
+    ctx, stream = _ctx_stream()
+    wl = W.workload_ksat_large(n_steps=2)
+    lits, n, R = wl["lits"], wl["n_vars"], 1024
+    inst = ctx.load_ksat(lits, n)
+    bb = W.seeded_subset(n, 0.2, 77)
+    labels = np.where(bb, 0, -1).astype(np.int32)
+    cycles, th, tc, tu = 10, 20, 20, 10
+    T = cycles * (th + tc + tu)
+    ctx.set_schedule_backbone(inst, labels, cycles, th, tc, tu, 3.0, 4.0)
+    rs = ctx.replicas_create(inst, R, seed=1)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+
+    def held(i):
+        ctx.replicas_reset(rs, 10 + i)
+        ctx.replicas_run(rs, 0, T)
+
+    clocks = Clocks(0)
+    clocks.start()
+    ms = _timed_events(stream, held, args.warmup, args.steps, flush)
+    ck = clocks.stop()
+    nb = int(bb.sum())
+    attempts = R * cycles * (th * nb + tc * (n - nb) + tu * n)
+    ctx.set_schedule_factored(inst, np.full(T, 3.0, np.float32), np.ones(n, np.float32))
+    ms_plain = _timed_events(stream, held, 1, max(2, args.steps // 2), flush)
+    mask = bb.astype(np.uint8)
+    beta = np.full(R, 0.75, np.float32)
+    ms_flip = _timed_events(stream, lambda i: ctx.cluster_flip(rs, mask, beta, 1000 + i),
+                            2, 5, flush)
+    ms_white = _timed_events(stream, lambda i: ctx.whitening(rs), 1, 3, flush)
+    frozen = ctx.whitening(rs)
+    st = ctx.replicas_read(rs)
+    ctx.close()
+    import oracle as O
+    sched = O.backbone_schedule(labels, 3.0, 4.0, 1, th, tc, tu)[:, :th]
+    t = time.time()
+    O.ksat_anneal(lits, n, sched, 0, th, 1, replicas=16)
+    cpu_s = time.time() - t
+    t = time.time()
+    for r in range(4):
+        O.ksat_whitening(lits, n, st["states"][r])
+    cpu_w = (time.time() - t) / 4
+    cpu = {"value": 16 * th * nb / cpu_s, "unit": UNIT, "cores": min(16, os.cpu_count() or 1),
+           "kind": "oracle",
+           "sample": f"16 replicas x the {th} hot sweeps of the first cycle ({cpu_s:.1f} s, "
+                     f"includes the oracle's colouring); whitening {cpu_w * 1e3:.0f} ms per "
+                     f"replica single-threaded"}
+    return {"metric": "Metropolis attempts/s (two-chain held sampling)",
+            "value": attempts / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "u32 (bit-sliced 32 replicas/word)", "data": "synthetic (seeded random 4-SAT)",
+            "config": {"workload": f"twochain_4sat_n{n}_r{R}_bb20pct_{cycles}x({th}+{tc}+{tu})",
+                       "attempts_per_step": attempts, "sweeps": T,
+                       "l2": "flushed between steps (512 MB write)"},
+            "nothing_held": {"ms_per_step": ms_plain, "value": n * R * T / (ms_plain / 1e3)},
+            "cluster_flip": {"ms_per_move": ms_flip, "mask_vars": nb, "replicas": R},
+            "whitening": {"ms": ms_white, "frozen_mean": float(frozen.mean())},
+            "clocks": ck, "cpu_baseline": cpu}
 
 
 def run_serving(args):
@@ -651,7 +799,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--workload", default="ksat_large",
                     choices=["ksat_large", "ksat_small", "ksat_batch", "qap_batch", "serving",
-                             "pt"])
+                             "pt", "learning", "moves"])
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--qap-steps", type=int, default=50)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -672,7 +820,8 @@ def main():
         res = run_reference(args, world, rank)
     elif args.workload != "ksat_large":
         fn = {"ksat_small": run_ksat_small, "ksat_batch": run_ksat_batch,
-              "qap_batch": run_qap_batch, "serving": run_serving, "pt": run_pt}[args.workload]
+              "qap_batch": run_qap_batch, "serving": run_serving, "pt": run_pt,
+              "learning": run_learning, "moves": run_moves}[args.workload]
         res = fn(args) if rank == 0 else None
     else:
         res = run_ours(args, world, rank, local)
