@@ -71,6 +71,18 @@ __device__ __forceinline__ uint32_t lit_word(const uint32_t *xs, int l) {
   return xs[l >> 1] ^ (0u - (uint32_t)(l & 1));
 }
 
+// Adds the bit-sliced counter p into c (ripple carry).
+template <int NB>
+__device__ __forceinline__ void add_planes(uint32_t (&c)[NB], const uint32_t (&p)[NB]) {
+  uint32_t carry = 0u;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    const uint32_t a = c[j], b = p[j];
+    c[j] = a ^ b ^ carry;
+    carry = maj3b(a, b, carry);
+  }
+}
+
 // v = c0 + off is a variable of colour class c (starting at new id c0). With PT, replica j
 // of the word moves at min(2^32-1, (mult_s[j] * bq) >> 16) instead of bq.
 template <int KQ, bool PT>
@@ -151,14 +163,14 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
   for (int q = 0; q < 4; ++q) {
     const unsigned long long xm = transpose8(gather_bytes(s8, q));
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int g = 2 * q + h;
+    for (int hh = 0; hh < 2; ++hh) {
+      const int g = 2 * q + hh;
       int de[4];
       uint32_t th[4];
       bool need = false;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        de[j] = (int)(signed char)(unsigned char)(xm >> (8 * (4 * h + j)));
+        de[j] = (int)(signed char)(unsigned char)(xm >> (8 * (4 * hh + j)));
         th[j] = 0u;
         if (de[j] > 0) {
           uint32_t hi = bq_hi, lo = bq_lo;
@@ -193,6 +205,25 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
     }
   }
   return x ^ flip;
+}
+
+// A colour class [c0, c1) is shared out among the CS CTAs of a cluster by 32-variable groups,
+// round-robin: CTA `rank` takes groups rank, rank + CS, ... Variables are degree-descending
+// inside a class, so each CTA gets a like mix of long and short occurrence lists (contiguous
+// shares would give rank 0 all the longest lists and make every class wait for it).
+template <int CS>
+__device__ __forceinline__ int share_count(int c0, int c1, int rank) {
+  const int ng = (c1 - c0 + 31) >> 5;
+  const int mine = ng > rank ? (ng - rank + CS - 1) / CS : 0;
+  int cnt = mine * 32;
+  if (mine > 0 && rank + (mine - 1) * CS == ng - 1) cnt -= ng * 32 - (c1 - c0);  // last, partial
+  return cnt;
+}
+
+// Local index li (0 <= li < share_count) -> variable.
+template <int CS>
+__device__ __forceinline__ int share_var(int c0, int rank, int li) {
+  return c0 + 32 * (rank + CS * (li >> 5)) + (li & 31);
 }
 
 // Synchronises the CS CTAs of a cluster (or the CTA when CS = 1); cluster barriers are
@@ -267,9 +298,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
       for (int j = 0; j < kAccPlanes; ++j) acc[j] = 0u;
       for (int c = 0; c < B.n_colours; ++c) {
         const int c0 = __ldg(B.col_ptr + c), c1 = __ldg(B.col_ptr + c + 1);
-        const int part = ((c1 - c0 + CS - 1) / CS + 31) & ~31;  // whole 32-variable groups
-        const int v0 = c0 + rank * part, v1 = min(c1, v0 + part);
-        for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        // the class's 32-variable groups are dealt round-robin to the cluster's CTAs
+        const int cnt = share_count<CS>(c0, c1, rank);
+        for (int li = threadIdx.x; li < cnt; li += blockDim.x) {
+          const int v = share_var<CS>(c0, rank, li);
           const uint32_t xn = attempt_batch<KQ, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, v, t, acc);
           if (CS == 1) {
             xs[v] = xn;
@@ -351,17 +383,6 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 // acceptance of replica groups [t*8/TL, (t+1)*8/TL) (one Philox block per group of 4 replicas)
 // and the team ORs the flip bits. A colour class of a few hundred variables then costs the
 // latency of a TL-th of one attempt instead of a whole one.
-template <int NB>
-__device__ __forceinline__ void add_planes(uint32_t (&c)[NB], const uint32_t (&p)[NB]) {
-  uint32_t carry = 0u;
-#pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    const uint32_t a = c[j], b = p[j];
-    c[j] = a ^ b ^ carry;
-    carry = maj3b(a, b, carry);
-  }
-}
-
 template <int KQ, int TL, bool PT>
 __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint32_t *xs,
                                                  const uint32_t *tab_s, int tab_len,
@@ -533,6 +554,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
       for (int i = 0; i < 32 / TL; ++i) acc[i] = 0;
       for (int c = 0; c < B.n_colours; ++c) {
         const int c0 = __ldg(B.col_ptr + c), c1 = __ldg(B.col_ptr + c + 1);
+        // contiguous shares here (measured: round-robin groups are slower for the teams)
         const int part = ((c1 - c0 + CS - 1) / CS + 31) & ~31;
         const int v0 = c0 + rank * part, v1 = min(c1, v0 + part);
         // warp-uniform trip count: the warp's teams take consecutive variables each round
