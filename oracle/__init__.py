@@ -68,7 +68,7 @@ def _load():
                                                i32, u64, P, P, P, P, P, P, P]
             lib.orc_ksat_pt_anneal.restype = C.c_int
             lib.orc_ksat_cluster_flip.argtypes = [i32, i32, i32, P, i32, P, P, P, P, i32, P, P,
-                                                  u32, u64, P]
+                                                  u32, u64, P, P]
             lib.orc_ksat_cluster_flip.restype = C.c_int
             dbl = C.c_double
             lib.orc_cnf_lbp.argtypes = [i32, i32, i32, P, P, P, dbl, i32, P, dbl, i32, P, P, P, P,
@@ -229,11 +229,11 @@ def ksat_pt_anneal(lits, n_vars, beta, ladder, t0, t1, sweeps_per_round, seed, r
     return dict(states=out_s, energies=e, best_energies=be, best_states=out_b, slots=slots)
 
 
-def ksat_cluster_flip(lits, n_vars, chain, mask, beta, move_id, seed):
+def ksat_cluster_flip(lits, n_vars, chain, mask, beta, move_id, seed, replica_ids=None):
     """Collective move of every replica of `chain` (a dict as ksat_anneal returns: states,
     energies, best_states, best_energies): replica r proposes x xor mask_r (mask [1 or R, N] 0/1)
-    and accepts by the Metropolis rule at beta[r]. Returns a new dict of the same form plus
-    `accepted` uint8[R]."""
+    and accepts by the Metropolis rule at beta[r]. replica_ids: the id (Philox stream, mask row)
+    of each row, default 0..R-1. Returns a new dict of the same form plus `accepted` uint8[R]."""
     lits, m, k = _cnf(lits)
     st = np.array(chain["states"], dtype=np.uint8, order="C")
     bs = np.array(chain["best_states"], dtype=np.uint8, order="C")
@@ -243,9 +243,10 @@ def ksat_cluster_flip(lits, n_vars, chain, mask, beta, move_id, seed):
     mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1, n_vars)
     beta = np.ascontiguousarray(np.broadcast_to(np.asarray(beta, dtype=np.float32), (R,)))
     acc = np.zeros(R, dtype=np.uint8)
+    ids = None if replica_ids is None else np.ascontiguousarray(replica_ids, dtype=np.int32)
     rc = _load().orc_ksat_cluster_flip(n_vars, m, k, _p(lits), R, _p(st), _p(e), _p(bs), _p(be),
                                        mask.shape[0], _p(mask), _p(beta), int(move_id) & 0xFFFFFFFF,
-                                       int(seed) & (2**64 - 1), _p(acc))
+                                       int(seed) & (2**64 - 1), _p(acc), _p(ids))
     if rc != 0:
         raise ValueError("orc_ksat_cluster_flip rejected its arguments")
     return dict(states=st, energies=e, best_energies=be, best_states=bs, accepted=acc)

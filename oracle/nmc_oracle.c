@@ -760,26 +760,29 @@ int orc_qap_anneal(int32_t n, const int32_t *F, const int32_t *D, int32_t n_step
 /*
  * states: R*n uint8 in/out; energies, best_energies: R int64 in/out; best_states: R*n in/out.
  * mask: mask_rows*n uint8 (mask_rows 1: one mask for all replicas, or R). beta: R floats.
- * accepted: R uint8 out (nullable). Returns 0 or -1 on a bad argument.
+ * accepted: R uint8 out (nullable). rep_ids: the replica id of each row (its Philox stream and
+ * mask row; NULL = 0..R-1). Returns 0 or -1 on a bad argument.
  */
 int orc_ksat_cluster_flip(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, int32_t R,
                           uint8_t *states, int64_t *energies, uint8_t *best_states,
                           int64_t *best_energies, int32_t mask_rows, const uint8_t *mask,
-                          const float *beta, uint32_t move_id, uint64_t seed, uint8_t *accepted) {
+                          const float *beta, uint32_t move_id, uint64_t seed, uint8_t *accepted,
+                          const int32_t *rep_ids) {
   if (n <= 0 || m < 0 || kmax <= 0 || R <= 0 || (mask_rows != 1 && mask_rows != R)) return -1;
   orc_table tab;
   table_init(&tab);
   uint8_t *y = (uint8_t *)malloc((size_t)n);
   for (int32_t r = 0; r < R; ++r) {
+    const uint32_t id = rep_ids ? (uint32_t)rep_ids[r] : (uint32_t)r;
     uint8_t *x = states + (size_t)r * n;
-    const uint8_t *mr = mask + (size_t)(mask_rows == 1 ? 0 : r) * n;
+    const uint8_t *mr = mask + (size_t)(mask_rows == 1 ? 0 : id) * n;
     for (int32_t v = 0; v < n; ++v) y[v] = (uint8_t)(x[v] ^ (mr[v] & 1u));
     const int64_t e0 = orc_ksat_energy(n, m, kmax, lits, x);
     const int64_t e1 = orc_ksat_energy(n, m, kmax, lits, y);
     const int64_t d = e1 - e0;
     int acc = 1;
     if (d > 0) {
-      const uint32_t u = philox_word(move_id, 0u, (uint32_t)r >> 2, ORC_TAG_CLUSTER, seed, r & 3);
+      const uint32_t u = philox_word(move_id, 0u, id >> 2, ORC_TAG_CLUSTER, seed, (int)(id & 3u));
       acc = accept_uphill(&tab, orc_quantize_beta(beta[r]), d, u);
     }
     if (acc) {
