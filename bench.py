@@ -398,6 +398,8 @@ def run_ksat_batch(args):
         sets.append(rs)
         attempts += n * R * T
         per.append((rs, n * R * T))
+    # launch shapes tuned on 8 sweeps of this batch (outside the timed region; states restored)
+    shapes = ctx.batch_autotune(sets, 0, 8).tolist()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for i in range(args.warmup + args.steps):
         for j, rs in enumerate(sets):
@@ -422,7 +424,9 @@ def run_ksat_batch(args):
     return {"metric": "Metropolis attempts/s (batched, one launch)", "value": attempts / (ms / 1e3),
             "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
             "config": {"workload": f"ksat_batch_{n_inst}x_N1k-20k_R32-256_t{T}",
-                       "attempts_per_step": attempts},
+                       "attempts_per_step": attempts,
+                       "tuned_shapes": {"k<=4": shapes[0], "k<=8": shapes[1],
+                                        "fields": "CTAs per item, lanes, us per sweep"}},
             "plain_per_instance": {"value": plain, "unit": UNIT,
                                    "sample": f"{len(sample)} of the {n_inst} sets, one launch each"}}
 

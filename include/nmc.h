@@ -184,6 +184,20 @@ int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t
  */
 int nmc_batch_run_noalloc(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
                           const int32_t *t1);
+/*
+ * Autotuner of the batched sweep. Times every launch shape (1, 2, 4 or 8 CTAs per work item x
+ * 1, 4 or 8 lanes per variable) on sweeps [t0, t0 + sweeps) of the k-SAT replica sets rs[i]
+ * (the batch nmc_batch_run would run), separately for the two occurrence widths (k <= 4,
+ * k <= 8), and keeps the fastest on this context: later nmc_batch_run / nmc_replicas_run /
+ * replica-exchange launches whose work list has the same width, largest n_vars and number of
+ * work items (32-replica words) use it; the variables NMC_BATCH_CTAS / NMC_BATCH_LANES still
+ * take precedence. Every shape gives the same results bit for bit, and the sets' states, best
+ * states and energies are saved before the trials and restored after them, so the call leaves
+ * the sets as it found them. shapes_out (host, nullable): int32 [2][3] = (CTAs per item, lanes,
+ * microseconds per sweep) per width, zeros where the width has no items. Synchronises.
+ */
+int nmc_batch_autotune(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, int32_t t0,
+                       int32_t sweeps, int32_t *shapes_out);
 /* Batched QAP steps: runs steps t0[i]..t1[i]-1 of QAP replica sets rs[i] in one launch (one CTA
  * per block of 32 replicas), asynchronously; results as nmc_replicas_run on each set alone. */
 int nmc_qap_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,

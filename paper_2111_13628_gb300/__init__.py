@@ -60,7 +60,8 @@ SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_
            "nmc_server_last_error", "nmc_batch_run_noalloc", "nmc_qap_batch_run",
            "nmc_replicas_set_ladder", "nmc_replicas_run_pt", "nmc_replicas_read_slots",
            "nmc_adaptive_ladder", "nmc_replicas_cluster_flip", "nmc_cnf_lbp",
-           "nmc_cnf_backbone", "nmc_set_schedule_backbone", "nmc_replicas_whitening"]
+           "nmc_cnf_backbone", "nmc_set_schedule_backbone", "nmc_replicas_whitening",
+           "nmc_batch_autotune"]
 
 
 def library_path() -> str:
@@ -127,6 +128,7 @@ def load(build_if_missing: bool = True):
             "nmc_set_schedule_backbone": ([P, i32, P, i32, i32, i32, i32, C.c_float, C.c_float],
                                           C.c_int),
             "nmc_replicas_whitening": ([P, i32, i32, i32, P, P, P], C.c_int),
+            "nmc_batch_autotune": ([P, i32, P, i32, i32, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -293,6 +295,15 @@ class Context:
         t0 = np.ascontiguousarray(np.broadcast_to(t0, rs.shape), dtype=np.int32)
         t1 = np.ascontiguousarray(np.broadcast_to(t1, rs.shape), dtype=np.int32)
         self._check(self._lib.nmc_qap_batch_run(self._h, rs.size, _ptr(rs), _ptr(t0), _ptr(t1)))
+
+    def batch_autotune(self, rs, t0: int, sweeps: int):
+        """Times every batched-sweep shape on these sets and keeps the fastest for this context.
+        Returns int32 [2, 3]: (CTAs per item, lanes per variable, us per sweep) per width."""
+        rs = np.ascontiguousarray(np.atleast_1d(rs), dtype=np.int32)
+        out = np.zeros((2, 3), np.int32)
+        self._check(self._lib.nmc_batch_autotune(self._h, rs.size, _ptr(rs), int(t0), int(sweeps),
+                                                 _ptr(out)))
+        return out
 
     def batch_max_vars(self) -> int:
         return int(self._lib.nmc_batch_max_vars(self._h))

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "nmc.h"
@@ -81,6 +82,8 @@ struct nmc_ctx {
   int32_t *next_item = nullptr;  // two work counters (one per occurrence width)
   QapArgs *qitems = nullptr;     // batched QAP work list (grown on demand)
   size_t qitems_cap = 0;
+  // tuned batched-sweep shapes: (occurrence width, largest n, work items) -> (cs, lanes)
+  std::map<std::tuple<int, int, int>, std::pair<int, int>> tune;
 };
 
 namespace {
@@ -305,12 +308,19 @@ int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t
     plan->cnt[q] = static_cast<int>(idx.size());
     for (size_t k : idx) plan->items.push_back(by_kq[q][k]);
     // CTAs per item: spread few items over the SMs (word vectors replicated per cluster)
-    int cs = 1;
-    if (const char *env = getenv("NMC_BATCH_CTAS")) cs = atoi(env);
-    else
+    int cs = 1, lanes = 0;
+    const auto tuned = ctx->tune.find(std::make_tuple(q + 1, plan->max_n[q], plan->cnt[q]));
+    if (const char *env = getenv("NMC_BATCH_CTAS")) {
+      cs = atoi(env);
+    } else if (tuned != ctx->tune.end()) {
+      cs = tuned->second.first;
+      lanes = tuned->second.second;
+    } else {
       while (cs < 8 && static_cast<long long>(plan->cnt[q]) * cs * 2 <= sms) cs *= 2;
+    }
     if (cs != 1 && cs != 2 && cs != 4 && cs != 8) cs = 1;
     plan->cs[q] = cs;
+    plan->lanes[q] = lanes;
   }
   plan->device = ctx->device;
   plan->stream = ctx->stream;
@@ -340,7 +350,8 @@ int reserve_items(nmc_ctx *ctx, size_t total) {
 // Uploads a work list and launches it: items [off[q], off[q] + cnt[q]) have occurrence width
 // q + 1. pt selects the kernels with temperature multipliers and energy statistics.
 int launch_items(nmc_ctx *ctx, const std::vector<BatchItem> &items, const size_t off[2],
-                 const int cnt[2], const int max_n[2], const int cs[2], bool pt) {
+                 const int cnt[2], const int max_n[2], const int cs[2], bool pt,
+                 const int lanes[2]) {
   if (items.empty()) return NMC_OK;
   const int rc = reserve_items(ctx, items.size());
   if (rc != NMC_OK) return rc;
@@ -351,7 +362,7 @@ int launch_items(nmc_ctx *ctx, const std::vector<BatchItem> &items, const size_t
   for (int q = 0; q < 2; ++q) {
     if (!cnt[q]) continue;
     NMC_CUDA(ksat_batch(ctx->items + off[q], cnt[q], q + 1, cs[q], max_n[q], ctx->next_item + q,
-                        ctx->tab, ctx->tab_len, ctx->device, ctx->stream, pt),
+                        ctx->tab, ctx->tab_len, ctx->device, ctx->stream, pt, lanes[q]),
              "launch batched sweep");
   }
   return NMC_OK;
@@ -381,6 +392,10 @@ BatchItem ksat_item(const Instance &I, const ReplicaSet &S, int32_t w, int32_t t
   return B;
 }
 
+// CTAs per work item and lanes per variable for a launch of `cnt` items of one instance (a
+// tuned shape when the context has one, else as batch_plan chooses).
+void tuned_shape(nmc_ctx *ctx, int kq, int max_n, int cnt, int *cs, int *lanes);
+
 // CTAs per work item for a launch of `cnt` items (as batch_plan chooses).
 int ctas_per_item(nmc_ctx *ctx, long long cnt) {
   int sms = 0;
@@ -394,6 +409,17 @@ int ctas_per_item(nmc_ctx *ctx, long long cnt) {
     while (cs < 8 && cnt * cs * 2 <= sms) cs *= 2;
   if (cs != 1 && cs != 2 && cs != 4 && cs != 8) cs = 1;
   return cs;
+}
+
+void tuned_shape(nmc_ctx *ctx, int kq, int max_n, int cnt, int *cs, int *lanes) {
+  *lanes = 0;
+  const auto t = ctx->tune.find(std::make_tuple(kq, max_n, cnt));
+  if (!getenv("NMC_BATCH_CTAS") && t != ctx->tune.end()) {
+    *cs = t->second.first;
+    *lanes = t->second.second;
+    return;
+  }
+  *cs = ctas_per_item(ctx, cnt);
 }
 
 // The checks every batched-kernel path makes on a k-SAT instance.
@@ -1201,7 +1227,7 @@ int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t
   BatchPlan plan;
   const int rc = batch_plan(ctx, n_sets, rs, t0, t1, &plan);
   if (rc != NMC_OK) return rc;
-  return launch_items(ctx, plan.items, plan.off, plan.cnt, plan.max_n, plan.cs, false);
+  return launch_items(ctx, plan.items, plan.off, plan.cnt, plan.max_n, plan.cs, false, plan.lanes);
 }
 
 int nmc_replicas_set_ladder(nmc_ctx *ctx, int32_t rs, int32_t n_temps, const float *ladder,
@@ -1277,7 +1303,8 @@ int nmc_replicas_run_pt(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1,
   DeviceGuard dg(ctx->device);
   const int32_t W = S->ks.W, L = S->pt_L, G = S->R / L, per = sweeps_per_round;
   const int kq = I->ks.kq;
-  const int cs = ctas_per_item(ctx, W);
+  int cs = 1, lanes = 0;
+  tuned_shape(ctx, kq, I->ks.n, W, &cs, &lanes);
   // segments end at t1 or after sweep t with (t+1) % per == 0, where an exchange round follows;
   // their work items are uploaded in chunks
   const int64_t max_chunk_items = std::max<int64_t>(W, 1 << 18);
@@ -1304,7 +1331,7 @@ int nmc_replicas_run_pt(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1,
              "upload work list");
     for (size_t i = 0; i < seg.size(); ++i) {
       NMC_CUDA(ksat_batch(ctx->items + i * W, W, kq, cs, I->ks.n, ctx->next_item, ctx->tab,
-                          ctx->tab_len, ctx->device, ctx->stream, true),
+                          ctx->tab_len, ctx->device, ctx->stream, true, lanes),
                "launch sweeps");
       const int32_t te = seg[i].second;
       if (te % per == 0)
@@ -1429,6 +1456,108 @@ struct DevScratch {
 }  // namespace
 
 extern "C" {
+
+int nmc_batch_autotune(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, int32_t t0,
+                       int32_t sweeps, int32_t *shapes_out) {
+  if (!ctx) return NMC_EINVAL;
+  if (sweeps < 1 || t0 < 0) return fail(ctx, NMC_EINVAL, "need t0 >= 0 and sweeps >= 1");
+  DeviceGuard g(ctx->device);
+  std::vector<int32_t> a(n_sets > 0 ? n_sets : 1, t0), b(n_sets > 0 ? n_sets : 1, t0 + sweeps);
+  BatchPlan plan;
+  int rc = batch_plan(ctx, n_sets, rs, a.data(), b.data(), &plan);
+  if (rc != NMC_OK) return rc;
+  if (shapes_out) std::fill(shapes_out, shapes_out + 6, 0);
+  if (plan.items.empty()) return NMC_OK;
+  // snapshot of every set's state, restored before each trial and at the end
+  std::vector<std::pair<void *, size_t>> parts;
+  for (int32_t i = 0; i < n_sets; ++i) {
+    ReplicaSet *S = find_set(ctx, rs[i]);
+    Instance *I = find_inst(ctx, S->inst);
+    const size_t W = S->ks.W, n = I->ks.n;
+    parts.push_back({S->ks.S, sizeof(uint32_t) * (2 * n + 2) * W});
+    parts.push_back({S->ks.best, sizeof(uint32_t) * n * W});
+    parts.push_back({S->ks.energy, sizeof(int32_t) * 32 * W});
+    parts.push_back({S->ks.best_energy, sizeof(int32_t) * 32 * W});
+  }
+  size_t total = 0;
+  for (auto &p : parts) total += (p.second + 255) & ~static_cast<size_t>(255);
+  DevScratch d;
+  d.st = ctx->stream;
+  char *snap = nullptr;
+  NMC_CUDA(d.get(&snap, total), "allocate tuning snapshot");
+  auto copy_all = [&](bool save) -> cudaError_t {
+    size_t off = 0;
+    for (auto &p : parts) {
+      char *s = snap + off;
+      const cudaError_t e = save ? cudaMemcpyAsync(s, p.first, p.second, cudaMemcpyDeviceToDevice, ctx->stream)
+                                 : cudaMemcpyAsync(p.first, s, p.second, cudaMemcpyDeviceToDevice, ctx->stream);
+      if (e != cudaSuccess) return e;
+      off += (p.second + 255) & ~static_cast<size_t>(255);
+    }
+    return cudaSuccess;
+  };
+  NMC_CUDA(copy_all(true), "snapshot replica sets");
+  rc = reserve_items(ctx, plan.items.size());
+  if (rc != NMC_OK) return rc;
+  NMC_CUDA(cudaMemcpyAsync(ctx->items, plan.items.data(), sizeof(BatchItem) * plan.items.size(),
+                           cudaMemcpyHostToDevice, ctx->stream),
+           "upload batch work list");
+  cudaEvent_t ev0, ev1;
+  NMC_CUDA(cudaEventCreate(&ev0), "create event");
+  if (cudaEventCreate(&ev1) != cudaSuccess) {
+    cudaEventDestroy(ev0);
+    return cuda_fail(ctx, cudaErrorUnknown, "create event");
+  }
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+    if (!plan.cnt[q]) continue;
+    float best_ms = 1e30f;
+    int best_cs = plan.cs[q], best_lanes = 0;
+    for (int cs : {1, 2, 4, 8}) {
+      for (int lanes : {1, 4, 8}) {
+        float ms = 0.0f;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {  // the first run loads and sizes the kernel
+          if ((e = copy_all(false)) != cudaSuccess) break;
+          if ((e = cudaEventRecord(ev0, ctx->stream)) != cudaSuccess) break;
+          const cudaError_t le = ksat_batch(ctx->items + plan.off[q], plan.cnt[q], q + 1, cs,
+                                            plan.max_n[q], ctx->next_item + q, ctx->tab,
+                                            ctx->tab_len, ctx->device, ctx->stream, false, lanes);
+          if (le != cudaSuccess) {  // a shape this device cannot launch: skip it
+            cudaGetLastError();
+            ok = false;
+            break;
+          }
+          if ((e = cudaEventRecord(ev1, ctx->stream)) != cudaSuccess ||
+              (e = cudaEventSynchronize(ev1)) != cudaSuccess ||
+              (e = cudaEventElapsedTime(&ms, ev0, ev1)) != cudaSuccess)
+            break;
+        }
+        if (e != cudaSuccess) break;
+        if (ok && ms < best_ms) {
+          best_ms = ms;
+          best_cs = cs;
+          best_lanes = lanes;
+        }
+      }
+      if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess && best_ms < 1e30f) {
+      ctx->tune[std::make_tuple(q + 1, plan.max_n[q], plan.cnt[q])] = {best_cs, best_lanes};
+      if (shapes_out) {
+        shapes_out[3 * q] = best_cs;
+        shapes_out[3 * q + 1] = best_lanes;
+        shapes_out[3 * q + 2] = static_cast<int32_t>(best_ms * 1000.0f / sweeps);
+      }
+    }
+  }
+  if (e == cudaSuccess) e = copy_all(false);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+  return NMC_OK;
+}
 
 int nmc_cnf_lbp(nmc_ctx *ctx, int32_t inst, int32_t n_seeds, const uint8_t *x_star,
                 const double *eps, double beta, int32_t n_lambda, const double *lambdas,
@@ -1700,16 +1829,16 @@ int nmc_adaptive_ladder(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t s
     }
     const int q = I->ks.kq == 1 ? 0 : 1;
     size_t off[2] = {0, 0};
-    int cnt[2] = {0, 0}, max_n[2] = {0, 0}, cs[2] = {1, 1};
+    int cnt[2] = {0, 0}, max_n[2] = {0, 0}, cs[2] = {1, 1}, lanes[2] = {0, 0};
     cnt[q] = W;
     max_n[q] = n;
-    cs[q] = ctas_per_item(ctx, W);
+    tuned_shape(ctx, q + 1, n, W, &cs[q], &lanes[q]);
     if ((e = fill_schedule(bq, static_cast<size_t>(n) * T, beta, ctx->flag, ctx->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(stats, 0, sizeof(long long) * 64 * W, ctx->stream)) != cudaSuccess) {
       rc = cuda_fail(ctx, e, "prepare ladder level");
       break;
     }
-    rc = launch_items(ctx, items, off, cnt, max_n, cs, true);
+    rc = launch_items(ctx, items, off, cnt, max_n, cs, true, lanes);
     if (rc != NMC_OK) break;
     double out[2] = {0.0, 0.0};
     if ((e = ladder_step(stats, S->R, W, static_cast<long long>(S->R) * sweeps_meas, beta, alpha,

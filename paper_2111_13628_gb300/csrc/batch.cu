@@ -698,11 +698,12 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
 
 // Lanes per variable of the batched kernel: 1 (one thread per variable) or a team of 4 or 8.
 // Few variables per CTA per colour class favour teams (latency), many favour single threads.
-int batch_lanes(int cs, int max_n) {
+int batch_lanes(int cs, int max_n, int want) {
   if (const char *env = getenv("NMC_BATCH_LANES")) {
     const int l = atoi(env);
     if (l == 1 || l == 4 || l == 8) return l;
   }
+  if (want == 1 || want == 4 || want == 8) return want;  // a tuned shape
   // variables of one colour class per CTA, taking ~32 classes. Measured on 4-SAT (alpha ~9.9,
   // 640 threads): teams of 8 lanes win up to ~24 variables per CTA and class, teams of 4 up to
   // ~100 (5,000 variables over 4-CTA clusters: 151 us per sweep vs 160 with 8 lanes and 227
@@ -715,15 +716,15 @@ int batch_lanes(int cs, int max_n) {
 
 template <int KQ, int CS>
 cudaError_t dispatch_lanes(const BatchItem *items, int n_items, int *next_item, const uint32_t *tab,
-                           int tab_len, int max_n, int device, cudaStream_t st, bool pt) {
+                           int tab_len, int max_n, int device, cudaStream_t st, bool pt, int lanes) {
   if (pt) {
-    switch (batch_lanes(CS, max_n)) {
+    switch (batch_lanes(CS, max_n, lanes)) {
       case 4: return launch_batch<KQ, CS, 4, true>(items, n_items, next_item, tab, tab_len, max_n, device, st);
       case 8: return launch_batch<KQ, CS, 8, true>(items, n_items, next_item, tab, tab_len, max_n, device, st);
       default: return launch_batch<KQ, CS, 1, true>(items, n_items, next_item, tab, tab_len, max_n, device, st);
     }
   }
-  switch (batch_lanes(CS, max_n)) {
+  switch (batch_lanes(CS, max_n, lanes)) {
     case 4: return launch_batch<KQ, CS, 4>(items, n_items, next_item, tab, tab_len, max_n, device, st);
     case 8: return launch_batch<KQ, CS, 8>(items, n_items, next_item, tab, tab_len, max_n, device, st);
     default: return launch_batch<KQ, CS, 1>(items, n_items, next_item, tab, tab_len, max_n, device, st);
@@ -733,12 +734,12 @@ cudaError_t dispatch_lanes(const BatchItem *items, int n_items, int *next_item, 
 template <int KQ>
 cudaError_t dispatch_batch(int cs, const BatchItem *items, int n_items, int *next_item,
                            const uint32_t *tab, int tab_len, int max_n, int device, cudaStream_t st,
-                           bool pt) {
+                           bool pt, int lanes) {
   switch (cs) {
-    case 8: return dispatch_lanes<KQ, 8>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt);
-    case 4: return dispatch_lanes<KQ, 4>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt);
-    case 2: return dispatch_lanes<KQ, 2>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt);
-    default: return dispatch_lanes<KQ, 1>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt);
+    case 8: return dispatch_lanes<KQ, 8>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt, lanes);
+    case 4: return dispatch_lanes<KQ, 4>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt, lanes);
+    case 2: return dispatch_lanes<KQ, 2>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt, lanes);
+    default: return dispatch_lanes<KQ, 1>(items, n_items, next_item, tab, tab_len, max_n, device, st, pt, lanes);
   }
 }
 
@@ -812,7 +813,8 @@ extern "C" int nmc_batch_run_noalloc(nmc_ctx *ctx, int32_t n_sets, const int32_t
     for (int q = 0; q < 2 && e == cudaSuccess; ++q)
       if (plan.cnt[q] > 0)  // the launcher clears counters[q] on the stream before the kernel
         e = ksat_batch(items + plan.off[q], plan.cnt[q], q + 1, plan.cs[q], plan.max_n[q],
-                       counters + q, plan.tab, plan.tab_len, plan.device, plan.stream);
+                       counters + q, plan.tab, plan.tab_len, plan.device, plan.stream, false,
+                       plan.lanes[q]);
   }
   if (prev >= 0) cudaSetDevice(prev);
   if (rc != NMC_OK)
@@ -837,10 +839,10 @@ size_t batch_max_vars(int tab_len, int device) {
 
 cudaError_t ksat_batch(const BatchItem *items_dev, int n_items, int kq, int cs, int max_n,
                        int *next_item, const uint32_t *tab, int tab_len, int device,
-                       cudaStream_t st, bool pt) {
+                       cudaStream_t st, bool pt, int lanes) {
   if (n_items <= 0) return cudaSuccess;
-  if (kq == 1) return dispatch_batch<1>(cs, items_dev, n_items, next_item, tab, tab_len, max_n, device, st, pt);
-  return dispatch_batch<2>(cs, items_dev, n_items, next_item, tab, tab_len, max_n, device, st, pt);
+  if (kq == 1) return dispatch_batch<1>(cs, items_dev, n_items, next_item, tab, tab_len, max_n, device, st, pt, lanes);
+  return dispatch_batch<2>(cs, items_dev, n_items, next_item, tab, tab_len, max_n, device, st, pt, lanes);
 }
 
 }  // namespace nmc

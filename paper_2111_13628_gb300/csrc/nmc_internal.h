@@ -130,10 +130,11 @@ cudaError_t quantize_schedule(const float *beta, int32_t n_units, int32_t n_step
 size_t batch_max_vars(int tab_len, int device);
 // Runs n_items items (all of one occurrence width kq) in one launch with cs CTAs (1, 2, 4, 8)
 // per item; next_item is a device int. With pt, every item carries temperature multipliers
-// (mult) and may carry energy statistics.
+// (mult) and may carry energy statistics. lanes: lanes per variable (1, 4, 8; 0 = the built-in
+// choice from cs and max_n).
 cudaError_t ksat_batch(const BatchItem *items_dev, int n_items, int kq, int cs, int max_n,
                        int *next_item, const uint32_t *tab, int tab_len, int device,
-                       cudaStream_t st, bool pt = false);
+                       cudaStream_t st, bool pt = false, int lanes = 0);
 
 // A validated batched launch, ready to be placed into device memory: the work items in launch
 // order (occurrence width 1 first, then 2), with their counts, shapes and the context's
@@ -144,6 +145,7 @@ struct BatchPlan {
   int cnt[2];
   int max_n[2];
   int cs[2];
+  int lanes[2];  // 0 = built-in choice
   int device;
   cudaStream_t stream;
   const uint32_t *tab;
