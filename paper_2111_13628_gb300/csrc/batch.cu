@@ -462,6 +462,9 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
   const uint32_t vo = active ? (uint32_t)__ldg(B.orig + v) : 0u;
   const uint32_t bq_hi = bqv >> 8, bq_lo = bqv & 255u;
   constexpr int GPL = 8 / TL;  // Philox groups per lane
+  // the lane's replicas lie in one block of 8: one 8x8 transpose of the 8 planes of D gives
+  // their signed bytes
+  const unsigned long long xm = transpose8(gather_bytes(d, (tl * GPL) >> 1));
   uint32_t flip = 0u;
 #pragma unroll
   for (int gi = 0; gi < GPL; ++gi) {
@@ -472,10 +475,7 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int r = 4 * g + j;
-      int val = 0;
-#pragma unroll
-      for (int k = 0; k < NB; ++k) val |= (int)((d[k] >> r) & 1u) << k;
-      val -= (int)((d[NB] >> r) & 1u) << NB;
+      const int val = (int)(signed char)(unsigned char)(xm >> (8 * (r & 7)));
       de[j] = val;
       th[j] = 0u;
       if (val > 0) {
