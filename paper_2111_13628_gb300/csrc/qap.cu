@@ -139,10 +139,13 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
           bqs = (uint32_t)(((unsigned long long)br + bs) >> 1);
         }
         const int cnt = (n - a0) < 32 ? (n - a0) : 32;
+        // r, s (< 256 each) and the held flag of every lane's attempt in one word: one
+        // broadcast per attempt
+        const int packed = fr | (fs << 9) | (frz << 18);
         for (int j = 0; j < cnt; ++j) {
-          if (__shfl_sync(0xFFFFFFFFu, frz, j)) continue;  // uniform over the warp
-          const int rr = __shfl_sync(0xFFFFFFFFu, fr, j);
-          const int ss = __shfl_sync(0xFFFFFFFFu, fs, j);
+          const int pj = __shfl_sync(0xFFFFFFFFu, packed, j);
+          if (pj >> 18) continue;  // a held facility (uniform over the warp)
+          const int rr = pj & 511, ss = (pj >> 9) & 511;
           const int pr = __shfl_sync(0xFFFFFFFFu, pick<NPL>(p, rr >> 5), rr & 31);
           const int ps = __shfl_sync(0xFFFFFFFFu, pick<NPL>(p, ss >> 5), ss & 31);
           const uint8_t *Fr = Fs + rr * LDF, *Fsr = Fs + ss * LDF;
@@ -156,8 +159,7 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
             const int pk = p[i];
             acc += ((int)Fr[k] - (int)Fsr[k]) * ((int)Dsr[pk] - (int)Dr[pk]);
           }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+          acc = __reduce_add_sync(0xFFFFFFFFu, acc);  // |partial sums| < 2^24: exact in int
           acc += 2 * (int)Fr[ss] * (int)Dr[ps];
           const long long d = 2LL * acc;
           bool ok = d <= 0;
