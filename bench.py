@@ -498,9 +498,9 @@ def run_pt(args):
         ctx.replicas_reset(rs, 100 + i)
         ctx.run_pt(rs, 0, T, per)
 
-    def plain_step(i):
+    def plain_step(i):  # the same ladder temperatures, no exchange round (one launch)
         ctx.replicas_reset(rs, 100 + i)
-        ctx.replicas_run(rs, 0, T)
+        ctx.run_pt(rs, 0, T, T + 1)
 
     clocks = Clocks(0)
     clocks.start()

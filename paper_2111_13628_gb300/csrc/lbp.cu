@@ -67,7 +67,7 @@ __global__ void lbp_clause_kernel(const int32_t *__restrict__ clits, int32_t m, 
       const long long e = a * kmax + q;
       f[q] = 1.0;
       if (clits[e] < 2 * n) {
-        f[q] = (1.0 - tanh(h[e * S + s])) / 2.0;
+        f[q] = 1.0 / (1.0 + exp(2.0 * h[e * S + s]));  // (1 - tanh h) / 2, one exp
         ++k;
       }
     }

@@ -2,7 +2,8 @@
 the CPU oracle, through the C ABI.
 
 LBP runs in double precision on both sides. The GPU forms each cavity field by subtracting the
-edge's own message from the variable's total field and uses CUDA's tanh / log1p, the oracle
+edge's own message from the variable's total field and uses CUDA's exp / log1p (the clause
+pass forms (1 - tanh h)/2 as 1/(1 + e^{2h})), the oracle
 sums the other clauses directly with the host libm: each step differs by a few units in the
 last place (about 1e-16 relative), and in the contracting regime the fixed-point map shrinks
 such differences instead of growing them, so 1e-9 absolute on marginals, correlations and
