@@ -61,16 +61,32 @@ __global__ void white_round_kernel(const int4 *__restrict__ occ, const int32_t *
   }
 }
 
-// frozen count of replica 32w + j: variables whose white bit j stays clear.
+// frozen count of replica 32w + j: variables whose white bit j stays clear. A warp takes a
+// (32-variable group, word) pair at a time: lane l loads variable 32g + l's frozen bits, and one
+// ballot per replica bit counts them; lane j keeps replica j's sum. count must start at zero.
 __global__ void white_count_kernel(const uint32_t *__restrict__ star, int32_t n, int32_t R, int32_t W,
                                    int32_t *count) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  const int w = r >> 5;
-  const uint32_t bit = 1u << (r & 31);
-  int c = 0;
-  for (int v = 0; v < n; ++v) c += (star[(size_t)v * W + w] & bit) ? 0 : 1;
-  count[r] = c;
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long groups = (n + 31) / 32;
+  int mine = 0, w_cur = -1;
+  for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < groups * W; i += warps) {
+    const int w = (int)(i % W);
+    const long long g = i / W;
+    if (w != w_cur) {  // flush the running sum when the word changes (warp-uniform)
+      if (w_cur >= 0 && 32 * w_cur + lane < R && mine) atomicAdd(&count[32 * w_cur + lane], mine);
+      mine = 0;
+      w_cur = w;
+    }
+    const long long v = 32 * g + lane;
+    const uint32_t x = v < n ? ~star[(size_t)v * W + w] : 0u;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int c = __popc(__ballot_sync(0xFFFFFFFFu, (x >> r) & 1u));
+      if (lane == r) mine += c;
+    }
+  }
+  if (w_cur >= 0 && 32 * w_cur + lane < R && mine) atomicAdd(&count[32 * w_cur + lane], mine);
 }
 
 // frozen[r][orig v] = 1 - white bit.
@@ -131,7 +147,9 @@ int whitening_run(const KsatDevice &I, const uint32_t *X, int32_t xrows2, int32_
     if (!ch) break;
   }
   *rounds = r + 1;
-  white_count_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(a, n, R, W, count);
+  if ((e = cudaMemsetAsync(count, 0, sizeof(int32_t) * R, st)) != cudaSuccess) return (int)e;
+  white_count_kernel<<<white_blocks((long long)(n + 31) / 32 * W * 32), kWhiteBlock, 0, st>>>(
+      a, n, R, W, count);
   if (frozen)
     white_unpack_kernel<<<white_blocks((long long)n * R), kWhiteBlock, 0, st>>>(a, I.orig, n, R, W, frozen);
   return (int)cudaGetLastError();
