@@ -216,7 +216,8 @@ int32_t nmc_batch_max_vars(nmc_ctx *ctx);
  * within its ladder, each ladder's slots a permutation of 0..n_temps-1; NULL puts replica
  * g*n_temps + i at slot i. A replica at slot k moves at min(2^32-1, (lq[k] bq_v[t]) >> 16)
  * instead of the schedule's bq_v[t]: the schedule gives the spatial profile, the ladder the
- * temperature. Replaces an earlier ladder; reset and restore leave the ladder and slots alone.
+ * temperature. Replaces an earlier ladder; reset and restore leave the ladder and slots alone,
+ * and nmc_replicas_run / nmc_batch_run ignore it (they sweep at the schedule's beta).
  * Needs an instance nmc_batch_run accepts (NMC_EINVAL otherwise).
  */
 int nmc_replicas_set_ladder(nmc_ctx *ctx, int32_t rs, int32_t n_temps, const float *ladder,
