@@ -209,16 +209,18 @@ int32_t nmc_batch_max_vars(nmc_ctx *ctx);
  * Replica exchange (parallel tempering, App. "Adaptive Parallel Tempering": replicas at
  * adjacent temperatures exchange with probability min{1, exp[(beta_i - beta_j)(E_i - E_j)]}).
  *
- * nmc_replicas_set_ladder attaches a temperature ladder to a k-SAT replica set whose R is a
+ * nmc_replicas_set_ladder attaches a temperature ladder to a replica set whose R is a
  * multiple of n_temps: the set becomes G = R / n_temps independent ladders, replica g*n_temps
  * + i in ladder g. ladder: n_temps floats (host), each finite and in [0, 65535], quantised to
  * Q16 like the schedule (lq[k]). slots (host, nullable): R int32, the slot of every replica
  * within its ladder, each ladder's slots a permutation of 0..n_temps-1; NULL puts replica
  * g*n_temps + i at slot i. A replica at slot k moves at min(2^32-1, (lq[k] bq_v[t]) >> 16)
- * instead of the schedule's bq_v[t]: the schedule gives the spatial profile, the ladder the
- * temperature. Replaces an earlier ladder; reset and restore leave the ladder and slots alone,
- * and nmc_replicas_run / nmc_batch_run ignore it (they sweep at the schedule's beta).
- * Needs an instance nmc_batch_run accepts (NMC_EINVAL otherwise).
+ * instead of the schedule's bq_v[t] (QAP: of the swap's pair temperature
+ * (bq_r[t] + bq_s[t]) >> 1): the schedule gives the spatial profile, the ladder the
+ * temperature. Works on k-SAT and QAP sets (the adaptive ladder below is k-SAT only).
+ * Replaces an earlier ladder; reset and restore leave the ladder and slots alone, and
+ * nmc_replicas_run / nmc_batch_run ignore it (they sweep at the schedule's beta).
+ * A k-SAT instance must be one nmc_batch_run accepts (NMC_EINVAL otherwise).
  */
 int nmc_replicas_set_ladder(nmc_ctx *ctx, int32_t rs, int32_t n_temps, const float *ladder,
                             const int32_t *slots);
@@ -228,7 +230,8 @@ int nmc_replicas_set_ladder(nmc_ctx *ctx, int32_t rs, int32_t n_temps, const flo
  * q = (t+1)/sweeps_per_round - 1 tries the slot pairs (k, k+1), k = q mod 2, k+2, ..., of
  * every ladder g; replicas a (at k) and b (at k+1) exchange slots when
  * d = (lq[k] - lq[k+1]) (E_a - E_b) >= 0, else when ((-d) >> 8) < L and u < Tab[(-d) >> 8],
- * u = word 0 of the Philox block for counter (k, q, g, 0x50545357) under the set's seed.
+ * u = word 0 of the Philox block for counter (k, q, g, 0x50545357) under the set's seed (d is
+ * formed exactly: QAP costs reach 2^33). For QAP sets a "sweep" is a step of n swap attempts.
  * Rounds are absolute like t, so [t0, t1) then [t1, t2) equals [t0, t2).
  */
 int nmc_replicas_run_pt(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1,

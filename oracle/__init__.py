@@ -78,6 +78,9 @@ def _load():
             lib.orc_cnf_backbone.restype = i32
             lib.orc_ksat_whitening.argtypes = [i32, i32, i32, P, P, i32, P]
             lib.orc_ksat_whitening.restype = i32
+            lib.orc_qap_pt_anneal.argtypes = [i32, P, P, i32, P, i32, i32, P, P, i32, i32, i32, u64,
+                                              P, P, P, P, P, P, P]
+            lib.orc_qap_pt_anneal.restype = C.c_int
             lib.orc_qap_cost.argtypes = [i32, P, P, P]
             lib.orc_qap_cost.restype = i64
             lib.orc_qap_swap_delta.argtypes = [i32, P, P, P, i32, i32]
@@ -395,3 +398,32 @@ def qap_anneal(F, D, beta, t0, t1, seed, replicas=None, replica_ids=None, init=N
     if rc != 0:
         raise ValueError("orc_qap_anneal rejected its arguments")
     return dict(perms=out_p, energies=e, best_energies=be, best_perms=out_b)
+
+
+def qap_pt_anneal(F, D, beta, ladder, t0, t1, sweeps_per_round, seed, replicas=None, slots=None,
+                  init=None, init_best=None, init_best_energy=None):
+    """Replica exchange for the QAP swap chain (see ksat_pt_anneal). Returns dict(perms,
+    energies, best_energies, best_perms, slots)."""
+    F = _c(F, np.int32)
+    D = _c(D, np.int32)
+    n = F.shape[0]
+    beta = np.ascontiguousarray(beta, dtype=np.float32)
+    ladder = np.ascontiguousarray(ladder, dtype=np.float32)
+    L = ladder.shape[0]
+    R = L if replicas is None else int(replicas)
+    slots = (np.arange(R, dtype=np.int32) % L if slots is None
+             else np.array(slots, dtype=np.int32))
+    init = _c(init, np.int16)
+    init_best = _c(init_best, np.int16)
+    init_best_energy = _c(init_best_energy, np.int64)
+    out_p = np.zeros((R, n), dtype=np.int16)
+    out_b = np.zeros((R, n), dtype=np.int16)
+    e = np.zeros(R, dtype=np.int64)
+    be = np.zeros(R, dtype=np.int64)
+    rc = _load().orc_qap_pt_anneal(n, _p(F), _p(D), beta.shape[1], _p(beta), R, L, _p(ladder),
+                                   _p(slots), int(t0), int(t1), int(sweeps_per_round),
+                                   int(seed) & (2**64 - 1), _p(init), _p(init_best),
+                                   _p(init_best_energy), _p(out_p), _p(e), _p(be), _p(out_b))
+    if rc != 0:
+        raise ValueError("orc_qap_pt_anneal rejected its arguments")
+    return dict(perms=out_p, energies=e, best_energies=be, best_perms=out_b, slots=slots)

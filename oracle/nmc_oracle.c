@@ -34,7 +34,8 @@
  *    (k, k+1) with k = q mod 2, k+2, ... of every ladder try to exchange their replicas a (at k)
  *    and b (at k+1): d = (lq[k] - lq[k+1]) (E_a - E_b) accepts when d >= 0, else iff
  *    ((-d) >> 8) < L and u < Tab[(-d) >> 8] for u = word 0 of the Philox block for counter
- *    (k, q, g, TAG_PT_SWAP).
+ *    (k, q, g, TAG_PT_SWAP). The QAP chain takes the same ladder on its pair temperature
+ *    (bq_r + bq_s) >> 1, with the exchange product formed exactly in 128 bits.
  *  Frozen units (the two chains of Algorithm 1 sample one subset with the other held fixed,
  *    Fig. 2 caption): beta_v[t] = +infinity holds unit v fixed at step t. A frozen k-SAT variable
  *    is not attempted; a QAP swap that involves a frozen facility is rejected (its Philox block is
@@ -853,4 +854,129 @@ int32_t orc_ksat_whitening(int32_t n, int32_t m, int32_t kmax, const int32_t *li
   free(star);
   cnf_free(&f);
   return cnt;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * QAP with replica exchange (single-threaded: the exchange rounds couple the replicas).
+ * ------------------------------------------------------------------------------------- */
+/*
+ * As orc_ksat_pt_anneal for the QAP swap chain: R = G * L replicas, replica g*L + i in ladder
+ * g, slot s(r) with Q16 temperature lq[s]; an uphill swap of replica r is tested at
+ * min(2^32-1, (lq[s(r)] * ((bq_r[t] + bq_s[t]) >> 1)) >> 16). Exchange rounds as for k-SAT, with
+ * the product (lq[k] - lq[k+1]) (E_a - E_b) formed exactly in 128 bits (QAP costs reach 2^33).
+ */
+int orc_qap_pt_anneal(int32_t n, const int32_t *F, const int32_t *D, int32_t n_steps,
+                      const float *beta, int32_t R, int32_t L, const float *ladder,
+                      int32_t *slots, int32_t t0, int32_t t1, int32_t S, uint64_t seed,
+                      const int16_t *init, const int16_t *init_best, const int64_t *init_best_e,
+                      int16_t *final_perms, int64_t *energies, int64_t *best_energies,
+                      int16_t *best_perms) {
+  if (n <= 0 || t0 < 0 || t1 < t0 || t1 > n_steps || R <= 0 || S <= 0 || L <= 0 || R % L != 0)
+    return -1;
+  const int32_t G = R / L;
+  orc_table tab;
+  table_init(&tab);
+  uint32_t *bq = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n * (size_t)n_steps);
+  for (size_t i = 0; i < (size_t)n * (size_t)n_steps; ++i) bq[i] = orc_quantize_beta(beta[i]);
+  uint32_t *lq = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)L);
+  for (int32_t k = 0; k < L; ++k) lq[k] = orc_quantize_beta(ladder[k]);
+  int32_t *at = (int32_t *)malloc(sizeof(int32_t) * (size_t)R);
+  for (int32_t r = 0; r < R; ++r) at[(r / L) * L + slots[r]] = r;
+  int16_t *p = (int16_t *)malloc(sizeof(int16_t) * (size_t)R * n);
+  int16_t *best = (int16_t *)malloc(sizeof(int16_t) * (size_t)R * n);
+  int64_t *e = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+  int64_t *be = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int32_t r = 0; r < R; ++r) {
+    int16_t *pr = p + (size_t)r * n;
+    if (init) {
+      memcpy(pr, init + (size_t)r * n, sizeof(int16_t) * (size_t)n);
+    } else {
+      for (int q = 0; q < n; ++q) pr[q] = (int16_t)q;
+      for (int q = n - 1; q >= 1; --q) {
+        const uint32_t u = philox_word((uint32_t)q, 0u, (uint32_t)r, ORC_TAG_QAP_INIT, seed, 0);
+        const int kk = (int)(((uint64_t)u * (uint64_t)(q + 1)) >> 32);
+        const int16_t tmp = pr[q];
+        pr[q] = pr[kk];
+        pr[kk] = tmp;
+      }
+    }
+    e[r] = orc_qap_cost(n, F, D, pr);
+    if (init_best) {
+      memcpy(best + (size_t)r * n, init_best + (size_t)r * n, sizeof(int16_t) * (size_t)n);
+      be[r] = init_best_e[r];
+    } else {
+      memcpy(best + (size_t)r * n, pr, sizeof(int16_t) * (size_t)n);
+      be[r] = e[r];
+    }
+  }
+  for (int32_t t = t0; t < t1; ++t) {
+    for (int32_t r = 0; r < R && n >= 2; ++r) {
+      int16_t *pr = p + (size_t)r * n;
+      const uint64_t mult = lq[slots[r]];
+      for (int32_t a = 0; a < n; ++a) {
+        const uint32_t ctr[4] = {(uint32_t)a, (uint32_t)t, (uint32_t)r, ORC_TAG_QAP_STEP};
+        uint32_t u[4];
+        orc_philox4x32_10(ctr, key, u);
+        const int32_t fr = (int32_t)(((uint64_t)u[0] * (uint64_t)n) >> 32);
+        int32_t fs = (int32_t)(((uint64_t)u[1] * (uint64_t)(n - 1)) >> 32);
+        if (fs >= fr) fs += 1;
+        const uint32_t br = bq[(size_t)fr * n_steps + t], bs = bq[(size_t)fs * n_steps + t];
+        if (br == ORC_FROZEN || bs == ORC_FROZEN) continue;
+        const int64_t d = orc_qap_swap_delta(n, F, D, pr, fr, fs);
+        int acc = 1;
+        if (d > 0) {
+          uint64_t b = (mult * (((uint64_t)br + (uint64_t)bs) >> 1)) >> 16;
+          if (b > 0xFFFFFFFFull) b = 0xFFFFFFFFull;
+          acc = accept_uphill(&tab, (uint32_t)b, d, u[2]);
+        }
+        if (acc) {
+          const int16_t tmp = pr[fr];
+          pr[fr] = pr[fs];
+          pr[fs] = tmp;
+          e[r] += d;
+        }
+      }
+      if (e[r] < be[r]) {
+        be[r] = e[r];
+        memcpy(best + (size_t)r * n, pr, sizeof(int16_t) * (size_t)n);
+      }
+    }
+    if ((t + 1) % S == 0) {
+      const uint32_t round = (uint32_t)((t + 1) / S - 1);
+      for (int32_t g = 0; g < G; ++g) {
+        int32_t *atg = at + (size_t)g * L;
+        for (int32_t k = (int32_t)(round & 1u); k + 1 < L; k += 2) {
+          const int32_t a = atg[k], b = atg[k + 1];
+          const __int128 dd = (__int128)((int64_t)lq[k] - (int64_t)lq[k + 1]) * (__int128)(e[a] - e[b]);
+          int acc = 1;
+          if (dd < 0) {
+            const __int128 idx = (-dd) >> 8;
+            const uint32_t u = philox_word((uint32_t)k, round, (uint32_t)g, ORC_TAG_PT_SWAP, seed, 0);
+            acc = idx < (__int128)tab.len && u < tab.tab[(size_t)idx];
+          }
+          if (acc) {
+            atg[k] = b;
+            atg[k + 1] = a;
+            slots[a] = k + 1;
+            slots[b] = k;
+          }
+        }
+      }
+    }
+  }
+  if (final_perms) memcpy(final_perms, p, sizeof(int16_t) * (size_t)R * n);
+  if (best_perms) memcpy(best_perms, best, sizeof(int16_t) * (size_t)R * n);
+  for (int32_t r = 0; r < R; ++r) {
+    if (energies) energies[r] = e[r];
+    if (best_energies) best_energies[r] = be[r];
+  }
+  free(p);
+  free(best);
+  free(e);
+  free(be);
+  free(at);
+  free(lq);
+  free(bq);
+  return 0;
 }

@@ -1237,11 +1237,15 @@ int nmc_replicas_set_ladder(nmc_ctx *ctx, int32_t rs, int32_t n_temps, const flo
   if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
   Instance *I = find_inst(ctx, S->inst);
   if (!I) return fail(ctx, NMC_ESTATE, "instance was unloaded");
-  int rc = check_batchable(ctx, *I);
-  if (rc != NMC_OK) return rc;
+  if (I->kind == NMC_KIND_KSAT) {
+    const int rc = check_batchable(ctx, *I);
+    if (rc != NMC_OK) return rc;
+  }
   if (n_temps < 1 || !ladder || S->R % n_temps != 0)
     return fail(ctx, NMC_EINVAL, "need a ladder of n_temps >= 1 temperatures dividing R");
-  const int32_t R = S->R, L = n_temps, G = R / L, W = S->ks.W;
+  const int32_t R = S->R, L = n_temps, G = R / L;
+  // one multiplier per replica lane: 32W for k-SAT words, R for QAP
+  const int32_t W = I->kind == NMC_KIND_KSAT ? S->ks.W : (R + 31) / 32;
   std::vector<uint32_t> lq(L);
   for (int32_t k = 0; k < L; ++k) {
     const float b = ladder[k];
@@ -1292,7 +1296,7 @@ int nmc_replicas_run_pt(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1,
   if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set");
   Instance *I = find_inst(ctx, S->inst);
   if (!I) return fail(ctx, NMC_ESTATE, "instance was unloaded");
-  int rc = check_batchable(ctx, *I);
+  int rc = I->kind == NMC_KIND_KSAT ? check_batchable(ctx, *I) : NMC_OK;
   if (rc != NMC_OK) return rc;
   if (S->pt_L < 1) return fail(ctx, NMC_ESTATE, "no ladder attached (nmc_replicas_set_ladder)");
   if (sweeps_per_round < 1) return fail(ctx, NMC_EINVAL, "sweeps_per_round must be >= 1");
@@ -1301,6 +1305,53 @@ int nmc_replicas_run_pt(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1,
     return fail(ctx, NMC_ESTATE, "schedule missing or shorter than t1");
   if (t1 == t0) return NMC_OK;
   DeviceGuard dg(ctx->device);
+  if (I->kind == NMC_KIND_QAP) {
+    // QAP: per segment one batched launch of the set's 32-replica blocks (with the
+    // multipliers), then the exchange round on the 64-bit costs
+    const int32_t Lq = S->pt_L, Gq = S->R / Lq, perq = sweeps_per_round;
+    const int32_t nblk = (S->R + 31) / 32, n = I->qp.n, npl = (n + 31) / 32;
+    int32_t t = t0;
+    std::vector<QapArgs> qitems;
+    std::vector<int32_t> ends;
+    const int64_t max_chunk = std::max<int64_t>(nblk, 1 << 16);
+    while (t < t1) {
+      qitems.clear();
+      ends.clear();
+      while (t < t1 && static_cast<int64_t>(ends.size() + 1) * nblk <= max_chunk) {
+        const int64_t te = std::min<int64_t>(t1, (static_cast<int64_t>(t) / perq + 1) * perq);
+        for (int32_t b = 0; b < nblk; ++b) {
+          QapArgs a = qap_block_args(I->qp, S->qp, I->bq, ctx->tab, ctx->tab_len, t,
+                                     static_cast<int32_t>(te), S->seed, b);
+          a.mult = S->pt_mult;
+          qitems.push_back(a);
+        }
+        ends.push_back(static_cast<int32_t>(te));
+        t = static_cast<int32_t>(te);
+      }
+      if (qitems.size() > ctx->qitems_cap) {
+        NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+        dev_free(ctx->qitems);
+        ctx->qitems_cap = 0;
+        NMC_CUDA(dev_alloc(&ctx->qitems, qitems.size()), "allocate QAP work list");
+        ctx->qitems_cap = qitems.size();
+      }
+      NMC_CUDA(cudaMemcpyAsync(ctx->qitems, qitems.data(), sizeof(QapArgs) * qitems.size(),
+                               cudaMemcpyHostToDevice, ctx->stream),
+               "upload QAP work list");
+      for (size_t i = 0; i < ends.size(); ++i) {
+        NMC_CUDA(qap_batch(ctx->qitems + i * nblk, nblk, npl, n, ctx->tab_len, ctx->stream),
+                 "launch QAP steps");
+        if (ends[i] % perq == 0)
+          NMC_CUDA(pt_exchange64(S->pt_lq, Lq, Gq, reinterpret_cast<const long long *>(S->qp.energy),
+                                 S->pt_slot, S->pt_at, S->pt_mult, ctx->tab, ctx->tab_len,
+                                 static_cast<uint32_t>(ends[i] / perq - 1),
+                                 static_cast<uint32_t>(S->seed), static_cast<uint32_t>(S->seed >> 32),
+                                 ctx->stream),
+                   "launch exchange round");
+      }
+    }
+    return NMC_OK;
+  }
   const int32_t W = S->ks.W, L = S->pt_L, G = S->R / L, per = sweeps_per_round;
   const int kq = I->ks.kq;
   int cs = 1, lanes = 0;

@@ -179,6 +179,11 @@ cudaError_t pt_exchange(const uint32_t *lq, int32_t L, int32_t G, const int32_t 
                         int32_t *slot, int32_t *at, uint32_t *mult, const uint32_t *tab,
                         int32_t tab_len, uint32_t round, uint32_t k0, uint32_t k1,
                         cudaStream_t st);
+// The same round for 64-bit energies (QAP costs); the product is tested exactly in 128 bits.
+cudaError_t pt_exchange64(const uint32_t *lq, int32_t L, int32_t G, const long long *energy,
+                          int32_t *slot, int32_t *at, uint32_t *mult, const uint32_t *tab,
+                          int32_t tab_len, uint32_t round, uint32_t k0, uint32_t k1,
+                          cudaStream_t st);
 // bq[i] = Q16(float(beta)) for i < count (a constant schedule).
 cudaError_t fill_schedule(uint32_t *bq, size_t count, double beta, int32_t *bad, cudaStream_t st);
 // From per-replica energy sums over `samples` sweeps of R replicas: sigma = sqrt(<E^2> - <E>^2)
@@ -258,6 +263,7 @@ struct QapArgs {
   uint32_t k0, k1;
   int init_mode;  // 0: run steps; 1: draw initial states (Fisher-Yates); 2: states given
   int block;      // batched launches: replica block (32 replicas) this CTA runs; else -1
+  const uint32_t *mult;  // replica exchange: Q16 temperature multiplier of each replica, or null
 };
 
 QapArgs qap_block_args(const QapDevice &I, QapReplicas &Rp, const uint32_t *bq, const uint32_t *tab,

@@ -19,8 +19,11 @@ namespace nmc {
 
 namespace {
 
+// E: int (k-SAT) or long long (QAP). The product (lq[k] - lq[k+1]) (E_a - E_b) is tested from
+// its sign and the 128-bit product of the magnitudes (QAP costs reach 2^33, lq 2^32).
+template <typename E>
 __global__ void pt_exchange_kernel(const uint32_t *__restrict__ lq, int32_t L, int32_t G,
-                                   const int32_t *__restrict__ energy, int32_t *slot, int32_t *at,
+                                   const E *__restrict__ energy, int32_t *slot, int32_t *at,
                                    uint32_t *mult, const uint32_t *__restrict__ tab,
                                    int32_t tab_len, uint32_t round, uint32_t k0, uint32_t k1) {
   const int pairs = L / 2 + 1;  // upper bound of the pairs of one ladder in either parity
@@ -31,13 +34,16 @@ __global__ void pt_exchange_kernel(const uint32_t *__restrict__ lq, int32_t L, i
   if (k + 1 >= L) return;
   int32_t *atg = at + (size_t)g * L;
   const int a = atg[k], b = atg[k + 1];
-  const long long d = ((long long)lq[k] - (long long)lq[k + 1]) *
-                      ((long long)energy[a] - (long long)energy[b]);
+  const long long dl = (long long)lq[k] - (long long)lq[k + 1];
+  const long long de = (long long)energy[a] - (long long)energy[b];
   bool acc = true;
-  if (d < 0) {
-    const unsigned long long idx = (unsigned long long)(-d) >> 8;
+  if ((dl < 0 && de > 0) || (dl > 0 && de < 0)) {  // a negative product
+    const unsigned long long ma = (unsigned long long)(dl < 0 ? -dl : dl);
+    const unsigned long long mb = (unsigned long long)(de < 0 ? -de : de);
+    const unsigned long long hi = __umul64hi(ma, mb), lo = ma * mb;
+    const unsigned long long idx = (lo >> 8) | (hi << 56);  // exact when hi < 2^8
     const uint32_t u = philox4x32_10(make_uint4((uint32_t)k, round, (uint32_t)g, kTagPtSwap), k0, k1).x;
-    acc = idx < (unsigned long long)tab_len && u < tab[idx];
+    acc = (hi >> 8) == 0 && idx < (unsigned long long)tab_len && u < tab[idx];
   }
   if (acc) {
     atg[k] = b;
@@ -107,8 +113,21 @@ cudaError_t pt_exchange(const uint32_t *lq, int32_t L, int32_t G, const int32_t 
   const long long threads = (long long)(L / 2 + 1) * G;
   const int block = 128;
   const unsigned grid = (unsigned)((threads + block - 1) / block);
-  pt_exchange_kernel<<<grid, block, 0, st>>>(lq, L, G, energy, slot, at, mult, tab, tab_len,
-                                             round, k0, k1);
+  pt_exchange_kernel<int><<<grid, block, 0, st>>>(lq, L, G, energy, slot, at, mult, tab, tab_len,
+                                                  round, k0, k1);
+  return cudaGetLastError();
+}
+
+cudaError_t pt_exchange64(const uint32_t *lq, int32_t L, int32_t G, const long long *energy,
+                          int32_t *slot, int32_t *at, uint32_t *mult, const uint32_t *tab,
+                          int32_t tab_len, uint32_t round, uint32_t k0, uint32_t k1,
+                          cudaStream_t st) {
+  if (L < 2 || G < 1) return cudaSuccess;
+  const long long threads = (long long)(L / 2 + 1) * G;
+  const int block = 128;
+  const unsigned grid = (unsigned)((threads + block - 1) / block);
+  pt_exchange_kernel<long long><<<grid, block, 0, st>>>(lq, L, G, energy, slot, at, mult, tab,
+                                                        tab_len, round, k0, k1);
   return cudaGetLastError();
 }
 

@@ -119,6 +119,7 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
   long long e = a.energy[r];
   long long be = a.best_energy[r];
   const int nm1 = n - 1;
+  const unsigned long long mr = a.mult ? a.mult[r] : 0ull;  // replica exchange multiplier
   for (int t = a.t0; t < a.t1; ++t) {
     if (n >= 2) {
       const uint32_t *bqt = a.bq + (size_t)t * n;
@@ -164,8 +165,12 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
           const long long d = 2LL * acc;
           bool ok = d <= 0;
           if (!ok) {
-            const uint32_t bj = __shfl_sync(0xFFFFFFFFu, bqs, j);
+            uint32_t bj = __shfl_sync(0xFFFFFFFFu, bqs, j);
             const uint32_t uj = __shfl_sync(0xFFFFFFFFu, u2, j);
+            if (a.mult) {  // min(2^32 - 1, (mult * bq) >> 16)
+              const unsigned long long be2 = (mr * bj) >> 16;
+              bj = be2 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)be2;
+            }
             const unsigned long long idx = ((unsigned long long)bj * (unsigned long long)d) >> 8;
             ok = idx < (unsigned long long)a.tab_len && uj < tab_s[idx];
           }
@@ -269,6 +274,7 @@ QapArgs make_args(const QapDevice &I, QapReplicas &Rp, uint64_t seed) {
   a.k1 = (uint32_t)(seed >> 32);
   a.init_mode = 0;
   a.block = -1;
+  a.mult = nullptr;
   return a;
 }
 

@@ -138,3 +138,29 @@ def test_pt_argument_checks(ctx):
     assert e.value.code == nmc.NMC_EINVAL
     ctx.replicas_destroy(rs)
     ctx.unload(inst)
+
+
+@pytest.mark.parametrize("n,L,G,per", [(24, 8, 4, 2), (100, 16, 2, 3), (200, 12, 3, 1)])
+def test_qap_pt_parity(ctx, n, L, G, per):
+    """QAP replica exchange: 1, 4 and 7 registers per lane, several ladders, exchange rounds
+    between and across run boundaries."""
+    F, D = W.random_qap(n, 700 + n)
+    T = 14
+    beta = W.beta_scaled_linear(n, T, 0.01, 1.0, 0.5, 1.5, 9)
+    ladder = W.geometric_profile(0.1, 3.0, L).astype(np.float32)
+    R = G * L
+    inst = ctx.load_qap(F, D)
+    ctx.set_schedule(inst, beta)
+    rs = ctx.replicas_create(inst, R, 21)
+    ctx.set_ladder(rs, ladder)
+    ctx.run_pt(rs, 0, 5, per)
+    ctx.run_pt(rs, 5, T, per)
+    got = ctx.replicas_read(rs)
+    slots = ctx.read_slots(rs)
+    ctx.replicas_destroy(rs)
+    ctx.unload(inst)
+    want = O.qap_pt_anneal(F, D, beta, ladder, 0, T, per, 21, replicas=R)
+    for a, b in (("states", "perms"), ("energies", "energies"), ("best_energies", "best_energies"),
+                 ("best_states", "best_perms")):
+        assert np.array_equal(got[a], want[b]), a
+    assert np.array_equal(slots, want["slots"])

@@ -941,3 +941,49 @@ def test_whitening_generalized_whitens_more_on_low_energy_states():
     lits2 = np.array([[1, 0, 0], [2, 3, 0]], np.int32)
     fr, c = O.ksat_whitening(lits2, 3, np.array([1, 1, 1], np.uint8))
     assert fr.tolist() == [1, 0, 0] and c == 1
+
+
+# ---------------------------------------------------------------- QAP replica exchange
+def test_qap_pt_equal_ladder_is_the_plain_chain_and_segments():
+    n, T = 9, 20
+    F, D = W.random_qap(n, 31)
+    beta = W.beta_scaled_linear(n, T, 0.01, 1.0, 0.5, 1.5, 2)
+    L, G = 6, 2
+    pt = O.qap_pt_anneal(F, D, beta, np.ones(L, np.float32), 0, T, 2, 5, replicas=G * L)
+    plain = O.qap_anneal(F, D, beta, 0, T, 5, replicas=G * L)
+    for a, b in (("perms", "perms"), ("energies", "energies"), ("best_energies", "best_energies"),
+                 ("best_perms", "best_perms")):
+        assert np.array_equal(pt[a], plain[b]), a
+    ladder = W.geometric_profile(0.02, 0.5, L).astype(np.float32)
+    full = O.qap_pt_anneal(F, D, beta, ladder, 0, T, 3, 5, replicas=G * L)
+    a = O.qap_pt_anneal(F, D, beta, ladder, 0, 7, 3, 5, replicas=G * L)
+    b = O.qap_pt_anneal(F, D, beta, ladder, 7, T, 3, 5, replicas=G * L, slots=a["slots"],
+                        init=a["perms"], init_best=a["best_perms"],
+                        init_best_energy=a["best_energies"])
+    for key in ("perms", "energies", "best_energies", "best_perms", "slots"):
+        assert np.array_equal(b[key], full[key]), key
+    for r in range(G * L):
+        assert full["energies"][r] == _qap_cost_numpy(F, D, full["perms"][r])
+    for g in range(G):
+        assert sorted(full["slots"][g * L:(g + 1) * L].tolist()) == list(range(L))
+
+
+def test_qap_pt_keeps_each_slot_boltzmann():
+    n = 4
+    F, D = W.random_qap(n, 14, max_entry=9)
+    perms = list(itertools.permutations(range(n)))
+    pos = {p: j for j, p in enumerate(perms)}
+    E = np.array([_qap_cost_numpy(F, D, np.array(p)) for p in perms], dtype=np.float64)
+    ladder = np.array([0.02, 0.15], dtype=np.float32)
+    T = 24
+    beta = W.beta_constant(n, T, 1.0)
+    counts = [np.zeros(len(perms)), np.zeros(len(perms))]
+    for run in range(1250):
+        res = O.qap_pt_anneal(F, D, beta, ladder, 0, T, 1, 3000 + run, replicas=4)
+        for r in range(4):
+            counts[res["slots"][r]][pos[tuple(int(x) for x in res["perms"][r])]] += 1
+    for k, b in enumerate(ladder):
+        w = np.exp(-np.float64(b) * (E - E.min()))
+        assert _chi2_pvalue(counts[k], w / w.sum()) > 1e-4, k
+    w = np.exp(-np.float64(ladder[0]) * (E - E.min()))
+    assert _chi2_pvalue(counts[1], w / w.sum()) < 1e-6
