@@ -164,3 +164,33 @@ def test_qap_pt_parity(ctx, n, L, G, per):
                  ("best_states", "best_perms")):
         assert np.array_equal(got[a], want[b]), a
     assert np.array_equal(slots, want["slots"])
+
+
+def test_pt_checkpoint_resume(ctx):
+    """A replica-exchange run read back after [0, 13) (states, best states, slots) and restored
+    into a fresh set of the same instance and seed continues exactly: [13, 30) there equals the
+    uninterrupted [0, 30)."""
+    wl = W.workload_ksat_small(30)
+    lits, n, beta = wl["lits"], wl["n_vars"], wl["beta"]
+    L, G, per = 16, 4, 3
+    ladder = W.geometric_profile(0.4, 2.5, L).astype(np.float32)
+    inst = ctx.load_ksat(lits, n)
+    ctx.set_schedule(inst, beta)
+    a = ctx.replicas_create(inst, G * L, 8)
+    ctx.set_ladder(a, ladder)
+    ctx.run_pt(a, 0, 13, per)
+    ck = ctx.replicas_read(a)
+    ck_slots = ctx.read_slots(a)
+    ctx.run_pt(a, 13, 30, per)
+    full = ctx.replicas_read(a)
+    full["slots"] = ctx.read_slots(a)
+    b = ctx.replicas_create(inst, G * L, 8)
+    ctx.replicas_restore(b, ck)
+    ctx.set_ladder(b, ladder, ck_slots)
+    ctx.run_pt(b, 13, 30, per)
+    got = ctx.replicas_read(b)
+    got["slots"] = ctx.read_slots(b)
+    ctx.replicas_destroy(a)
+    ctx.replicas_destroy(b)
+    ctx.unload(inst)
+    _same(got, full)
