@@ -646,6 +646,18 @@ def run_moves(args):
     ck = clocks.stop()
     nb = int(bb.sum())
     attempts = R * cycles * (th * nb + tc * (n - nb) + tu * n)
+    # byte model restricted to the attempted variables: per variable and sweep its clauses' other
+    # literals (k-1 words each), its own word read and written, its entries (k int32 each) and
+    # its beta (the same terms as algorithmic_bytes_per_sweep)
+    used = lits != 0
+    deg = np.bincount(np.abs(lits[used]) - 1, minlength=n).astype(np.int64)
+    kk = used.sum(axis=1)
+    nbr = np.zeros(n, np.int64)
+    np.add.at(nbr, np.abs(lits[used]) - 1, np.repeat(kk - 1, kk))
+    Wd = (R + 31) // 32
+    per_var = nbr * 4 * Wd + 2 * 4 * Wd + deg * lits.shape[1] * 4 + 4
+    bytes_step = cycles * (th * int(per_var[bb].sum()) + tc * int(per_var[~bb].sum()) +
+                           tu * int(per_var.sum()))
     ctx.set_schedule_factored(inst, np.full(T, 3.0, np.float32), np.ones(n, np.float32))
     ms_plain = _timed_events(stream, held, 1, max(2, args.steps // 2), flush)
     mask = bb.astype(np.uint8)
@@ -680,6 +692,11 @@ def run_moves(args):
             "nothing_held": {"ms_per_step": ms_plain, "value": n * R * T / (ms_plain / 1e3)},
             "cluster_flip": {"ms_per_move": ms_flip, "mask_vars": nb, "replicas": R},
             "whitening": {"ms": ms_white, "frozen_mean": float(frozen.mean())},
+            "roofline": {"bound": "hbm", "achieved": bytes_step / (ms / 1e3) / 1e9,
+                         "peak": peaks()[0], "unit": "GB/s",
+                         "frac": bytes_step / (ms / 1e3) / 1e9 / peaks()[0], "traffic": None,
+                         "peak_source": peaks()[1],
+                         "note": "sweep byte model over the attempted (unheld) variables"},
             "clocks": ck, "cpu_baseline": cpu}
 
 
