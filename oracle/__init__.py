@@ -86,7 +86,7 @@ def _load():
             lib.orc_qap_swap_delta.argtypes = [i32, P, P, P, i32, i32]
             lib.orc_qap_swap_delta.restype = i64
             lib.orc_qap_anneal.argtypes = [i32, P, P, i32, P, i32, P, i32, i32, u64, P, P, P,
-                                           i32, P, P, P, P]
+                                           i32, P, P, P, P, i32, P, P]
             lib.orc_qap_anneal.restype = C.c_int
             _lib = lib
     return _lib
@@ -371,9 +371,10 @@ def qap_swap_delta(F, D, p, r, s) -> int:
 
 
 def qap_anneal(F, D, beta, t0, t1, seed, replicas=None, replica_ids=None, init=None,
-               init_best=None, init_best_energy=None, n_threads=None):
+               init_best=None, init_best_energy=None, n_threads=None, stats_from=None):
     """Runs QAP steps t0..t1-1 (n swap attempts each). Returns dict(perms int16[R,n],
-    energies, best_energies, best_perms)."""
+    energies, best_energies, best_perms); with stats_from also e_sum / e_sq float64[R]: the
+    end-of-step costs (and squares) of steps t >= stats_from, added in step order."""
     F = _c(F, np.int32)
     D = _c(D, np.int32)
     n = F.shape[0]
@@ -391,13 +392,21 @@ def qap_anneal(F, D, beta, t0, t1, seed, replicas=None, replica_ids=None, init=N
     out_b = np.zeros((nr, n), dtype=np.int16)
     e = np.zeros(nr, dtype=np.int64)
     be = np.zeros(nr, dtype=np.int64)
+    s1 = s2 = None
+    if stats_from is not None:
+        s1 = np.zeros(nr, dtype=np.float64)
+        s2 = np.zeros(nr, dtype=np.float64)
     rc = _load().orc_qap_anneal(n, _p(F), _p(D), beta.shape[1], _p(beta), nr, _p(ids), int(t0),
                                 int(t1), int(seed) & (2**64 - 1), _p(init), _p(init_best),
                                 _p(init_best_energy), int(n_threads), _p(out_p), _p(e), _p(be),
-                                _p(out_b))
+                                _p(out_b), int(stats_from) if stats_from is not None else 0,
+                                _p(s1), _p(s2))
     if rc != 0:
         raise ValueError("orc_qap_anneal rejected its arguments")
-    return dict(perms=out_p, energies=e, best_energies=be, best_perms=out_b)
+    out = dict(perms=out_p, energies=e, best_energies=be, best_perms=out_b)
+    if stats_from is not None:
+        out.update(e_sum=s1, e_sq=s2)
+    return out
 
 
 def qap_pt_anneal(F, D, beta, ladder, t0, t1, sweeps_per_round, seed, replicas=None, slots=None,
@@ -427,3 +436,39 @@ def qap_pt_anneal(F, D, beta, ladder, t0, t1, sweeps_per_round, seed, replicas=N
     if rc != 0:
         raise ValueError("orc_qap_pt_anneal rejected its arguments")
     return dict(perms=out_p, energies=e, best_energies=be, best_perms=out_b, slots=slots)
+
+
+def qap_adaptive_ladder(F, D, replicas, seed, beta0, alpha, sigma_min, max_temps, steps_eq,
+                        steps_meas):
+    """The adaptive ladder of adaptive_ladder() for the QAP swap chain: level i runs steps
+    [i T, (i+1) T) at the homogeneous beta_i (every facility; float32, then Q16); the per-replica
+    double sums of the last steps_meas costs (and squares) are added over the replicas in replica
+    order, then sigma_i^2 = <E^2> - <E>^2 and beta_{i+1} = beta_i + alpha / sigma_i."""
+    F = _c(F, np.int32)
+    n = F.shape[0]
+    T = int(steps_eq) + int(steps_meas)
+    betas, sigmas = [], []
+    beta = float(beta0)
+    state = dict(init=None, init_best=None, init_best_energy=None)
+    for i in range(int(max_temps)):
+        t0, t1 = i * T, (i + 1) * T
+        sched = np.full((n, t1), np.float32(beta), dtype=np.float32)
+        res = qap_anneal(F, D, sched, t0, t1, seed, replicas=replicas,
+                         stats_from=t0 + int(steps_eq), **state)
+        state = dict(init=res["perms"], init_best=res["best_perms"],
+                     init_best_energy=res["best_energies"])
+        s1 = 0.0
+        s2 = 0.0
+        for r in range(int(replicas)):
+            s1 += float(res["e_sum"][r])
+            s2 += float(res["e_sq"][r])
+        samples = float(int(replicas) * int(steps_meas))
+        mean = s1 / samples
+        var = s2 / samples - mean * mean
+        sigma = math.sqrt(max(var, 0.0))
+        betas.append(beta)
+        sigmas.append(sigma)
+        if sigma <= sigma_min:
+            break
+        beta = beta + alpha / sigma
+    return np.array(betas, dtype=np.float64), np.array(sigmas, dtype=np.float64)

@@ -626,6 +626,8 @@ typedef struct {
   const int64_t *init_best_e;
   int16_t *final_perms, *best_perms;
   int64_t *energies, *best_energies;
+  int32_t stats_t0;
+  double *e_sum, *e_sq; /* nr each or NULL: sums of E and E^2 (double, step order) */
   int32_t j_begin, j_end;
 } qap_job;
 
@@ -690,6 +692,10 @@ static void qap_one_replica(const qap_job *J, int32_t j) {
       best_e = e;
       memcpy(best, p, sizeof(int16_t) * (size_t)n);
     }
+    if (J->e_sum && t >= J->stats_t0) {
+      J->e_sum[j] += (double)e;
+      J->e_sq[j] += (double)e * (double)e;
+    }
   }
   if (J->final_perms) memcpy(J->final_perms + (size_t)j * n, p, sizeof(int16_t) * (size_t)n);
   if (J->energies) J->energies[j] = e;
@@ -706,13 +712,21 @@ static void *qap_worker(void *arg) {
 }
 
 /* Runs steps t0..t1-1 of the QAP swap chain for nr replicas; arguments as orc_ksat_anneal,
- * with int16 permutations p[facility] = location. */
+ * with int16 permutations p[facility] = location. e_sum / e_sq (nr doubles each, or NULL):
+ * per replica, the end-of-step costs of steps t >= stats_t0 added in step order in double
+ * (costs reach 2^33, their squares 2^66). */
 int orc_qap_anneal(int32_t n, const int32_t *F, const int32_t *D, int32_t n_steps,
                    const float *beta, int32_t nr, const int32_t *rep_ids, int32_t t0, int32_t t1,
                    uint64_t seed, const int16_t *init, const int16_t *init_best,
                    const int64_t *init_best_e, int32_t n_threads, int16_t *final_perms,
-                   int64_t *energies, int64_t *best_energies, int16_t *best_perms) {
+                   int64_t *energies, int64_t *best_energies, int16_t *best_perms,
+                   int32_t stats_t0, double *e_sum, double *e_sq) {
   if (n <= 0 || t0 < 0 || t1 < t0 || t1 > n_steps || nr < 0) return -1;
+  if (e_sum && e_sq) {
+    for (int32_t j = 0; j < nr; ++j) e_sum[j] = e_sq[j] = 0.0;
+  } else {
+    e_sum = e_sq = NULL;
+  }
   orc_table tab;
   table_init(&tab);
   uint32_t *bq = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n * (size_t)n_steps);
@@ -742,6 +756,9 @@ int orc_qap_anneal(int32_t n, const int32_t *F, const int32_t *D, int32_t n_step
     J->best_perms = best_perms;
     J->energies = energies;
     J->best_energies = best_energies;
+    J->stats_t0 = stats_t0;
+    J->e_sum = e_sum;
+    J->e_sq = e_sq;
     J->j_begin = (int32_t)((int64_t)nr * w / n_threads);
     J->j_end = (int32_t)((int64_t)nr * (w + 1) / n_threads);
   }

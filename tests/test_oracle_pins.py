@@ -987,3 +987,57 @@ def test_qap_pt_keeps_each_slot_boltzmann():
         assert _chi2_pvalue(counts[k], w / w.sum()) > 1e-4, k
     w = np.exp(-np.float64(ladder[0]) * (E - E.min()))
     assert _chi2_pvalue(counts[1], w / w.sum()) < 1e-6
+
+
+def test_qap_energy_statistics_and_ladder_follow_their_definition():
+    n = 7
+    F, D = W.random_qap(n, 41)
+    R, eq, meas = 6, 3, 5
+    betas, sigmas = O.qap_adaptive_ladder(F, D, R, 5, 0.001, 1.1, 0.5, 6, eq, meas)
+    T = eq + meas
+    x = None
+    for i, b in enumerate(betas):
+        sched = np.full((n, (i + 1) * T), np.float32(b), np.float32)
+        es = []
+        for t in range(i * T, (i + 1) * T):
+            step = (O.qap_anneal(F, D, sched, t, t + 1, 5, replicas=R) if x is None else
+                    O.qap_anneal(F, D, sched, t, t + 1, 5, replicas=R, init=x))
+            x = step["perms"]
+            if t >= i * T + eq:
+                es.append([_qap_cost_numpy(F, D, p) for p in x])
+        es = np.array(es, dtype=np.float64)  # [steps, replicas]
+        sig = float(np.std(es))
+        assert abs(sig - sigmas[i]) <= 1e-9 * max(1.0, sig), i
+        if i + 1 < len(betas):
+            assert betas[i + 1] == b + 1.1 / sigmas[i]
+    # the statistics themselves: per replica, the costs of the measured steps summed in order
+    res = O.qap_anneal(F, D, np.full((n, 12), np.float32(0.01), np.float32), 0, 12, 2,
+                       replicas=R, stats_from=4)
+    y = None
+    s1 = np.zeros(R)
+    s2 = np.zeros(R)
+    for t in range(12):
+        step = (O.qap_anneal(F, D, np.full((n, 12), np.float32(0.01), np.float32), t, t + 1, 2,
+                             replicas=R) if y is None else
+                O.qap_anneal(F, D, np.full((n, 12), np.float32(0.01), np.float32), t, t + 1, 2,
+                             replicas=R, init=y))
+        y = step["perms"]
+        if t >= 4:
+            c = np.array([_qap_cost_numpy(F, D, p) for p in y], dtype=np.float64)
+            s1 += c
+            s2 += c * c
+    assert np.array_equal(res["e_sum"], s1) and np.array_equal(res["e_sq"], s2)
+
+
+def test_qap_ladder_measures_the_equilibrium_fluctuation():
+    n = 4
+    F, D = W.random_qap(n, 14, max_entry=9)
+    perms = list(itertools.permutations(range(n)))
+    E = np.array([_qap_cost_numpy(F, D, np.array(p)) for p in perms], dtype=np.float64)
+    betas, sigmas = O.qap_adaptive_ladder(F, D, 512, 3, 0.005, 0.6, 1.0, 5, 20, 60)
+    assert len(betas) >= 3
+    for b, sg in zip(betas, sigmas):
+        w = np.exp(-float(np.float32(b)) * (E - E.min()))
+        w /= w.sum()
+        exact = math.sqrt(float((w * E * E).sum() - (w * E).sum() ** 2))
+        assert abs(sg - exact) <= 0.06 * exact + 0.05, (b, sg, exact)
