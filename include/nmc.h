@@ -217,7 +217,7 @@ int32_t nmc_batch_max_vars(nmc_ctx *ctx);
  * g*n_temps + i at slot i. A replica at slot k moves at min(2^32-1, (lq[k] bq_v[t]) >> 16)
  * instead of the schedule's bq_v[t] (QAP: of the swap's pair temperature
  * (bq_r[t] + bq_s[t]) >> 1): the schedule gives the spatial profile, the ladder the
- * temperature. Works on k-SAT and QAP sets (the adaptive ladder below is k-SAT only).
+ * temperature. Works on k-SAT and QAP sets.
  * Replaces an earlier ladder; reset and restore leave the ladder and slots alone, and
  * nmc_replicas_run / nmc_batch_run ignore it (they sweep at the schedule's beta).
  * A k-SAT instance must be one nmc_batch_run accepts (NMC_EINVAL otherwise).
@@ -333,6 +333,10 @@ int nmc_replicas_whitening(nmc_ctx *ctx, int32_t rs, int32_t use_best, int32_t g
  * betas_out, sigmas_out: max_temps doubles (host); *n_temps_out = levels run. The instance's
  * own schedule is not used or changed. sigma_min must be >= 0 (so sigma = 0 always stops).
  * NMC_EINVAL if a beta leaves [0, 65535].
+ * QAP instances: the same with swap steps for sweeps (n attempts each) and every facility at
+ * beta_i; the costs (up to 2^33, squares beyond 2^53) are summed in double instead, per replica
+ * in step order (E converted exactly, E*E and every sum rounded to nearest), then over the
+ * replicas in replica order, so the result is reproducible but not an exact integer moment.
  */
 int nmc_adaptive_ladder(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t seed, double beta0,
                         double alpha, double sigma_min, int32_t max_temps, int32_t sweeps_eq,

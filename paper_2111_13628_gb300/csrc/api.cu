@@ -1504,6 +1504,79 @@ struct DevScratch {
   }
 };
 
+// The adaptive ladder on a QAP replica set S (fresh, Philox initial states): level i runs steps
+// [i T, (i+1) T) of every 32-replica block in one batched launch at the constant schedule beta_i,
+// with per-replica double sums of the costs of the last sweeps_meas steps, then the one-thread
+// ladder step.
+int qap_ladder(nmc_ctx *ctx, const Instance &I, ReplicaSet &S, double beta0, double alpha,
+                      double sigma_min, int32_t max_temps, int32_t sweeps_eq, int32_t sweeps_meas,
+                      double *betas_out, double *sigmas_out, int32_t *n_temps_out) {
+  const int32_t n = I.qp.n, R = S.R, nblk = (R + 31) / 32, npl = (n + 31) / 32;
+  const int64_t T = static_cast<int64_t>(sweeps_eq) + sweeps_meas;
+  uint32_t *bq = nullptr;
+  double *stats = nullptr, *out_dev = nullptr;
+  int rc = NMC_OK;
+  cudaError_t e = cudaSuccess;
+  if ((e = dev_alloc(&bq, static_cast<size_t>(n) * T)) != cudaSuccess ||
+      (e = dev_alloc(&stats, 2 * static_cast<size_t>(R))) != cudaSuccess ||
+      (e = dev_alloc(&out_dev, 2)) != cudaSuccess)
+    rc = cuda_fail(ctx, e, "allocate ladder scratch");
+  if (rc == NMC_OK && static_cast<size_t>(nblk) > ctx->qitems_cap) {
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+      rc = cuda_fail(ctx, e, "stream synchronize");
+    } else {
+      dev_free(ctx->qitems);
+      ctx->qitems_cap = 0;
+      if ((e = dev_alloc(&ctx->qitems, nblk)) != cudaSuccess)
+        rc = cuda_fail(ctx, e, "allocate QAP work list");
+      else
+        ctx->qitems_cap = nblk;
+    }
+  }
+  std::vector<QapArgs> items(nblk);
+  double beta = beta0;
+  for (int32_t i = 0; rc == NMC_OK && i < max_temps; ++i) {
+    const float bf = static_cast<float>(beta);
+    if (!(bf >= 0.0f && bf <= 65535.0f)) {
+      rc = fail(ctx, NMC_EINVAL, "a ladder temperature left [0, 65535]");
+      break;
+    }
+    const int32_t ts = static_cast<int32_t>(i * T), te = static_cast<int32_t>(ts + T);
+    // the level's schedule holds steps [ts, te) only: the base pointer is moved back by ts steps
+    // so that the kernel's index t * n + v lands in it (no access before bq)
+    const uint32_t *base = reinterpret_cast<const uint32_t *>(
+        reinterpret_cast<uintptr_t>(bq) - sizeof(uint32_t) * static_cast<size_t>(ts) * n);
+    for (int32_t b = 0; b < nblk; ++b) {
+      items[b] = qap_block_args(I.qp, S.qp, base, ctx->tab, ctx->tab_len, ts, te, S.seed, b);
+      items[b].stats = stats;
+      items[b].stats_t0 = ts + sweeps_eq;
+    }
+    double out[2] = {0.0, 0.0};
+    if ((e = fill_schedule(bq, static_cast<size_t>(n) * T, beta, ctx->flag, ctx->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(stats, 0, sizeof(double) * 2 * R, ctx->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(ctx->qitems, items.data(), sizeof(QapArgs) * nblk, cudaMemcpyHostToDevice,
+                             ctx->stream)) != cudaSuccess ||
+        (e = qap_batch(ctx->qitems, nblk, npl, n, ctx->tab_len, ctx->stream)) != cudaSuccess ||
+        (e = ladder_step_f64(stats, R, static_cast<long long>(R) * sweeps_meas, beta, alpha, out_dev,
+                             ctx->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(out, out_dev, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+      rc = cuda_fail(ctx, e, "ladder level");
+      break;
+    }
+    betas_out[i] = beta;
+    sigmas_out[i] = out[0];
+    *n_temps_out = i + 1;
+    if (out[0] <= sigma_min) break;
+    beta = out[1];
+  }
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(bq);
+  dev_free(stats);
+  dev_free(out_dev);
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1827,7 +1900,8 @@ int nmc_adaptive_ladder(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t s
   if (!ctx) return NMC_EINVAL;
   Instance *I = find_inst(ctx, inst);
   if (!I) return fail(ctx, NMC_EINVAL, "unknown instance");
-  int rc = check_batchable(ctx, *I);
+  const bool qap = I->kind == NMC_KIND_QAP;
+  int rc = qap ? NMC_OK : check_batchable(ctx, *I);
   if (rc != NMC_OK) return rc;
   if (!betas_out || !sigmas_out || !n_temps_out) return fail(ctx, NMC_EINVAL, "NULL output");
   if (max_temps < 1 || sweeps_eq < 0 || sweeps_meas < 1)
@@ -1836,8 +1910,8 @@ int nmc_adaptive_ladder(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t s
     return fail(ctx, NMC_EINVAL, "beta0 and alpha must be finite, sigma_min finite and >= 0");
   const int64_t T = static_cast<int64_t>(sweeps_eq) + sweeps_meas;
   if (T * max_temps > 0x7FFFFFFF) return fail(ctx, NMC_EINVAL, "too many sweeps in total");
-  // the energy sums stay exact: m^2 * replicas * sweeps_meas < 2^62
-  const double mm = static_cast<double>(I->ks.m);
+  // the k-SAT energy sums stay exact: m^2 * replicas * sweeps_meas < 2^62
+  const double mm = qap ? 0.0 : static_cast<double>(I->ks.m);
   if (mm * mm * replicas * sweeps_meas >= 4.6e18)
     return fail(ctx, NMC_EINVAL, "energy sums could overflow: fewer replicas or sweeps");
   *n_temps_out = 0;
@@ -1846,6 +1920,17 @@ int nmc_adaptive_ladder(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t s
   if (rc != NMC_OK) return rc;
   ReplicaSet *S = find_set(ctx, rs);
   DeviceGuard dg(ctx->device);
+  if (qap) {
+    rc = qap_ladder(ctx, *I, *S, beta0, alpha, sigma_min, max_temps, sweeps_eq, sweeps_meas,
+                    betas_out, sigmas_out, n_temps_out);
+    const std::string keep = ctx->err;
+    const int rc2 = nmc_replicas_destroy(ctx, rs);
+    if (rc != NMC_OK) {
+      ctx->err = keep;
+      return rc;
+    }
+    return rc2;
+  }
   const int32_t n = I->ks.n, W = S->ks.W;
   uint32_t *bq = nullptr, *mult = nullptr;
   long long *stats = nullptr;

@@ -190,6 +190,9 @@ cudaError_t fill_schedule(uint32_t *bq, size_t count, double beta, int32_t *bad,
 // (IEEE double, no contraction); out[0] = sigma, out[1] = beta + alpha / sigma.
 cudaError_t ladder_step(const long long *stats, int32_t R, int32_t W, long long samples,
                         double beta, double alpha, double *out, cudaStream_t st);
+// The same from per-replica double sums stats[2][R] (QAP costs), added over r = 0..R-1 in order.
+cudaError_t ladder_step_f64(const double *stats, int32_t R, long long samples, double beta,
+                            double alpha, double *out, cudaStream_t st);
 
 // ---- collective move (cluster.cu) --------------------------------------------------------
 // Device scratch one ksat_cluster_flip needs for an instance of n variables and W words.
@@ -264,6 +267,8 @@ struct QapArgs {
   int init_mode;  // 0: run steps; 1: draw initial states (Fisher-Yates); 2: states given
   int block;      // batched launches: replica block (32 replicas) this CTA runs; else -1
   const uint32_t *mult;  // replica exchange: Q16 temperature multiplier of each replica, or null
+  double *stats;         // energy statistics [2][R] (running sums of E and E^2), or null
+  int32_t stats_t0;      // first step whose end-of-step cost enters stats
 };
 
 QapArgs qap_block_args(const QapDevice &I, QapReplicas &Rp, const uint32_t *bq, const uint32_t *tab,

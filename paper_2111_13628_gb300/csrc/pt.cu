@@ -10,8 +10,9 @@
 // thread per pair needs no synchronisation.
 //
 // Ladder step: sigma(beta)^2 = <E^2> - <E>^2 over the sampled sweeps of all replicas, from
-// exact integer sums, then beta_next = beta + alpha / sigma, in IEEE double with every
-// operation rounded on its own (no fused multiply-add), so the ladder is reproducible.
+// exact integer sums (k-SAT) or per-replica double sums (QAP), then beta_next = beta +
+// alpha / sigma, in IEEE double with every operation rounded on its own (no fused
+// multiply-add), so the ladder is reproducible.
 #include "nmc_internal.h"
 #include "philox.cuh"
 
@@ -103,6 +104,24 @@ __global__ void ladder_step_kernel(const long long *__restrict__ stats, int32_t 
   }
 }
 
+// One thread: the per-replica double sums are added in replica order, as one sequential sum
+// (a tree would round differently), then the same sigma and beta step as above.
+__global__ void ladder_step_f64_kernel(const double *__restrict__ stats, int32_t R, long long samples,
+                                       double beta, double alpha, double *out) {
+  double t1 = 0.0, t2 = 0.0;
+  for (int r = 0; r < R; ++r) {
+    t1 = __dadd_rn(t1, stats[r]);
+    t2 = __dadd_rn(t2, stats[(size_t)R + r]);
+  }
+  const double nn = (double)samples;
+  const double mean = __ddiv_rn(t1, nn);
+  double var = __dsub_rn(__ddiv_rn(t2, nn), __dmul_rn(mean, mean));
+  if (var < 0.0) var = 0.0;
+  const double sigma = __dsqrt_rn(var);
+  out[0] = sigma;
+  out[1] = __dadd_rn(beta, __ddiv_rn(alpha, sigma));
+}
+
 }  // namespace
 
 cudaError_t pt_exchange(const uint32_t *lq, int32_t L, int32_t G, const int32_t *energy,
@@ -143,6 +162,12 @@ cudaError_t fill_schedule(uint32_t *bq, size_t count, double beta, int32_t *bad,
 cudaError_t ladder_step(const long long *stats, int32_t R, int32_t W, long long samples,
                         double beta, double alpha, double *out, cudaStream_t st) {
   ladder_step_kernel<<<1, 1024, 0, st>>>(stats, R, W, samples, beta, alpha, out);
+  return cudaGetLastError();
+}
+
+cudaError_t ladder_step_f64(const double *stats, int32_t R, long long samples, double beta,
+                            double alpha, double *out, cudaStream_t st) {
+  ladder_step_f64_kernel<<<1, 1, 0, st>>>(stats, R, samples, beta, alpha, out);
   return cudaGetLastError();
 }
 

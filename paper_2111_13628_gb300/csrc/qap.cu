@@ -120,6 +120,13 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
   long long be = a.best_energy[r];
   const int nm1 = n - 1;
   const unsigned long long mr = a.mult ? a.mult[r] : 0ull;  // replica exchange multiplier
+  // energy statistics: running double sums of the costs after steps t >= stats_t0 (and of their
+  // squares), continued from the stored values so that split runs add in step order
+  double s1 = 0.0, s2 = 0.0;
+  if (a.stats) {
+    s1 = a.stats[r];
+    s2 = a.stats[(size_t)a.R + r];
+  }
   for (int t = a.t0; t < a.t1; ++t) {
     if (n >= 2) {
       const uint32_t *bqt = a.bq + (size_t)t * n;
@@ -190,6 +197,11 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
         if (k < n) a.best_perm[(size_t)r * n + k] = (int16_t)p[i];
       }
     }
+    if (a.stats && t >= a.stats_t0) {
+      const double ed = (double)e;
+      s1 = __dadd_rn(s1, ed);
+      s2 = __dadd_rn(s2, __dmul_rn(ed, ed));
+    }
   }
 #pragma unroll
   for (int i = 0; i < NPL; ++i) {
@@ -199,6 +211,10 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
   if (lane == 0) {
     a.energy[r] = e;
     a.best_energy[r] = be;
+    if (a.stats) {
+      a.stats[r] = s1;
+      a.stats[(size_t)a.R + r] = s2;
+    }
   }
 }
 
@@ -275,6 +291,8 @@ QapArgs make_args(const QapDevice &I, QapReplicas &Rp, uint64_t seed) {
   a.init_mode = 0;
   a.block = -1;
   a.mult = nullptr;
+  a.stats = nullptr;
+  a.stats_t0 = 0;
   return a;
 }
 

@@ -1,5 +1,6 @@
 """Replica exchange and the adaptive ladder on the GPU, through the C ABI, against the CPU
-oracle: bit for bit (states, energies, best-so-far, slots; the ladder's doubles exactly).
+oracle: bit for bit (states, energies, best-so-far, slots; the ladders' doubles exactly, k-SAT
+and QAP).
 
 Cases span several colour classes, several replica words with a ragged last word, both
 occurrence widths (k <= 4 and k <= 8), exchange rounds that straddle run boundaries, and the
@@ -103,6 +104,20 @@ def test_adaptive_ladder_parity(ctx):
     betas, sigmas = ctx.adaptive_ladder(inst, *args)
     ctx.unload(inst)
     ob, osg = O.adaptive_ladder(lits, n, *args)
+    assert len(betas) >= 3
+    assert np.array_equal(betas, ob) and np.array_equal(sigmas, osg)
+
+
+@pytest.mark.parametrize("n,R", [(24, 70), (100, 40)])
+def test_qap_adaptive_ladder_parity(ctx, n, R):
+    """QAP ladder: per-replica double cost sums in the kernel (a ragged last 32-replica block),
+    the one-thread sequential sum over replicas; betas and sigmas equal to the last bit."""
+    F, D = W.random_qap(n, 900 + n)
+    inst = ctx.load_qap(F, D)
+    args = (R, 13, 0.0005, 0.9, 1.0, 6, 5, 9)
+    betas, sigmas = ctx.adaptive_ladder(inst, *args)
+    ctx.unload(inst)
+    ob, osg = O.qap_adaptive_ladder(F, D, *args)
     assert len(betas) >= 3
     assert np.array_equal(betas, ob) and np.array_equal(sigmas, osg)
 
