@@ -2,12 +2,16 @@
 // Sec. "Quadratic Assignment Problems"; per-facility inverse temperature as in the sampling
 // stage of Algorithm 1).
 //
-// One warp runs one replica; lane l owns the locations p[k] of facilities k = l + 32 i in
-// registers. F and D (entries 0..255, stored as bytes) of the CTA's instance sit in shared
-// memory, shared by the 32 replicas (warps) of the CTA. The swap change
+// One warp runs one replica; with NPL = ceil(n / 32), lane l owns the locations p[k] of the
+// facilities k = NPL l + i (i < NPL) in registers. F and D (entries 0..255, stored as bytes) of
+// the CTA's instance sit in shared memory, shared by the 32 replicas (warps) of the CTA; each F
+// row is stored as 32 lane chunks of CHB = 4 or 8 bytes (lane l's facilities, zero padded), so
+// a lane reads its part of a row with one aligned load. The swap change
 //   dC(r,s) = 2 sum_{k != r,s} (F_rk - F_sk)(D_{p(s)p(k)} - D_{p(r)p(k)})
-// is an O(n) dot product split over the lanes and summed with shuffles. The Philox blocks of
-// 32 consecutive attempts are drawn in parallel, one per lane, and broadcast in turn.
+// is an O(n) dot product split over the lanes: the gathered D bytes are packed four to a word
+// and the four byte products F_r D_s + F_s D_r - F_r D_r - F_s D_s are summed with dp4a, then
+// over the warp with one reduction. The Philox blocks of 32 consecutive attempts are drawn in
+// parallel, one per lane, and broadcast in turn.
 #include "nmc_internal.h"
 #include "philox.cuh"
 
@@ -33,7 +37,21 @@ __device__ __forceinline__ void put(int (&p)[NPL], int i, int v) {
     if (q == i) p[q] = v;
 }
 
-// Cost of the permutation held in registers: sum_i sum_j F_ij D_{p(i)p(j)}.
+// Shared-memory layout of F: row r at r * ldf(NPL); facility k at lane chunk k / NPL, byte
+// k % NPL of it.
+template <int NPL>
+struct FLayout {
+  static constexpr int CHB = NPL <= 4 ? 4 : 8;  // bytes of one lane's chunk of a row
+  static constexpr int LDF = 32 * CHB;          // row stride in bytes
+  __device__ __forceinline__ static int at(int r, int k) { return r * LDF + CHB * (k / NPL) + k % NPL; }
+};
+
+// Four zero-extended bytes (b[0] lowest) packed into one word.
+__device__ __forceinline__ uint32_t pack4(uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) {
+  return __byte_perm(__byte_perm(b0, b1, 0x0040), __byte_perm(b2, b3, 0x0040), 0x5410);
+}
+
+// Cost of the permutation ps: sum_i sum_j F_ij D_{p(i)p(j)}.
 template <int NPL>
 __device__ long long warp_cost(const uint8_t *Fs, const uint8_t *Ds, const uint8_t *ps, int n,
                                int lane) {
@@ -41,7 +59,7 @@ __device__ long long warp_cost(const uint8_t *Fs, const uint8_t *Ds, const uint8
   for (int i = lane; i < n; i += 32) {
     const int pi = ps[i];
     for (int j = 0; j < n; ++j)
-      acc += (long long)Fs[i * (32 * NPL) + j] * (long long)Ds[pi * n + ps[j]];
+      acc += (long long)Fs[FLayout<NPL>::at(i, j)] * (long long)Ds[pi * n + ps[j]];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
@@ -52,15 +70,15 @@ template <int NPL>
 __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
   extern __shared__ uint32_t smem[];
   const int n = a.n;
-  constexpr int LDF = 32 * NPL;  // F rows padded with zeros to the lanes' reach
+  constexpr int CHB = FLayout<NPL>::CHB, LDF = FLayout<NPL>::LDF;
   uint32_t *tab_s = smem;
   uint8_t *Fs = (uint8_t *)(smem + ((a.tab_len + 31) & ~31));
   uint8_t *Ds = Fs + ((n * LDF + 15) & ~15);
   uint8_t *pw_all = Ds + ((n * n + 15) & ~15);  // one n-byte row per warp (permutation copy)
   for (int i = threadIdx.x; i < a.tab_len; i += blockDim.x) tab_s[i] = a.tab[i];
   for (int i = threadIdx.x; i < n * LDF; i += blockDim.x) {
-    const int row = i / LDF, col = i % LDF;
-    Fs[i] = col < n ? a.F[row * n + col] : (uint8_t)0;
+    const int row = i / LDF, col = i % LDF, j = col % CHB, k = NPL * (col / CHB) + j;
+    Fs[i] = (j < NPL && k < n) ? a.F[row * n + k] : (uint8_t)0;
   }
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) Ds[i] = a.D[i];
   __syncthreads();
@@ -110,10 +128,10 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
     return;
   }
 
-  int p[NPL];
+  int p[NPL];  // padding facilities (k >= n) sit at location 0; their F entries are zero
 #pragma unroll
   for (int i = 0; i < NPL; ++i) {
-    const int k = lane + 32 * i;
+    const int k = NPL * lane + i;
     p[i] = k < n ? pw[k] : 0;
   }
   long long e = a.energy[r];
@@ -154,21 +172,45 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
           const int pj = __shfl_sync(0xFFFFFFFFu, packed, j);
           if (pj >> 18) continue;  // a held facility (uniform over the warp)
           const int rr = pj & 511, ss = (pj >> 9) & 511;
-          const int pr = __shfl_sync(0xFFFFFFFFu, pick<NPL>(p, rr >> 5), rr & 31);
-          const int ps = __shfl_sync(0xFFFFFFFFu, pick<NPL>(p, ss >> 5), ss & 31);
-          const uint8_t *Fr = Fs + rr * LDF, *Fsr = Fs + ss * LDF;
+          const int pr = __shfl_sync(0xFFFFFFFFu, pick<NPL>(p, rr % NPL), rr / NPL);
+          const int ps = __shfl_sync(0xFFFFFFFFu, pick<NPL>(p, ss % NPL), ss / NPL);
           const uint8_t *Dr = Ds + pr * n, *Dsr = Ds + ps * n;
-          // sum over every k (padded columns of F are zero); the k = r and k = s terms sum to
-          // -2 F_rs D_{p(r)p(s)} by symmetry and are added back below
-          int acc = 0;
-#pragma unroll
-          for (int i = 0; i < NPL; ++i) {
-            const int k = lane + 32 * i;
-            const int pk = p[i];
-            acc += ((int)Fr[k] - (int)Fsr[k]) * ((int)Dsr[pk] - (int)Dr[pk]);
+          // this lane's chunks of rows r and s of F
+          uint32_t fr[CHB / 4], fs[CHB / 4];
+          if constexpr (CHB == 8) {
+            const uint2 a2 = *reinterpret_cast<const uint2 *>(Fs + rr * LDF + 8 * lane);
+            const uint2 b2 = *reinterpret_cast<const uint2 *>(Fs + ss * LDF + 8 * lane);
+            fr[0] = a2.x;
+            fr[1] = a2.y;
+            fs[0] = b2.x;
+            fs[1] = b2.y;
+          } else {
+            fr[0] = *reinterpret_cast<const uint32_t *>(Fs + rr * LDF + 4 * lane);
+            fs[0] = *reinterpret_cast<const uint32_t *>(Fs + ss * LDF + 4 * lane);
           }
+          // sum over every k (padding bytes of F are zero); the k = r and k = s terms sum to
+          // -2 F_rs D_{p(r)p(s)} by symmetry and are added back below. Positive and negative
+          // products are summed apart (unsigned, below 2^21) and subtracted at the end.
+          uint32_t accp = 0u, accn = 0u;
+#pragma unroll
+          for (int w4 = 0; w4 < CHB / 4; ++w4) {
+            uint32_t dr[4], dsb[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int i = 4 * w4 + j;
+              dr[j] = i < NPL ? (uint32_t)Dr[p[i < NPL ? i : 0]] : 0u;
+              dsb[j] = i < NPL ? (uint32_t)Dsr[p[i < NPL ? i : 0]] : 0u;
+            }
+            const uint32_t wr = pack4(dr[0], dr[1], dr[2], dr[3]);
+            const uint32_t wsv = pack4(dsb[0], dsb[1], dsb[2], dsb[3]);
+            accp = __dp4a(fr[w4], wsv, accp);
+            accp = __dp4a(fs[w4], wr, accp);
+            accn = __dp4a(fr[w4], wr, accn);
+            accn = __dp4a(fs[w4], wsv, accn);
+          }
+          int acc = (int)(accp - accn);
           acc = __reduce_add_sync(0xFFFFFFFFu, acc);  // |partial sums| < 2^24: exact in int
-          acc += 2 * (int)Fr[ss] * (int)Dr[ps];
+          acc += 2 * (int)Fs[FLayout<NPL>::at(rr, ss)] * (int)Dr[ps];
           const long long d = 2LL * acc;
           bool ok = d <= 0;
           if (!ok) {
@@ -182,8 +224,8 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
             ok = idx < (unsigned long long)a.tab_len && uj < tab_s[idx];
           }
           if (ok) {
-            if (lane == (rr & 31)) put<NPL>(p, rr >> 5, ps);
-            if (lane == (ss & 31)) put<NPL>(p, ss >> 5, pr);
+            if (lane == rr / NPL) put<NPL>(p, rr % NPL, ps);
+            if (lane == ss / NPL) put<NPL>(p, ss % NPL, pr);
             e += d;
           }
         }
@@ -193,7 +235,7 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
       be = e;
 #pragma unroll
       for (int i = 0; i < NPL; ++i) {
-        const int k = lane + 32 * i;
+        const int k = NPL * lane + i;
         if (k < n) a.best_perm[(size_t)r * n + k] = (int16_t)p[i];
       }
     }
@@ -205,7 +247,7 @@ __device__ __forceinline__ void qap_body(const QapArgs &a, int block) {
   }
 #pragma unroll
   for (int i = 0; i < NPL; ++i) {
-    const int k = lane + 32 * i;
+    const int k = NPL * lane + i;
     if (k < n) gp[k] = (int16_t)p[i];
   }
   if (lane == 0) {
@@ -233,7 +275,7 @@ __global__ void __launch_bounds__(kQapWarps * 32) qap_batch_kernel(const QapArgs
 template <int NPL>
 cudaError_t launch_qap(const QapArgs &a, cudaStream_t st) {
   const int n = a.n;
-  const size_t smem = sizeof(uint32_t) * ((a.tab_len + 31) & ~31) + (size_t)((n * 32 * NPL + 15) & ~15) +
+  const size_t smem = sizeof(uint32_t) * ((a.tab_len + 31) & ~31) + (size_t)((n * FLayout<NPL>::LDF + 15) & ~15) +
                       (size_t)((n * n + 15) & ~15) + (size_t)kQapWarps * ((n + 15) & ~15);
   auto kern = qap_kernel<NPL>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -297,7 +339,8 @@ QapArgs make_args(const QapDevice &I, QapReplicas &Rp, uint64_t seed) {
 }
 
 size_t qap_smem(int n, int npl, int tab_len) {
-  return sizeof(uint32_t) * ((tab_len + 31) & ~31) + (size_t)((n * 32 * npl + 15) & ~15) +
+  const int ldf = 32 * (npl <= 4 ? 4 : 8);  // FLayout<npl>::LDF
+  return sizeof(uint32_t) * ((tab_len + 31) & ~31) + (size_t)((n * ldf + 15) & ~15) +
          (size_t)((n * n + 15) & ~15) + (size_t)kQapWarps * ((n + 15) & ~15);
 }
 
