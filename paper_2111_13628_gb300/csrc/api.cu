@@ -1165,8 +1165,8 @@ int nmc_qap_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int
   if (n_sets < 0 || (n_sets > 0 && (!rs || !t0 || !t1)))
     return fail(ctx, NMC_EINVAL, "bad batch arrays");
   DeviceGuard g(ctx->device);
-  std::vector<QapArgs> by_npl[8];
-  int max_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  std::vector<QapArgs> by_npl[kQapShapes];
+  int max_n[kQapShapes] = {0};
   std::map<int32_t, int> seen;
   for (int32_t i = 0; i < n_sets; ++i) {
     ReplicaSet *S = find_set(ctx, rs[i]);
@@ -1179,14 +1179,14 @@ int nmc_qap_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int
       return fail(ctx, NMC_ESTATE, "schedule missing or shorter than t1");
     if (t1[i] == t0[i]) continue;
     const int n = I->qp.n;
-    const int q = (n + 31) / 32 - 1;  // registers per lane - 1
+    const int q = qap_shape(n);
     for (int b = 0; b < (S->R + 31) / 32; ++b)
       by_npl[q].push_back(qap_block_args(I->qp, S->qp, I->bq, ctx->tab, ctx->tab_len, t0[i], t1[i],
                                          S->seed, b));
     max_n[q] = std::max(max_n[q], n);
   }
   size_t total = 0;
-  for (int q = 0; q < 8; ++q) total += by_npl[q].size();
+  for (int q = 0; q < kQapShapes; ++q) total += by_npl[q].size();
   if (total == 0) return NMC_OK;
   if (total > ctx->qitems_cap) {
     NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
@@ -1197,17 +1197,17 @@ int nmc_qap_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int
   }
   std::vector<QapArgs> all;
   all.reserve(total);
-  size_t off[8];
-  for (int q = 0; q < 8; ++q) {
+  size_t off[kQapShapes];
+  for (int q = 0; q < kQapShapes; ++q) {
     off[q] = all.size();
     all.insert(all.end(), by_npl[q].begin(), by_npl[q].end());
   }
   NMC_CUDA(cudaMemcpyAsync(ctx->qitems, all.data(), sizeof(QapArgs) * total, cudaMemcpyHostToDevice,
                            ctx->stream),
            "upload QAP work list");
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < kQapShapes; ++q) {
     if (by_npl[q].empty()) continue;
-    NMC_CUDA(qap_batch(ctx->qitems + off[q], static_cast<int>(by_npl[q].size()), q + 1, max_n[q],
+    NMC_CUDA(qap_batch(ctx->qitems + off[q], static_cast<int>(by_npl[q].size()), q, max_n[q],
                        ctx->tab_len, ctx->stream),
              "launch batched QAP");
   }
@@ -1309,7 +1309,7 @@ int nmc_replicas_run_pt(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1,
     // QAP: per segment one batched launch of the set's 32-replica blocks (with the
     // multipliers), then the exchange round on the 64-bit costs
     const int32_t Lq = S->pt_L, Gq = S->R / Lq, perq = sweeps_per_round;
-    const int32_t nblk = (S->R + 31) / 32, n = I->qp.n, npl = (n + 31) / 32;
+    const int32_t nblk = (S->R + 31) / 32, n = I->qp.n, shape = qap_shape(n);
     int32_t t = t0;
     std::vector<QapArgs> qitems;
     std::vector<int32_t> ends;
@@ -1339,7 +1339,7 @@ int nmc_replicas_run_pt(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1,
                                cudaMemcpyHostToDevice, ctx->stream),
                "upload QAP work list");
       for (size_t i = 0; i < ends.size(); ++i) {
-        NMC_CUDA(qap_batch(ctx->qitems + i * nblk, nblk, npl, n, ctx->tab_len, ctx->stream),
+        NMC_CUDA(qap_batch(ctx->qitems + i * nblk, nblk, shape, n, ctx->tab_len, ctx->stream),
                  "launch QAP steps");
         if (ends[i] % perq == 0)
           NMC_CUDA(pt_exchange64(S->pt_lq, Lq, Gq, reinterpret_cast<const long long *>(S->qp.energy),
@@ -1511,7 +1511,7 @@ struct DevScratch {
 int qap_ladder(nmc_ctx *ctx, const Instance &I, ReplicaSet &S, double beta0, double alpha,
                       double sigma_min, int32_t max_temps, int32_t sweeps_eq, int32_t sweeps_meas,
                       double *betas_out, double *sigmas_out, int32_t *n_temps_out) {
-  const int32_t n = I.qp.n, R = S.R, nblk = (R + 31) / 32, npl = (n + 31) / 32;
+  const int32_t n = I.qp.n, R = S.R, nblk = (R + 31) / 32, shape = qap_shape(n);
   const int64_t T = static_cast<int64_t>(sweeps_eq) + sweeps_meas;
   uint32_t *bq = nullptr;
   double *stats = nullptr, *out_dev = nullptr;
@@ -1556,7 +1556,7 @@ int qap_ladder(nmc_ctx *ctx, const Instance &I, ReplicaSet &S, double beta0, dou
         (e = cudaMemsetAsync(stats, 0, sizeof(double) * 2 * R, ctx->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(ctx->qitems, items.data(), sizeof(QapArgs) * nblk, cudaMemcpyHostToDevice,
                              ctx->stream)) != cudaSuccess ||
-        (e = qap_batch(ctx->qitems, nblk, npl, n, ctx->tab_len, ctx->stream)) != cudaSuccess ||
+        (e = qap_batch(ctx->qitems, nblk, shape, n, ctx->tab_len, ctx->stream)) != cudaSuccess ||
         (e = ladder_step_f64(stats, R, static_cast<long long>(R) * sweeps_meas, beta, alpha, out_dev,
                              ctx->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(out, out_dev, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess ||

@@ -273,9 +273,13 @@ struct QapArgs {
 
 QapArgs qap_block_args(const QapDevice &I, QapReplicas &Rp, const uint32_t *bq, const uint32_t *tab,
                        int32_t tab_len, int32_t t0, int32_t t1, uint64_t seed, int block);
-// Runs n_blocks QAP replica blocks (items_dev[b] for CTA b) in one launch; npl = 1..8
-// registers per lane (n <= 32 npl for every item), max_n sizes the shared memory.
-cudaError_t qap_batch(const QapArgs *items_dev, int n_blocks, int npl, int max_n, int tab_len,
+// Launch shape of the QAP kernels for an instance of n facilities: 0..kQapShapes-1 (lanes per
+// replica and facilities per lane); a batched launch takes items of one shape.
+constexpr int kQapShapes = 12;
+int qap_shape(int n);
+// Runs n_blocks QAP replica blocks (items_dev[b] for CTA b) in one launch; every item has
+// qap_shape(n) == shape, and max_n (the largest n) sizes the shared memory.
+cudaError_t qap_batch(const QapArgs *items_dev, int n_blocks, int shape, int max_n, int tab_len,
                       cudaStream_t st);
 // (older single-set launchers below) ------------------------------------------------------------
 // Initial permutations (Fisher-Yates from Philox, or init_dev [R][n]) with their costs; with
