@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -540,6 +541,25 @@ int prep_fail(HostKsat *out, int code, const std::string &msg) {
   return code;
 }
 
+// Runs f(lo, hi) over [0, count) split into contiguous ranges on up to 16 host threads (inline
+// for small counts). Every range writes disjoint outputs, so the result does not depend on the
+// split.
+template <typename F>
+void parallel_ranges(int64_t count, F f) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int64_t T = hw == 0 ? 1 : std::min<unsigned>(hw, 16u);
+  if (count < 8192) T = 1;
+  if (T <= 1) {
+    f(int64_t{0}, count);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int64_t t = 1; t < T; ++t)
+    th.emplace_back([&, t] { f(count * t / T, count * (t + 1) / T); });
+  f(int64_t{0}, count / T);
+  for (auto &x : th) x.join();
+}
+
 int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t *lits,
                  HostKsat *out) {
   if (n_vars < 1 || n_vars >= (1 << 28)) return prep_fail(out, NMC_EINVAL, "n_vars out of range");
@@ -581,21 +601,46 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
         if (l != 0) vcl[fill[(l > 0 ? l : -l) - 1]++] = static_cast<int32_t>(a);
       }
   }
+  // -- occurrence entries in original ids, one per (variable, clause containing it): slot 0
+  //    the variable's own sign (0 or -1), slots 1.. the clause's other literals 2u + neg, the
+  //    rest lit_false. One pass of random clause reads, spread over threads; the colouring and
+  //    the renumbered lists below stream it.
+  const int kq = K <= 4 ? 1 : 2;
+  const int slots = 4 * kq;
+  const int32_t lit_false = 2 * n, lit_true = 2 * n + 1;
+  std::vector<int32_t> occ0(static_cast<size_t>(vptr[n] > 0 ? vptr[n] : 1) * slots, lit_false);
+  parallel_ranges(n, [&](int64_t v0, int64_t v1) {
+    for (int64_t ov = v0; ov < v1; ++ov)
+      for (int32_t e = vptr[ov]; e < vptr[ov + 1]; ++e) {
+        const int64_t a = vcl[e];
+        int32_t *slot = &occ0[static_cast<size_t>(e) * slots];
+        int s = 1;
+        for (int q = 0; q < K; ++q) {
+          const int32_t l = lits[a * K + q];
+          if (l == 0) continue;
+          const int32_t u = (l > 0 ? l : -l) - 1;
+          const int32_t neg = l < 0 ? 1 : 0;
+          if (u == ov)
+            slot[0] = neg ? -1 : 0;
+          else
+            slot[s++] = 2 * u + neg;
+        }
+      }
+  });
   // -- greedy colouring in ascending id: smallest colour absent among coloured neighbours
   std::vector<int32_t> colour(n, -1);
   std::vector<int32_t> stamp(static_cast<size_t>(dmax) * (K > 1 ? K - 1 : 1) + 2, -1);
   int32_t n_colours = 0;
   for (int32_t v = 0; v < n; ++v) {
-    for (int32_t e = vptr[v]; e < vptr[v + 1]; ++e) {
-      const int64_t a = vcl[e];
-      for (int q = 0; q < K; ++q) {
-        const int32_t l = lits[a * K + q];
-        if (l == 0) continue;
-        const int32_t u = (l > 0 ? l : -l) - 1;
-        const int32_t cu = colour[u];
-        if (u != v && cu >= 0 && cu < static_cast<int32_t>(stamp.size())) stamp[cu] = v;
+    const int32_t *p0 = &occ0[static_cast<size_t>(vptr[v]) * slots];
+    const int32_t *p1 = &occ0[static_cast<size_t>(vptr[v + 1]) * slots];
+    for (const int32_t *q = p0; q < p1; q += slots)
+      for (int z = 1; z < slots; ++z) {
+        const int32_t l = q[z];
+        if (l >= lit_false) continue;
+        const int32_t cu = colour[l >> 1];
+        if (cu >= 0 && cu < static_cast<int32_t>(stamp.size())) stamp[cu] = v;
       }
-    }
     int32_t c = 0;
     while (c < static_cast<int32_t>(stamp.size()) && stamp[c] == v) ++c;
     colour[v] = c;
@@ -618,37 +663,30 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
     for (int32_t p = 0; p < n; ++p) newid[orig[p]] = p;
   }
   // -- occurrence lists in new ids, each padded to a multiple of 4 occurrences
-  const int kq = K <= 4 ? 1 : 2;
-  const int slots = 4 * kq;
-  const int32_t lit_false = 2 * n, lit_true = 2 * n + 1;
   std::vector<int32_t> occ_ptr(n + 1, 0);
   for (int32_t v = 0; v < n; ++v) occ_ptr[v + 1] = occ_ptr[v] + ((deg[orig[v]] + 3) & ~3);
   const int64_t n_occ = occ_ptr[n];
   std::vector<int32_t> occ(static_cast<size_t>(n_occ > 0 ? n_occ : 1) * slots, lit_false);
-  for (int32_t v = 0; v < n; ++v) {
-    const int32_t ov = orig[v];
-    int64_t o = occ_ptr[v];
-    for (int32_t e = vptr[ov]; e < vptr[ov + 1]; ++e, ++o) {
-      const int64_t a = vcl[e];
-      int32_t *slot = &occ[static_cast<size_t>(o) * slots];
-      int s = 1;
-      for (int q = 0; q < K; ++q) {
-        const int32_t l = lits[a * K + q];
-        if (l == 0) continue;
-        const int32_t u = (l > 0 ? l : -l) - 1;
-        const int32_t neg = l < 0 ? 1 : 0;
-        if (u == ov)
-          slot[0] = neg ? -1 : 0;
-        else
-          slot[s++] = 2 * newid[u] + neg;
+  parallel_ranges(n, [&](int64_t v0, int64_t v1) {
+    for (int64_t v = v0; v < v1; ++v) {
+      const int32_t ov = orig[v];
+      int64_t o = occ_ptr[v];
+      for (int32_t e = vptr[ov]; e < vptr[ov + 1]; ++e, ++o) {
+        const int32_t *src = &occ0[static_cast<size_t>(e) * slots];
+        int32_t *slot = &occ[static_cast<size_t>(o) * slots];
+        slot[0] = src[0];
+        for (int z = 1; z < slots; ++z) {
+          const int32_t l = src[z];
+          slot[z] = l >= lit_false ? l : 2 * newid[l >> 1] + (l & 1);
+        }
+      }
+      for (; o < occ_ptr[v + 1]; ++o) {  // padding: a satisfied pseudo-clause (no effect)
+        int32_t *slot = &occ[static_cast<size_t>(o) * slots];
+        slot[0] = 0;
+        slot[1] = lit_true;
       }
     }
-    for (; o < occ_ptr[v + 1]; ++o) {  // padding: a satisfied pseudo-clause (no effect)
-      int32_t *slot = &occ[static_cast<size_t>(o) * slots];
-      slot[0] = 0;
-      slot[1] = lit_true;
-    }
-  }
+  });
   // -- the same lists interleaved per group of 32 consecutive variables of a colour class
   //    (group g covers new ids [col_ptr[c] + 32k, +32)): occurrence j of the group's lane l
   //    sits at grp_base[g] + (j*kq + q)*32 + l (int4 units), so one warp load of occurrence j
@@ -657,7 +695,7 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
   //    variable's word in the shared-memory word vector, and bit 7 of byte 0 / 1 / 2 / 3 of the
   //    first field set when the own literal / literal 1 / 2 / 3 is negated. For k > 4 the two
   //    int4 hold the literal ids as in the per-variable lists.
-  std::vector<int32_t> cgrp(n_colours + 1, 0), grp_base(1, 0);
+  std::vector<int32_t> cgrp(n_colours + 1, 0), grp_base(1, 0), grp_v0;
   for (int32_t c = 0; c < n_colours; ++c) {
     const int32_t size = col_ptr[c + 1] - col_ptr[c];
     cgrp[c + 1] = cgrp[c] + (size + 31) / 32;
@@ -666,19 +704,24 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
       for (int32_t v = g0; v < std::min(g0 + 32, col_ptr[c + 1]); ++v)
         len = std::max(len, occ_ptr[v + 1] - occ_ptr[v]);
       grp_base.push_back(grp_base.back() + len * kq * 32);
+      grp_v0.push_back(g0);
     }
   }
+  // the class end of every group's first variable
+  std::vector<int32_t> grp_end(grp_v0.size());
+  for (int32_t c = 0; c < n_colours; ++c)
+    for (int32_t g = cgrp[c]; g < cgrp[c + 1]; ++g) grp_end[g] = col_ptr[c + 1];
   std::vector<int32_t> occ_t(static_cast<size_t>(std::max<int64_t>(grp_base.back(), 1)) * 4);
-  for (int32_t c = 0; c < n_colours; ++c) {
-    int32_t g = cgrp[c];
-    for (int32_t g0 = col_ptr[c]; g0 < col_ptr[c + 1]; g0 += 32, ++g) {
+  parallel_ranges(static_cast<int64_t>(grp_v0.size()), [&](int64_t ga, int64_t gz) {
+    for (int64_t g = ga; g < gz; ++g) {
+      const int32_t g0 = grp_v0[g], cend = grp_end[g];
       const int32_t len = (grp_base[g + 1] - grp_base[g]) / (kq * 32);
       for (int32_t l = 0; l < 32; ++l) {
         const int32_t v = g0 + l;
         for (int32_t j = 0; j < len; ++j)
           for (int q = 0; q < kq; ++q) {
             int32_t *dst = &occ_t[(static_cast<size_t>(grp_base[g]) + (j * kq + q) * 32 + l) * 4];
-            const bool real = v < col_ptr[c + 1] && j < occ_ptr[v + 1] - occ_ptr[v];
+            const bool real = v < cend && j < occ_ptr[v + 1] - occ_ptr[v];
             const int32_t *src = real ? &occ[(static_cast<size_t>(occ_ptr[v] + j) * slots) + 4 * q] : nullptr;
             if (kq == 1) {
               // src: {own sign mask, lit1, lit2, lit3} in literal ids (2u + neg)
@@ -701,15 +744,17 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
           }
       }
     }
-  }
+  });
   std::vector<int32_t> clits(static_cast<size_t>(m > 0 ? m : 1) * K, lit_false);
-  for (int64_t a = 0; a < m; ++a)
-    for (int q = 0; q < K; ++q) {
-      const int32_t l = lits[a * K + q];
-      if (l == 0) continue;
-      const int32_t u = (l > 0 ? l : -l) - 1;
-      clits[a * K + q] = 2 * newid[u] + (l < 0 ? 1 : 0);
-    }
+  parallel_ranges(m, [&](int64_t a0, int64_t a1) {
+    for (int64_t a = a0; a < a1; ++a)
+      for (int q = 0; q < K; ++q) {
+        const int32_t l = lits[a * K + q];
+        if (l == 0) continue;
+        const int32_t u = (l > 0 ? l : -l) - 1;
+        clits[a * K + q] = 2 * newid[u] + (l < 0 ? 1 : 0);
+      }
+  });
   int nb = 2;
   while ((1 << nb) <= dmax) ++nb;
   out->n = n;
