@@ -57,15 +57,37 @@ __device__ __forceinline__ uint32_t pack4(uint32_t b0, uint32_t b1, uint32_t b2,
   return __byte_perm(__byte_perm(b0, b1, 0x0040), __byte_perm(b2, b3, 0x0040), 0x5410);
 }
 
-// Cost of the permutation ps with the whole warp: sum_i sum_j F_ij D_{p(i)p(j)}.
+// Cost of the permutation ps with the whole warp: sum_i sum_j F_ij D_{p(i)p(j)}. The warp's
+// 32 / LPR lane groups take rows i in turn; lane l of a group reads its chunk of F row i and the
+// bytes D_{p(i)p(k)} of its facilities k = NPL l + q, four to a word, and sums the products with
+// dp4a (a row's partial sum stays below 2^22).
 template <int NPL, int LPR>
 __device__ long long warp_cost(const uint8_t *Fs, const uint8_t *Ds, const uint8_t *ps, int n,
                                int lane) {
+  constexpr int CHB = FLayout<NPL, LPR>::CHB, LDF = FLayout<NPL, LPR>::LDF, RPW = 32 / LPR;
+  const int hl = lane % LPR;
+  int pk[NPL];
+#pragma unroll
+  for (int q = 0; q < NPL; ++q) {
+    const int k = NPL * hl + q;
+    pk[q] = k < n ? ps[k] : 0;  // padding facilities: F entries zero
+  }
   long long acc = 0;
-  for (int i = lane; i < n; i += 32) {
-    const int pi = ps[i];
-    for (int j = 0; j < n; ++j)
-      acc += (long long)Fs[FLayout<NPL, LPR>::at(i, j)] * (long long)Ds[pi * n + ps[j]];
+  for (int i = lane / LPR; i < n; i += RPW) {
+    const uint8_t *Drow = Ds + ps[i] * n;
+    const uint32_t *Fw = reinterpret_cast<const uint32_t *>(Fs + i * LDF + CHB * hl);
+    uint32_t row = 0u;
+#pragma unroll
+    for (int w4 = 0; w4 < CHB / 4; ++w4) {
+      uint32_t b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = 4 * w4 + q;
+        b[q] = j < NPL ? (uint32_t)Drow[pk[j < NPL ? j : 0]] : 0u;
+      }
+      row = __dp4a(Fw[w4], pack4(b[0], b[1], b[2], b[3]), row);
+    }
+    acc += row;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
