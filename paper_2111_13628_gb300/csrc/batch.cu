@@ -207,173 +207,6 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
   return x ^ flip;
 }
 
-// A colour class [c0, c1) is shared out among the CS CTAs of a cluster by 32-variable groups,
-// round-robin: CTA `rank` takes groups rank, rank + CS, ... Variables are degree-descending
-// inside a class, so each CTA gets a like mix of long and short occurrence lists (contiguous
-// shares would give rank 0 all the longest lists and make every class wait for it).
-template <int CS>
-__device__ __forceinline__ int share_count(int c0, int c1, int rank) {
-  const int ng = (c1 - c0 + 31) >> 5;
-  const int mine = ng > rank ? (ng - rank + CS - 1) / CS : 0;
-  int cnt = mine * 32;
-  if (mine > 0 && rank + (mine - 1) * CS == ng - 1) cnt -= ng * 32 - (c1 - c0);  // last, partial
-  return cnt;
-}
-
-// Local index li (0 <= li < share_count) -> variable.
-template <int CS>
-__device__ __forceinline__ int share_var(int c0, int rank, int li) {
-  return c0 + 32 * (rank + CS * (li >> 5)) + (li & 31);
-}
-
-// Synchronises the CS CTAs of a cluster (or the CTA when CS = 1); cluster barriers are
-// hardware barriers with release/acquire semantics for distributed shared memory.
-template <int CS>
-__device__ __forceinline__ void group_sync() {
-  if (CS == 1) {
-    __syncthreads();
-  } else {
-    cg::this_cluster().sync();
-  }
-}
-
-// Stores v at the same shared-memory word of CTA `rank` of the cluster (32-bit addressing).
-__device__ __forceinline__ void st_rank(uint32_t saddr, int rank, uint32_t v) {
-  uint32_t ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(saddr), "r"(rank));
-  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
-}
-
-template <int CS, typename T>
-__device__ __forceinline__ T *rank_ptr(T *p, int r) {
-  if (CS == 1) return p;
-  return cg::this_cluster().map_shared_rank(p, r);
-}
-
-// CS = CTAs per item. With CS > 1 every CTA of the cluster keeps a full copy of the item's
-// word vector; each CTA updates its share of every colour class and stores the new words
-// into all CS copies (distributed shared memory), then the cluster barrier publishes them.
-// PT: every item carries per-replica temperature multipliers and, optionally, accumulates the
-// end-of-sweep energies of sweeps t >= stats_t0 (sums of E and E^2 per replica).
-template <int KQ, int CS, bool PT>
-__global__ void __launch_bounds__(kBatchThreads, 1)
-    ksat_batch_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
-                      const uint32_t *tab, int tab_len, int xs_words) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t *xs = smem;                               // word vector first (byte offsets in lists)
-  uint32_t *tab_s = smem + ((xs_words + 31) & ~31);  // then the acceptance table
-  __shared__ int e_s[32], be_s[32], ep_s[32];
-  __shared__ uint32_t mult_s[32];
-  __shared__ uint32_t imp_s;
-  __shared__ int item_s;
-  __shared__ BatchItem item_b;  // the current item, read from shared memory where needed
-  const int rank = CS == 1 ? 0 : (int)cg::this_cluster().block_rank();
-  for (int i = threadIdx.x; i <= tab_len; i += blockDim.x) tab_s[i] = i < tab_len ? tab[i] : 0u;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  while (true) {
-    if (rank == 0 && threadIdx.x == 0) item_s = atomicAdd(next_item, 1);
-    group_sync<CS>();
-    const int it = *rank_ptr<CS>(&item_s, 0);
-    if (it < n_items && threadIdx.x == 0) item_b = items[it];
-    group_sync<CS>();  // every rank has read the item id before any rank moves on or exits
-    if (it >= n_items) break;
-    const BatchItem &B = item_b;
-    const int n = B.n, W = B.W, w = B.w;
-    const int share = (n + CS - 1) / CS;
-    for (int v = threadIdx.x; v < n; v += blockDim.x) xs[v] = B.S[(size_t)(2 * v) * W + w];
-    if (threadIdx.x == 0) xs[n] = 0u;
-    if (threadIdx.x < 32) {
-      ep_s[threadIdx.x] = 0;
-      if (PT) mult_s[threadIdx.x] = B.mult[32 * w + threadIdx.x];
-      if (rank == 0) {
-        e_s[threadIdx.x] = B.energy[32 * w + threadIdx.x];
-        be_s[threadIdx.x] = B.best_energy[32 * w + threadIdx.x];
-      }
-    }
-    long long s1 = 0, s2 = 0;  // energy statistics of this lane's replica (rank 0, warp 0)
-    group_sync<CS>();
-    for (int t = B.t0; t < B.t1; ++t) {
-      uint32_t acc[kAccPlanes];
-#pragma unroll
-      for (int j = 0; j < kAccPlanes; ++j) acc[j] = 0u;
-      for (int c = 0; c < B.n_colours; ++c) {
-        const int c0 = __ldg(B.col_ptr + c), c1 = __ldg(B.col_ptr + c + 1);
-        // the class's 32-variable groups are dealt round-robin to the cluster's CTAs
-        const int cnt = share_count<CS>(c0, c1, rank);
-        for (int li = threadIdx.x; li < cnt; li += blockDim.x) {
-          const int v = share_var<CS>(c0, rank, li);
-          const uint32_t xn = attempt_batch<KQ, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, v, t, acc);
-          if (CS == 1) {
-            xs[v] = xn;
-          } else {
-            const uint32_t sa = (uint32_t)__cvta_generic_to_shared(xs + v);
-#pragma unroll
-            for (int r = 0; r < CS; ++r) st_rank(sa, r, xn);
-          }
-        }
-        group_sync<CS>();
-      }
-      // per-replica sums of this sweep: planes -> 16-bit values (two byte transposes per block
-      // of 8 replicas), then a warp reduction per replica
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const unsigned long long lo = transpose8(gather_bytes(acc, q));
-        const unsigned long long hi = transpose8(gather_bytes(acc + 8, q));
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int val = (int)(short)(unsigned short)(((lo >> (8 * i)) & 0xFFull) |
-                                                       (((hi >> (8 * i)) & 0xFFull) << 8));
-          const int s2 = __reduce_add_sync(0xFFFFFFFFu, val);
-          if (lane == 0 && s2 != 0) atomicAdd(&ep_s[8 * q + i], s2);
-        }
-      }
-      group_sync<CS>();
-      if (rank == 0 && warp == 0) {
-        int sum = e_s[lane];
-#pragma unroll
-        for (int r = 0; r < CS; ++r) sum += rank_ptr<CS>(ep_s, r)[lane];
-        e_s[lane] = sum;
-        if (PT && B.stats && t >= B.stats_t0) {
-          s1 += sum;
-          s2 += (long long)sum * sum;
-        }
-        const bool better = sum < be_s[lane];
-        if (better) be_s[lane] = sum;
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, better);
-        if (lane == 0) imp_s = m;
-      }
-      group_sync<CS>();
-      const uint32_t m = *rank_ptr<CS>(&imp_s, 0);
-      if (threadIdx.x < 32) ep_s[threadIdx.x] = 0;
-      if (m) {
-        const int b0 = rank * share, b1 = min(n, b0 + share);
-        for (int v = b0 + threadIdx.x; v < b1; v += blockDim.x) {
-          const size_t bi = (size_t)v * W + w;
-          B.best[bi] = (B.best[bi] & ~m) | (xs[v] & m);
-        }
-        group_sync<CS>();
-      }
-    }
-    {
-      const int b0 = rank * share, b1 = min(n, b0 + share);
-      for (int v = b0 + threadIdx.x; v < b1; v += blockDim.x) {
-        B.S[(size_t)(2 * v) * W + w] = xs[v];
-        B.S[(size_t)(2 * v + 1) * W + w] = ~xs[v];
-      }
-    }
-    if (rank == 0 && threadIdx.x < 32) {
-      B.energy[32 * w + threadIdx.x] = e_s[threadIdx.x];
-      B.best_energy[32 * w + threadIdx.x] = be_s[threadIdx.x];
-      if (PT && B.stats) {  // one item per word in a launch: plain read-modify-write
-        B.stats[32 * w + threadIdx.x] += s1;
-        B.stats[32 * (B.W + w) + threadIdx.x] += s2;
-      }
-    }
-    group_sync<CS>();
-  }
-}
-
-
 // ---- team variant: TL lanes per variable --------------------------------------------------------
 //
 // Same dynamics, shorter critical path: a team of TL consecutive lanes evaluates one variable.
@@ -461,10 +294,12 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
   }
   const uint32_t vo = active ? (uint32_t)__ldg(B.orig + v) : 0u;
   const uint32_t bq_hi = bqv >> 8, bq_lo = bqv & 255u;
-  constexpr int GPL = 8 / TL;  // Philox groups per lane
-  // the lane's replicas lie in one block of 8: one 8x8 transpose of the 8 planes of D gives
-  // their signed bytes
-  const unsigned long long xm = transpose8(gather_bytes(d, (tl * GPL) >> 1));
+  constexpr int GPL = 8 / TL;             // Philox groups (4 replicas) per lane
+  constexpr int NBK = GPL >= 2 ? GPL / 2 : 1;  // blocks of 8 replicas the lane's groups lie in
+  // one 8x8 transpose of the 8 planes of D per block gives the replicas' signed bytes
+  unsigned long long xmb[NBK];
+#pragma unroll
+  for (int b = 0; b < NBK; ++b) xmb[b] = transpose8(gather_bytes(d, ((tl * GPL) >> 1) + b));
   uint32_t flip = 0u;
 #pragma unroll
   for (int gi = 0; gi < GPL; ++gi) {
@@ -475,7 +310,7 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int r = 4 * g + j;
-      const int val = (int)(signed char)(unsigned char)(xm >> (8 * (r & 7)));
+      const int val = (int)(signed char)(unsigned char)(xmb[gi >> 1] >> (8 * (r & 7)));
       de[j] = val;
       th[j] = 0u;
       if (val > 0) {
@@ -507,6 +342,216 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
   for (int sft = 1; sft < TL; sft <<= 1) flip |= __shfl_xor_sync(0xFFFFFFFFu, flip, sft);
   return x ^ flip;
 }
+
+// A colour class [c0, c1) is shared out among the CS CTAs of a cluster by 32-variable groups,
+// round-robin: CTA `rank` takes groups rank, rank + CS, ... Variables are degree-descending
+// inside a class, so each CTA gets a like mix of long and short occurrence lists (contiguous
+// shares would give rank 0 all the longest lists and make every class wait for it).
+template <int CS>
+__device__ __forceinline__ int share_count(int c0, int c1, int rank) {
+  const int ng = (c1 - c0 + 31) >> 5;
+  const int mine = ng > rank ? (ng - rank + CS - 1) / CS : 0;
+  int cnt = mine * 32;
+  if (mine > 0 && rank + (mine - 1) * CS == ng - 1) cnt -= ng * 32 - (c1 - c0);  // last, partial
+  return cnt;
+}
+
+// Local index li (0 <= li < share_count) -> variable.
+template <int CS>
+__device__ __forceinline__ int share_var(int c0, int rank, int li) {
+  return c0 + 32 * (rank + CS * (li >> 5)) + (li & 31);
+}
+
+// Synchronises the CS CTAs of a cluster (or the CTA when CS = 1); cluster barriers are
+// hardware barriers with release/acquire semantics for distributed shared memory.
+template <int CS>
+__device__ __forceinline__ void group_sync() {
+  if (CS == 1) {
+    __syncthreads();
+  } else {
+    cg::this_cluster().sync();
+  }
+}
+
+// Stores v at the same shared-memory word of CTA `rank` of the cluster (32-bit addressing).
+__device__ __forceinline__ void st_rank(uint32_t saddr, int rank, uint32_t v) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(saddr), "r"(rank));
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+}
+
+template <int CS, typename T>
+__device__ __forceinline__ T *rank_ptr(T *p, int r) {
+  if (CS == 1) return p;
+  return cg::this_cluster().map_shared_rank(p, r);
+}
+
+// A colour class whose share on this CTA is cnt <= blockDim / TT variables: team `team` (TT
+// consecutive lanes) updates local variable `team` (the same round-robin share as the one-thread
+// path) with attempt_team, stores its new word to every copy of the cluster, and adds its
+// replicas' energy changes to ep_s. Warps with no team in range skip the class.
+template <int KQ, int CS, int TT, bool PT>
+__device__ __forceinline__ void class_teams(const BatchItem &B, uint32_t *xs, const uint32_t *tab_s,
+                                            int tab_len, const uint32_t *mult_s, int c, int c0,
+                                            int cnt, int rank, int t, int *ep_s) {
+  const int lane = threadIdx.x & 31;
+  if ((int)(threadIdx.x & ~31u) / TT >= cnt) return;  // the whole warp
+  const int team = threadIdx.x / TT, tl = lane % TT;
+  const bool active = team < cnt;
+  const int v = active ? share_var<CS>(c0, rank, team) : c0;
+  int tacc[32 / TT];
+#pragma unroll
+  for (int i = 0; i < 32 / TT; ++i) tacc[i] = 0;
+  const uint32_t xn = attempt_team<KQ, TT, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, v, active, t, tl, tacc);
+  if (active && tl == 0) {
+    if (CS == 1) {
+      xs[v] = xn;
+    } else {
+      const uint32_t sa = (uint32_t)__cvta_generic_to_shared(xs + v);
+#pragma unroll
+      for (int r = 0; r < CS; ++r) st_rank(sa, r, xn);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 32 / TT; ++i)
+    if (tacc[i] != 0) atomicAdd(&ep_s[4 * (tl * (8 / TT) + i / 4) + (i & 3)], tacc[i]);
+}
+
+// CS = CTAs per item. With CS > 1 every CTA of the cluster keeps a full copy of the item's
+// word vector; each CTA updates its share of every colour class and stores the new words
+// into all CS copies (distributed shared memory), then the cluster barrier publishes them.
+// PT: every item carries per-replica temperature multipliers and, optionally, accumulates the
+// end-of-sweep energies of sweeps t >= stats_t0 (sums of E and E^2 per replica).
+template <int KQ, int CS, bool PT>
+__global__ void __launch_bounds__(kBatchThreads, 1)
+    ksat_batch_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
+                      const uint32_t *tab, int tab_len, int xs_words) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t *xs = smem;                               // word vector first (byte offsets in lists)
+  uint32_t *tab_s = smem + ((xs_words + 31) & ~31);  // then the acceptance table
+  __shared__ int e_s[32], be_s[32], ep_s[32];
+  __shared__ uint32_t mult_s[32];
+  __shared__ uint32_t imp_s;
+  __shared__ int item_s;
+  __shared__ BatchItem item_b;  // the current item, read from shared memory where needed
+  const int rank = CS == 1 ? 0 : (int)cg::this_cluster().block_rank();
+  for (int i = threadIdx.x; i <= tab_len; i += blockDim.x) tab_s[i] = i < tab_len ? tab[i] : 0u;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  while (true) {
+    if (rank == 0 && threadIdx.x == 0) item_s = atomicAdd(next_item, 1);
+    group_sync<CS>();
+    const int it = *rank_ptr<CS>(&item_s, 0);
+    if (it < n_items && threadIdx.x == 0) item_b = items[it];
+    group_sync<CS>();  // every rank has read the item id before any rank moves on or exits
+    if (it >= n_items) break;
+    const BatchItem &B = item_b;
+    const int n = B.n, W = B.W, w = B.w;
+    const int share = (n + CS - 1) / CS;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) xs[v] = B.S[(size_t)(2 * v) * W + w];
+    if (threadIdx.x == 0) xs[n] = 0u;
+    if (threadIdx.x < 32) {
+      ep_s[threadIdx.x] = 0;
+      if (PT) mult_s[threadIdx.x] = B.mult[32 * w + threadIdx.x];
+      if (rank == 0) {
+        e_s[threadIdx.x] = B.energy[32 * w + threadIdx.x];
+        be_s[threadIdx.x] = B.best_energy[32 * w + threadIdx.x];
+      }
+    }
+    long long s1 = 0, s2 = 0;  // energy statistics of this lane's replica (rank 0, warp 0)
+    group_sync<CS>();
+    for (int t = B.t0; t < B.t1; ++t) {
+      uint32_t acc[kAccPlanes];
+#pragma unroll
+      for (int j = 0; j < kAccPlanes; ++j) acc[j] = 0u;
+      for (int c = 0; c < B.n_colours; ++c) {
+        const int c0 = __ldg(B.col_ptr + c), c1 = __ldg(B.col_ptr + c + 1);
+        // the class's 32-variable groups are dealt round-robin to the cluster's CTAs
+        const int cnt = share_count<CS>(c0, c1, rank);
+        if (cnt <= kBatchThreads / 2) {
+          // a smaller share (the later colour classes): teams of 8, 4 or 2 lanes per variable
+          // shorten the class's critical path; their energy changes go to ep_s directly
+          if (cnt <= kBatchThreads / 8)
+            class_teams<KQ, CS, 8, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, cnt, rank, t, ep_s);
+          else if (cnt <= kBatchThreads / 4)
+            class_teams<KQ, CS, 4, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, cnt, rank, t, ep_s);
+          else
+            class_teams<KQ, CS, 2, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, cnt, rank, t, ep_s);
+        } else {
+          for (int li = threadIdx.x; li < cnt; li += blockDim.x) {
+            const int v = share_var<CS>(c0, rank, li);
+            const uint32_t xn = attempt_batch<KQ, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, v, t, acc);
+            if (CS == 1) {
+              xs[v] = xn;
+            } else {
+              const uint32_t sa = (uint32_t)__cvta_generic_to_shared(xs + v);
+#pragma unroll
+              for (int r = 0; r < CS; ++r) st_rank(sa, r, xn);
+            }
+          }
+        }
+        group_sync<CS>();
+      }
+      // per-replica sums of this sweep: planes -> 16-bit values (two byte transposes per block
+      // of 8 replicas), then a warp reduction per replica
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const unsigned long long lo = transpose8(gather_bytes(acc, q));
+        const unsigned long long hi = transpose8(gather_bytes(acc + 8, q));
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int val = (int)(short)(unsigned short)(((lo >> (8 * i)) & 0xFFull) |
+                                                       (((hi >> (8 * i)) & 0xFFull) << 8));
+          const int s2 = __reduce_add_sync(0xFFFFFFFFu, val);
+          if (lane == 0 && s2 != 0) atomicAdd(&ep_s[8 * q + i], s2);
+        }
+      }
+      group_sync<CS>();
+      if (rank == 0 && warp == 0) {
+        int sum = e_s[lane];
+#pragma unroll
+        for (int r = 0; r < CS; ++r) sum += rank_ptr<CS>(ep_s, r)[lane];
+        e_s[lane] = sum;
+        if (PT && B.stats && t >= B.stats_t0) {
+          s1 += sum;
+          s2 += (long long)sum * sum;
+        }
+        const bool better = sum < be_s[lane];
+        if (better) be_s[lane] = sum;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, better);
+        if (lane == 0) imp_s = m;
+      }
+      group_sync<CS>();
+      const uint32_t m = *rank_ptr<CS>(&imp_s, 0);
+      if (threadIdx.x < 32) ep_s[threadIdx.x] = 0;
+      __syncthreads();  // cleared before the next sweep's team-path adds
+      if (m) {
+        const int b0 = rank * share, b1 = min(n, b0 + share);
+        for (int v = b0 + threadIdx.x; v < b1; v += blockDim.x) {
+          const size_t bi = (size_t)v * W + w;
+          B.best[bi] = (B.best[bi] & ~m) | (xs[v] & m);
+        }
+        group_sync<CS>();
+      }
+    }
+    {
+      const int b0 = rank * share, b1 = min(n, b0 + share);
+      for (int v = b0 + threadIdx.x; v < b1; v += blockDim.x) {
+        B.S[(size_t)(2 * v) * W + w] = xs[v];
+        B.S[(size_t)(2 * v + 1) * W + w] = ~xs[v];
+      }
+    }
+    if (rank == 0 && threadIdx.x < 32) {
+      B.energy[32 * w + threadIdx.x] = e_s[threadIdx.x];
+      B.best_energy[32 * w + threadIdx.x] = be_s[threadIdx.x];
+      if (PT && B.stats) {  // one item per word in a launch: plain read-modify-write
+        B.stats[32 * w + threadIdx.x] += s1;
+        B.stats[32 * (B.W + w) + threadIdx.x] += s2;
+      }
+    }
+    group_sync<CS>();
+  }
+}
+
 
 template <int KQ, int CS, int TL, bool PT>
 __global__ void __launch_bounds__(kBatchThreads, 1)
