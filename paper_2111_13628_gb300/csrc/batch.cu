@@ -88,7 +88,7 @@ __device__ __forceinline__ void add_planes(uint32_t (&c)[NB], const uint32_t (&p
 template <int KQ, bool PT>
 __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint32_t *xs,
                                                   const uint32_t *tab_s, int tab_len,
-                                                  const uint32_t *mult_s, int c, int c0, int v,
+                                                  const uint32_t *mult_s, int cg, int c0, int v,
                                                   int t, uint32_t (&acc)[kAccPlanes]) {
   constexpr int NB = 7;
   const uint32_t x = xs[v];
@@ -101,7 +101,7 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
     mc[j] = 0u;
   }
   const int off = v - c0;
-  const int g = __ldg(B.cgrp + c) + (off >> 5), ln = off & 31;
+  const int g = cg + (off >> 5), ln = off & 31;  // cg: the class's first group
   const int gb = __ldg(B.grp_base + g);
   const int len = (__ldg(B.grp_base + g + 1) - gb) / (32 * KQ);
   const int4 *ent = B.occ_t + gb + ln;
@@ -219,7 +219,7 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
 template <int KQ, int TL, bool PT>
 __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint32_t *xs,
                                                  const uint32_t *tab_s, int tab_len,
-                                                 const uint32_t *mult_s, int c, int c0, int v,
+                                                 const uint32_t *mult_s, int cg, int c0, int v,
                                                  bool active, int t, int tl,
                                                  int (&acc)[32 / TL]) {
   constexpr int NB = 7;
@@ -237,7 +237,7 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
   const int4 *ent = nullptr;
   if (active && !frozen) {
     const int off = v - c0;
-    const int g = __ldg(B.cgrp + c) + (off >> 5), ln = off & 31;
+    const int g = cg + (off >> 5), ln = off & 31;  // cg: the class's first group
     const int gb = __ldg(B.grp_base + g);
     len = (__ldg(B.grp_base + g + 1) - gb) / (32 * KQ);
     ent = B.occ_t + gb + ln;
@@ -392,7 +392,7 @@ __device__ __forceinline__ T *rank_ptr(T *p, int r) {
 // replicas' energy changes to ep_s. Warps with no team in range skip the class.
 template <int KQ, int CS, int TT, bool PT>
 __device__ __forceinline__ void class_teams(const BatchItem &B, uint32_t *xs, const uint32_t *tab_s,
-                                            int tab_len, const uint32_t *mult_s, int c, int c0,
+                                            int tab_len, const uint32_t *mult_s, int cg, int c0,
                                             int cnt, int rank, int t, int *ep_s) {
   const int lane = threadIdx.x & 31;
   if ((int)(threadIdx.x & ~31u) / TT >= cnt) return;  // the whole warp
@@ -402,7 +402,7 @@ __device__ __forceinline__ void class_teams(const BatchItem &B, uint32_t *xs, co
   int tacc[32 / TT];
 #pragma unroll
   for (int i = 0; i < 32 / TT; ++i) tacc[i] = 0;
-  const uint32_t xn = attempt_team<KQ, TT, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, v, active, t, tl, tacc);
+  const uint32_t xn = attempt_team<KQ, TT, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, v, active, t, tl, tacc);
   if (active && tl == 0) {
     if (CS == 1) {
       xs[v] = xn;
@@ -463,23 +463,30 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
       uint32_t acc[kAccPlanes];
 #pragma unroll
       for (int j = 0; j < kAccPlanes; ++j) acc[j] = 0u;
+      // class bounds and first group: those of class c + 1 are requested during class c and
+      // arrive behind its barrier
+      int c0 = __ldg(B.col_ptr), c1 = __ldg(B.col_ptr + 1), cg = __ldg(B.cgrp);
       for (int c = 0; c < B.n_colours; ++c) {
-        const int c0 = __ldg(B.col_ptr + c), c1 = __ldg(B.col_ptr + c + 1);
+        int c2 = 0, cgn = 0;
+        if (c + 1 < B.n_colours) {
+          c2 = __ldg(B.col_ptr + c + 2);
+          cgn = __ldg(B.cgrp + c + 1);
+        }
         // the class's 32-variable groups are dealt round-robin to the cluster's CTAs
         const int cnt = share_count<CS>(c0, c1, rank);
         if (cnt <= kBatchThreads / 2) {
           // a smaller share (the later colour classes): teams of 8, 4 or 2 lanes per variable
           // shorten the class's critical path; their energy changes go to ep_s directly
           if (cnt <= kBatchThreads / 8)
-            class_teams<KQ, CS, 8, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, cnt, rank, t, ep_s);
+            class_teams<KQ, CS, 8, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, cnt, rank, t, ep_s);
           else if (cnt <= kBatchThreads / 4)
-            class_teams<KQ, CS, 4, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, cnt, rank, t, ep_s);
+            class_teams<KQ, CS, 4, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, cnt, rank, t, ep_s);
           else
-            class_teams<KQ, CS, 2, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, cnt, rank, t, ep_s);
+            class_teams<KQ, CS, 2, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, cnt, rank, t, ep_s);
         } else {
           for (int li = threadIdx.x; li < cnt; li += blockDim.x) {
             const int v = share_var<CS>(c0, rank, li);
-            const uint32_t xn = attempt_batch<KQ, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, v, t, acc);
+            const uint32_t xn = attempt_batch<KQ, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, v, t, acc);
             if (CS == 1) {
               xs[v] = xn;
             } else {
@@ -490,6 +497,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
           }
         }
         group_sync<CS>();
+        c0 = c1;
+        c1 = c2;
+        cg = cgn;
       }
       // per-replica sums of this sweep: planes -> 16-bit values (two byte transposes per block
       // of 8 replicas), then a warp reduction per replica
@@ -598,7 +608,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 #pragma unroll
       for (int i = 0; i < 32 / TL; ++i) acc[i] = 0;
       for (int c = 0; c < B.n_colours; ++c) {
-        const int c0 = __ldg(B.col_ptr + c), c1 = __ldg(B.col_ptr + c + 1);
+        const int c0 = __ldg(B.col_ptr + c), c1 = __ldg(B.col_ptr + c + 1), cg = __ldg(B.cgrp + c);
         // contiguous shares here (measured: round-robin groups are slower for the teams)
         const int part = ((c1 - c0 + CS - 1) / CS + 31) & ~31;
         const int v0 = c0 + rank * part, v1 = min(c1, v0 + part);
@@ -607,7 +617,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
           const int v = vw + (lane / TL);
           const bool active = v < v1;
           const uint32_t xn =
-              attempt_team<KQ, TL, PT>(B, xs, tab_s, tab_len, mult_s, c, c0, v, active, t, tl, acc);
+              attempt_team<KQ, TL, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, v, active, t, tl, acc);
           if (active && tl == 0) {
             if (CS == 1) {
               xs[v] = xn;
