@@ -246,6 +246,28 @@ int set_ctx_error(nmc_ctx *ctx, int code, const char *msg) {
   return code;
 }
 
+// Mean colour-class size of a k-SAT instance (variables per class, rounded up).
+int class_size(const Instance &I) { return (I.ks.n + I.ks.n_colours - 1) / std::max(1, I.ks.n_colours); }
+
+// CTAs per work item: few items are spread over the SMs (each cluster keeps its own copy of the
+// word vector), but a colour class is not split below about 32 variables per CTA, where a
+// cluster barrier per class costs more than the work it spreads (measured: 4-SAT N = 200 with 64
+// replicas, 43 us per sweep on one CTA per word against 78 on eight; N = 1,000 with 256, 82
+// against 105 on eight; N = 5,000 with 1,024 keeps four, 132 us).
+int choose_ctas(int sms, long long cnt, int per_class) {
+  int cs = 1;
+  while (cs < 8 && cnt * cs * 2 <= sms && per_class >= 64 * cs) cs *= 2;
+  return cs;
+}
+
+// Lanes per variable for about per_class / cs variables of a class on each CTA: teams of 8 up
+// to ~24, of 4 up to ~100, single threads beyond (the one-thread kernel still runs its smaller
+// classes with teams).
+int choose_lanes(int cs, int per_class) {
+  const int per_cta = per_class / cs;
+  return per_cta <= 24 ? 8 : (per_cta <= 100 ? 4 : 1);
+}
+
 int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
                const int32_t *t1, BatchPlan *plan) {
   if (!ctx || !plan) return NMC_EINVAL;
@@ -256,6 +278,7 @@ int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t
   std::vector<long long> cost[2];
   std::map<int32_t, int> seen;
   plan->max_n[0] = plan->max_n[1] = 0;
+  int per_class[2] = {0, 0};  // largest mean colour-class size among the items
   for (int32_t i = 0; i < n_sets; ++i) {
     ReplicaSet *S = find_set(ctx, rs[i]);
     if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set in batch");
@@ -294,6 +317,7 @@ int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t
       cost[q].push_back(static_cast<long long>(I->ks.n_occ + I->ks.n) * (t1[i] - t0[i]));
       if (I->ks.n > plan->max_n[q]) plan->max_n[q] = I->ks.n;
     }
+    per_class[q] = std::max(per_class[q], class_size(*I));
   }
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
@@ -317,7 +341,8 @@ int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t
       cs = tuned->second.first;
       lanes = tuned->second.second;
     } else {
-      while (cs < 8 && static_cast<long long>(plan->cnt[q]) * cs * 2 <= sms) cs *= 2;
+      cs = choose_ctas(sms, plan->cnt[q], per_class[q]);
+      lanes = choose_lanes(cs, per_class[q]);
     }
     if (cs != 1 && cs != 2 && cs != 4 && cs != 8) cs = 1;
     plan->cs[q] = cs;
@@ -393,34 +418,26 @@ BatchItem ksat_item(const Instance &I, const ReplicaSet &S, int32_t w, int32_t t
   return B;
 }
 
-// CTAs per work item and lanes per variable for a launch of `cnt` items of one instance (a
+// CTAs per work item and lanes per variable for a launch of the `cnt` items of one instance (a
 // tuned shape when the context has one, else as batch_plan chooses).
-void tuned_shape(nmc_ctx *ctx, int kq, int max_n, int cnt, int *cs, int *lanes);
-
-// CTAs per work item for a launch of `cnt` items (as batch_plan chooses).
-int ctas_per_item(nmc_ctx *ctx, long long cnt) {
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
-    cudaGetLastError();
-    sms = 1;
-  }
-  int cs = 1;
-  if (const char *env = getenv("NMC_BATCH_CTAS")) cs = atoi(env);
-  else
-    while (cs < 8 && cnt * cs * 2 <= sms) cs *= 2;
-  if (cs != 1 && cs != 2 && cs != 4 && cs != 8) cs = 1;
-  return cs;
-}
-
-void tuned_shape(nmc_ctx *ctx, int kq, int max_n, int cnt, int *cs, int *lanes) {
+void tuned_shape(nmc_ctx *ctx, const Instance &I, int cnt, int *cs, int *lanes) {
   *lanes = 0;
-  const auto t = ctx->tune.find(std::make_tuple(kq, max_n, cnt));
+  const auto t = ctx->tune.find(std::make_tuple(I.ks.kq, I.ks.n, cnt));
   if (!getenv("NMC_BATCH_CTAS") && t != ctx->tune.end()) {
     *cs = t->second.first;
     *lanes = t->second.second;
     return;
   }
-  *cs = ctas_per_item(ctx, cnt);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  int c = choose_ctas(sms, cnt, class_size(I));
+  if (const char *env = getenv("NMC_BATCH_CTAS")) c = atoi(env);
+  if (c != 1 && c != 2 && c != 4 && c != 8) c = 1;
+  *cs = c;
+  *lanes = choose_lanes(c, class_size(I));
 }
 
 // The checks every batched-kernel path makes on a k-SAT instance.
@@ -1400,7 +1417,7 @@ int nmc_replicas_run_pt(nmc_ctx *ctx, int32_t rs, int32_t t0, int32_t t1,
   const int32_t W = S->ks.W, L = S->pt_L, G = S->R / L, per = sweeps_per_round;
   const int kq = I->ks.kq;
   int cs = 1, lanes = 0;
-  tuned_shape(ctx, kq, I->ks.n, W, &cs, &lanes);
+  tuned_shape(ctx, *I, W, &cs, &lanes);
   // segments end at t1 or after sweep t with (t+1) % per == 0, where an exchange round follows;
   // their work items are uploaded in chunks
   const int64_t max_chunk_items = std::max<int64_t>(W, 1 << 18);
@@ -2013,7 +2030,7 @@ int nmc_adaptive_ladder(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t s
     int cnt[2] = {0, 0}, max_n[2] = {0, 0}, cs[2] = {1, 1}, lanes[2] = {0, 0};
     cnt[q] = W;
     max_n[q] = n;
-    tuned_shape(ctx, q + 1, n, W, &cs[q], &lanes[q]);
+    tuned_shape(ctx, *I, W, &cs[q], &lanes[q]);
     if ((e = fill_schedule(bq, static_cast<size_t>(n) * T, beta, ctx->flag, ctx->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(stats, 0, sizeof(long long) * 64 * W, ctx->stream)) != cudaSuccess) {
       rc = cuda_fail(ctx, e, "prepare ladder level");
