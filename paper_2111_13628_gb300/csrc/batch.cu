@@ -425,7 +425,7 @@ __device__ __forceinline__ void class_teams(const BatchItem &B, uint32_t *xs, co
 template <int KQ, int CS, bool PT>
 __global__ void __launch_bounds__(kBatchThreads, 1)
     ksat_batch_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
-                      const uint32_t *tab, int tab_len, int xs_words) {
+                      const uint32_t *tab, int tab_len, int xs_words, int small_teams) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t *xs = smem;                               // word vector first (byte offsets in lists)
   uint32_t *tab_s = smem + ((xs_words + 31) & ~31);  // then the acceptance table
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
         }
         // the class's 32-variable groups are dealt round-robin to the cluster's CTAs
         const int cnt = share_count<CS>(c0, c1, rank);
-        if (cnt <= kBatchThreads / 2) {
+        if (small_teams && cnt <= kBatchThreads / 2) {
           // a smaller share (the later colour classes): teams of 8, 4 or 2 lanes per variable
           // shorten the class's critical path; their energy changes go to ep_s directly
           if (cnt <= kBatchThreads / 8)
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 template <int KQ, int CS, int TL, bool PT>
 __global__ void __launch_bounds__(kBatchThreads, 1)
     ksat_team_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
-                     const uint32_t *tab, int tab_len, int xs_words) {
+                     const uint32_t *tab, int tab_len, int xs_words, int small_teams) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t *xs = smem;                               // word vector first (byte offsets in lists)
   uint32_t *tab_s = smem + ((xs_words + 31) & ~31);  // then the acceptance table
@@ -678,6 +678,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     group_sync<CS>();
   }
   (void)team;
+  (void)small_teams;
 }
 
 // The launch shape of each kernel instance is queried once per (device, shared-memory size):
@@ -691,6 +692,7 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
   auto kern = TL == 1 ? ksat_batch_kernel<KQ, CS, PT> : ksat_team_kernel<KQ, CS, (TL > 1 ? TL : 4), PT>;
   static std::mutex mu;
   static std::map<std::pair<int, size_t>, int> shapes;  // (device, smem) -> resident clusters
+  static std::map<int, int> sm_count;                    // device -> SMs
   static std::map<int, size_t> smem_set;                // device -> largest smem attribute set
   int clusters = 0;
   {
@@ -733,6 +735,22 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
     }
   }
   if (clusters < 1) return cudaErrorInvalidConfiguration;
+  int sms = 0;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = sm_count.find(device);
+    if (it == sm_count.end()) {
+      cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+      if (err != cudaSuccess) return err;
+      sm_count[device] = sms;
+    } else {
+      sms = it->second;
+    }
+  }
+  // Teams of lanes for the smaller colour classes shorten a class's critical path; they pay
+  // off when each SM runs one CTA of the launch (latency-bound), not when many items queue
+  // behind each other (measured on a 256-instance batch: 3% slower with them).
+  const int small_teams = (long long)n_items * CS <= sms ? 1 : 0;
   if (clusters > n_items) clusters = n_items;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kBatchThreads);
@@ -748,7 +766,7 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
   cfg.gridDim = dim3(clusters * CS);
   cudaError_t err = cudaMemsetAsync(next_item, 0, sizeof(int), st);
   if (err != cudaSuccess) return err;
-  return cudaLaunchKernelEx(&cfg, kern, items, n_items, next_item, tab, tab_len, xs_words);
+  return cudaLaunchKernelEx(&cfg, kern, items, n_items, next_item, tab, tab_len, xs_words, small_teams);
 }
 
 // Lanes per variable of the batched kernel: 1 (one thread per variable) or a team of 4 or 8.
