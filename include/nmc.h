@@ -198,8 +198,10 @@ int nmc_batch_run_noalloc(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const
  */
 int nmc_batch_autotune(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, int32_t t0,
                        int32_t sweeps, int32_t *shapes_out);
-/* Batched QAP steps: runs steps t0[i]..t1[i]-1 of QAP replica sets rs[i] in one launch (one CTA
- * per block of 32 replicas), asynchronously; results as nmc_replicas_run on each set alone. */
+/* Batched QAP steps: runs steps t0[i]..t1[i]-1 of QAP replica sets rs[i], one CTA per block of
+ * 32 replicas, one launch per launch shape (the sets' sizes pick the shapes); the shapes run side
+ * by side on internal streams forked from the context's stream and joined back to it, so the call
+ * stays asynchronous and ordered on that stream. Results as nmc_replicas_run on each set alone. */
 int nmc_qap_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
                       const int32_t *t1);
 /* Largest n_vars nmc_batch_run accepts on this context's device. */

@@ -83,6 +83,11 @@ struct nmc_ctx {
   int32_t *next_item = nullptr;  // two work counters (one per occurrence width)
   QapArgs *qitems = nullptr;     // batched QAP work list (grown on demand)
   size_t qitems_cap = 0;
+  // auxiliary streams of the batched QAP launches (one per launch shape, created on first use):
+  // forked from the context's stream after the work-list upload and joined back by events
+  cudaStream_t qaux[kQapShapes] = {};
+  cudaEvent_t qfork = nullptr;
+  cudaEvent_t qjoin[kQapShapes] = {};
   // tuned batched-sweep shapes: (occurrence width, largest n, work items) -> (cs, lanes)
   std::map<std::tuple<int, int, int>, std::pair<int, int>> tune;
 };
@@ -505,6 +510,14 @@ void nmc_destroy(nmc_ctx *ctx) {
   dev_free(ctx->items);
   dev_free(ctx->next_item);
   dev_free(ctx->qitems);
+  for (int q = 0; q < kQapShapes; ++q) {
+    if (ctx->qaux[q]) {
+      cudaStreamSynchronize(ctx->qaux[q]);
+      cudaStreamDestroy(ctx->qaux[q]);
+    }
+    if (ctx->qjoin[q]) cudaEventDestroy(ctx->qjoin[q]);
+  }
+  if (ctx->qfork) cudaEventDestroy(ctx->qfork);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaGetLastError();
   delete ctx;
@@ -843,6 +856,91 @@ int upload_ksat(nmc_ctx *ctx, HostKsat &h, int32_t *inst_out) {
   return NMC_OK;
 }
 
+
+}  // namespace nmc
+
+namespace nmc {
+
+int qap_batch_join(nmc_ctx *ctx, uint32_t joins) {
+  if (!ctx) return NMC_EINVAL;
+  cudaError_t err = cudaSuccess;
+  for (int q = 0; q < kQapShapes; ++q)
+    if (joins & (1u << q)) {
+      const cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->qjoin[q], 0);
+      if (err == cudaSuccess) err = e;
+    }
+  return err == cudaSuccess ? NMC_OK : cuda_fail(ctx, err, "join QAP streams");
+}
+
+int qap_batch_enqueue(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
+                      const int32_t *t1, uint32_t *joins) {
+  *joins = 0;
+  if (!ctx) return NMC_EINVAL;
+  if (n_sets < 0 || (n_sets > 0 && (!rs || !t0 || !t1)))
+    return fail(ctx, NMC_EINVAL, "bad batch arrays");
+  DeviceGuard g(ctx->device);
+  std::vector<QapArgs> by_npl[kQapShapes];
+  int max_n[kQapShapes] = {0};
+  std::map<int32_t, int> seen;
+  for (int32_t i = 0; i < n_sets; ++i) {
+    ReplicaSet *S = find_set(ctx, rs[i]);
+    if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set in batch");
+    if (seen[rs[i]]++) return fail(ctx, NMC_EINVAL, "replica set repeated in batch");
+    Instance *I = find_inst(ctx, S->inst);
+    if (!I || I->kind != NMC_KIND_QAP) return fail(ctx, NMC_EINVAL, "batch sets must be QAP");
+    if (t0[i] < 0 || t1[i] < t0[i]) return fail(ctx, NMC_EINVAL, "need 0 <= t0 <= t1");
+    if (t1[i] > t0[i] && (!I->bq || t1[i] > I->n_steps))
+      return fail(ctx, NMC_ESTATE, "schedule missing or shorter than t1");
+    if (t1[i] == t0[i]) continue;
+    const int n = I->qp.n;
+    const int q = qap_shape(n);
+    for (int b = 0; b < (S->R + 31) / 32; ++b)
+      by_npl[q].push_back(qap_block_args(I->qp, S->qp, I->bq, ctx->tab, ctx->tab_len, t0[i], t1[i],
+                                         S->seed, b));
+    max_n[q] = std::max(max_n[q], n);
+  }
+  size_t total = 0;
+  for (int q = 0; q < kQapShapes; ++q) total += by_npl[q].size();
+  if (total == 0) return NMC_OK;
+  if (total > ctx->qitems_cap) {
+    NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    dev_free(ctx->qitems);
+    ctx->qitems_cap = 0;
+    NMC_CUDA(dev_alloc(&ctx->qitems, total), "allocate QAP work list");
+    ctx->qitems_cap = total;
+  }
+  std::vector<QapArgs> all;
+  all.reserve(total);
+  size_t off[kQapShapes];
+  for (int q = 0; q < kQapShapes; ++q) {
+    off[q] = all.size();
+    all.insert(all.end(), by_npl[q].begin(), by_npl[q].end());
+  }
+  NMC_CUDA(cudaMemcpyAsync(ctx->qitems, all.data(), sizeof(QapArgs) * total, cudaMemcpyHostToDevice,
+                           ctx->stream),
+           "upload QAP work list");
+  // every launch shape on its own stream after the upload, so that shapes with few blocks run
+  // side by side (and beside whatever the caller enqueues on its stream before the join)
+  if (!ctx->qfork) {
+    for (int q = 0; q < kQapShapes; ++q) {
+      NMC_CUDA(cudaStreamCreateWithFlags(&ctx->qaux[q], cudaStreamNonBlocking), "create QAP stream");
+      NMC_CUDA(cudaEventCreateWithFlags(&ctx->qjoin[q], cudaEventDisableTiming), "create QAP event");
+    }
+    NMC_CUDA(cudaEventCreateWithFlags(&ctx->qfork, cudaEventDisableTiming), "create QAP event");
+  }
+  NMC_CUDA(cudaEventRecord(ctx->qfork, ctx->stream), "fork QAP streams");
+  cudaError_t err = cudaSuccess;
+  for (int q = 0; q < kQapShapes && err == cudaSuccess; ++q) {
+    if (by_npl[q].empty()) continue;
+    if ((err = cudaStreamWaitEvent(ctx->qaux[q], ctx->qfork, 0)) != cudaSuccess) break;
+    err = qap_batch(ctx->qitems + off[q], static_cast<int>(by_npl[q].size()), q, max_n[q],
+                    ctx->tab_len, ctx->qaux[q]);
+    const cudaError_t e2 = cudaEventRecord(ctx->qjoin[q], ctx->qaux[q]);
+    if (e2 == cudaSuccess) *joins |= 1u << q;  // launched (or failed): joined all the same
+    if (err == cudaSuccess) err = e2;
+  }
+  return err == cudaSuccess ? NMC_OK : cuda_fail(ctx, err, "launch batched QAP");
+}
 
 }  // namespace nmc
 
@@ -1224,56 +1322,10 @@ int nmc_replicas_read_device(nmc_ctx *ctx, int32_t rs, const nmc_result *out_dev
 int nmc_qap_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
                       const int32_t *t1) {
   if (!ctx) return NMC_EINVAL;
-  if (n_sets < 0 || (n_sets > 0 && (!rs || !t0 || !t1)))
-    return fail(ctx, NMC_EINVAL, "bad batch arrays");
-  DeviceGuard g(ctx->device);
-  std::vector<QapArgs> by_npl[kQapShapes];
-  int max_n[kQapShapes] = {0};
-  std::map<int32_t, int> seen;
-  for (int32_t i = 0; i < n_sets; ++i) {
-    ReplicaSet *S = find_set(ctx, rs[i]);
-    if (!S) return fail(ctx, NMC_EINVAL, "unknown replica set in batch");
-    if (seen[rs[i]]++) return fail(ctx, NMC_EINVAL, "replica set repeated in batch");
-    Instance *I = find_inst(ctx, S->inst);
-    if (!I || I->kind != NMC_KIND_QAP) return fail(ctx, NMC_EINVAL, "batch sets must be QAP");
-    if (t0[i] < 0 || t1[i] < t0[i]) return fail(ctx, NMC_EINVAL, "need 0 <= t0 <= t1");
-    if (t1[i] > t0[i] && (!I->bq || t1[i] > I->n_steps))
-      return fail(ctx, NMC_ESTATE, "schedule missing or shorter than t1");
-    if (t1[i] == t0[i]) continue;
-    const int n = I->qp.n;
-    const int q = qap_shape(n);
-    for (int b = 0; b < (S->R + 31) / 32; ++b)
-      by_npl[q].push_back(qap_block_args(I->qp, S->qp, I->bq, ctx->tab, ctx->tab_len, t0[i], t1[i],
-                                         S->seed, b));
-    max_n[q] = std::max(max_n[q], n);
-  }
-  size_t total = 0;
-  for (int q = 0; q < kQapShapes; ++q) total += by_npl[q].size();
-  if (total == 0) return NMC_OK;
-  if (total > ctx->qitems_cap) {
-    NMC_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
-    dev_free(ctx->qitems);
-    ctx->qitems_cap = 0;
-    NMC_CUDA(dev_alloc(&ctx->qitems, total), "allocate QAP work list");
-    ctx->qitems_cap = total;
-  }
-  std::vector<QapArgs> all;
-  all.reserve(total);
-  size_t off[kQapShapes];
-  for (int q = 0; q < kQapShapes; ++q) {
-    off[q] = all.size();
-    all.insert(all.end(), by_npl[q].begin(), by_npl[q].end());
-  }
-  NMC_CUDA(cudaMemcpyAsync(ctx->qitems, all.data(), sizeof(QapArgs) * total, cudaMemcpyHostToDevice,
-                           ctx->stream),
-           "upload QAP work list");
-  for (int q = 0; q < kQapShapes; ++q) {
-    if (by_npl[q].empty()) continue;
-    NMC_CUDA(qap_batch(ctx->qitems + off[q], static_cast<int>(by_npl[q].size()), q, max_n[q],
-                       ctx->tab_len, ctx->stream),
-             "launch batched QAP");
-  }
-  return NMC_OK;
+  uint32_t joins = 0;
+  const int rc = nmc::qap_batch_enqueue(ctx, n_sets, rs, t0, t1, &joins);
+  const int rcj = nmc::qap_batch_join(ctx, joins);
+  return rc != NMC_OK ? rc : rcj;
 }
 
 int32_t nmc_batch_max_vars(nmc_ctx *ctx) {

@@ -277,6 +277,13 @@ QapArgs qap_block_args(const QapDevice &I, QapReplicas &Rp, const uint32_t *bq, 
 // replica and facilities per lane); a batched launch takes items of one shape.
 constexpr int kQapShapes = 12;
 int qap_shape(int n);
+// The batched QAP launches of these sets (as nmc_qap_batch_run does them), each launch shape on
+// an auxiliary stream forked from the context's stream after the work-list upload; *joins gets
+// the streams to join. qap_batch_join makes the context's stream wait for them; call it also
+// after an error, so that nothing launched is left unjoined.
+int qap_batch_enqueue(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
+                      const int32_t *t1, uint32_t *joins);
+int qap_batch_join(nmc_ctx *ctx, uint32_t joins);
 // Runs n_blocks QAP replica blocks (items_dev[b] for CTA b) in one launch; every item has
 // qap_shape(n) == shape, and max_n (the largest n) sizes the shared memory.
 cudaError_t qap_batch(const QapArgs *items_dev, int n_blocks, int shape, int max_n, int tab_len,

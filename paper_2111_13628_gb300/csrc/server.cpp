@@ -6,7 +6,8 @@
 //      will hold stay within the configured limits (instance, schedule and replica state are
 //      then resident on the device until the request finishes);
 //   2. advance every active request by one slice of sweeps in a single batched launch (k-SAT
-//      words of all requests share the persistent kernel; QAP requests follow on the stream),
+//      words of all requests share the persistent kernel; the QAP launch shapes run beside it
+//      on auxiliary streams),
 //      the slice sized so that every request gets about the same amount of work per tick;
 //   3. read back and release the requests that reached the end of their schedule.
 // A request that arrives while others run joins at the next tick. Because sweeps are
@@ -199,11 +200,16 @@ void worker_loop(nmc_server *s) {
       tick_attempts += static_cast<int64_t>(t1 - r->t) * r->n * r->replicas;
       r->t = t1;
     }
+    // QAP shapes on their own streams first, then the k-SAT launch on the context's stream:
+    // the two run side by side and are joined before the tick's synchronisation
+    uint32_t qjoin = 0;
+    if (rc == NMC_OK && !qrs.empty())
+      rc = nmc::qap_batch_enqueue(s->ctx, static_cast<int32_t>(qrs.size()), qrs.data(), qa.data(),
+                                  qb.data(), &qjoin);
     if (rc == NMC_OK && !rs.empty())
       rc = nmc_batch_run(s->ctx, static_cast<int32_t>(rs.size()), rs.data(), a.data(), b.data());
-    if (rc == NMC_OK && !qrs.empty())
-      rc = nmc_qap_batch_run(s->ctx, static_cast<int32_t>(qrs.size()), qrs.data(), qa.data(),
-                             qb.data());
+    const int rcj = nmc::qap_batch_join(s->ctx, qjoin);
+    if (rc == NMC_OK) rc = rcj;
     if (rc == NMC_OK) rc = nmc_sync(s->ctx);
     const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
     if (rc != NMC_OK) {
