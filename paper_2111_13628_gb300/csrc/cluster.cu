@@ -4,10 +4,12 @@
 //
 // Three launches on multi-spin-coded words (32 replicas per uint32):
 //  1. the mask, host bytes in original variable order, packed to words mb[v][w] (new ids);
-//  2. dE of every replica: each thread evaluates a share of the clauses of one word, old and
-//     proposed (literal words xor the mask words), counts the clauses that become violated and
-//     those that become satisfied in bit-sliced counters, and the per-replica differences are
-//     reduced over the warp and the grid;
+//  2. dE of every replica: a warp takes a run of clauses and its lane l the replica word
+//     32 gy + l (grid row gy), so every literal's state and mask words are read as one
+//     coalesced 128-byte row per warp; each lane evaluates the clauses old and proposed (literal
+//     words xor the mask words), counts those that become violated and those that become
+//     satisfied in bit-sliced counters, and the per-replica differences are summed in shared
+//     memory and added to dE once per block;
 //  3. acceptance per replica (Philox counter (move_id, 0, r>>2, "CLST"), word r&3), energies
 //     and best energies, then the accepted flips and best-state copies applied word by word.
 #include "bits.cuh"
@@ -18,8 +20,8 @@ namespace nmc {
 
 namespace {
 
-constexpr int kDeltaThreads = 256;
-constexpr int kClausesPerThread = 64;  // counts <= 64 fit the 8 bit planes below
+constexpr int kDeltaWarps = 8;
+constexpr int kClausesPerWarp = 128;  // counts <= 128 fit the 8 bit planes below
 
 __global__ void pack_mask_kernel(const uint8_t *__restrict__ mask, int32_t rows, int32_t n,
                                  int32_t R, int32_t W, const int32_t *__restrict__ orig,
@@ -53,35 +55,39 @@ __device__ __forceinline__ void inc8(uint32_t (&c)[8], uint32_t b) {
   }
 }
 
-// grid (clause blocks, W): dE[32w + j] += sum over this thread's clauses of (becomes violated)
-// - (becomes satisfied) for replica j of word w.
-__global__ void __launch_bounds__(kDeltaThreads)
+// grid (clause runs, ceil(W / 32)): dE[32w + j] += sum over the block's clauses of (becomes
+// violated) - (becomes satisfied) for replica j of word w.
+__global__ void __launch_bounds__(kDeltaWarps * 32)
     cluster_delta_kernel(const int32_t *__restrict__ clits, int32_t m, int32_t kmax,
                          const uint32_t *__restrict__ S, const uint32_t *__restrict__ mb,
                          int32_t W, int32_t *dE) {
-  __shared__ int part[32];
-  const int w = blockIdx.y;
-  if (threadIdx.x < 32) part[threadIdx.x] = 0;
+  __shared__ int part[32 * 33];  // [word lane][replica], rows padded against bank conflicts
+  for (int i = threadIdx.x; i < 32 * 33; i += blockDim.x) part[i] = 0;
   __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = 32 * (int)blockIdx.y + lane;
+  const bool wok = w < W;
+  const long long a0 = ((long long)blockIdx.x * kDeltaWarps + warp) * kClausesPerWarp;
+  const long long a1 = a0 + kClausesPerWarp < (long long)m ? a0 + kClausesPerWarp : (long long)m;
   uint32_t up[8], down[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     up[j] = 0u;
     down[j] = 0u;
   }
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < m; a += stride) {
+  for (long long a = a0; a < a1; ++a) {
     uint32_t o = 0u, on = 0u;
     for (int q = 0; q < kmax; ++q) {
-      const int l = __ldg(clits + (size_t)a * kmax + q);  // literal id 2v + neg (pad 2n)
-      const uint32_t lw = __ldg(S + (size_t)l * W + w);
-      o |= lw;
-      on |= lw ^ __ldg(mb + (size_t)(l >> 1) * W + w);
+      const int l = __ldg(clits + (size_t)a * kmax + q);  // literal id 2v + neg (pad 2n): warp-uniform
+      if (wok) {
+        const uint32_t lw = __ldg(S + (size_t)l * W + w);
+        o |= lw;
+        on |= lw ^ __ldg(mb + (size_t)(l >> 1) * W + w);
+      }
     }
     inc8(up, o & ~on);    // satisfied -> violated: +1
     inc8(down, ~o & on);  // violated -> satisfied: -1
   }
-  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const unsigned long long xu = transpose8(gather_bytes(up, q));
@@ -89,12 +95,15 @@ __global__ void __launch_bounds__(kDeltaThreads)
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int val = (int)((xu >> (8 * i)) & 0xFFull) - (int)((xd >> (8 * i)) & 0xFFull);
-      const int s = __reduce_add_sync(0xFFFFFFFFu, val);
-      if (lane == 0 && s != 0) atomicAdd(&part[8 * q + i], s);
+      if (val != 0) atomicAdd(&part[lane * 33 + 8 * q + i], val);
     }
   }
   __syncthreads();
-  if (threadIdx.x < 32 && part[threadIdx.x] != 0) atomicAdd(&dE[32 * w + threadIdx.x], part[threadIdx.x]);
+  for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+    const int wl = i >> 5, j = i & 31, ww = 32 * (int)blockIdx.y + wl;
+    const int v = part[wl * 33 + j];
+    if (ww < W && v != 0) atomicAdd(&dE[32 * ww + j], v);
+  }
 }
 
 // One thread per replica lane of every word (whole warps = whole words).
@@ -185,9 +194,9 @@ cudaError_t ksat_cluster_flip(const KsatDevice &I, KsatReplicas &Rp, const uint8
                                                                          W, I.orig, mb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (I.m > 0) {
-    const long long per_block = (long long)kDeltaThreads * kClausesPerThread;
-    const dim3 grid((unsigned)((I.m + per_block - 1) / per_block), (unsigned)W);
-    cluster_delta_kernel<<<grid, kDeltaThreads, 0, st>>>(I.clits, I.m, I.kmax, Rp.S, mb, W, dE);
+    const long long per_block = (long long)kDeltaWarps * kClausesPerWarp;
+    const dim3 grid((unsigned)((I.m + per_block - 1) / per_block), (unsigned)((W + 31) / 32));
+    cluster_delta_kernel<<<grid, kDeltaWarps * 32, 0, st>>>(I.clits, I.m, I.kmax, Rp.S, mb, W, dE);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   cluster_accept_kernel<<<(unsigned)((32 * (long long)W + 255) / 256), 256, 0, st>>>(
