@@ -3,8 +3,10 @@
 // when it is neither satisfied by another of its variables nor holds another white variable
 // (generalized form: and it is satisfied by v itself, so violated clauses never report a frozen
 // variable). White sets only grow and the blocking test is monotone in them, so the parallel
-// rounds used here (every variable tested against the previous round's white set) reach the same
-// fixed point as inspecting one variable at a time. Frozen = not white at the fixed point.
+// rounds used here (every variable tested against the white set as it stands, the words updated
+// in place, so a round may already use bits set earlier in it) reach the same least fixed point
+// as inspecting one variable at a time: every bit set is justified by bits of that fixed point,
+// and a round that sets nothing certifies it. Frozen = not white at the fixed point.
 //
 // Per (variable v, word w) and occurrence (clause a): own = truth word of v's literal in a, o =
 // OR of the other literals' truth words (rows of the state array S), so = OR of the other
@@ -18,20 +20,18 @@ namespace {
 
 constexpr int kWhiteBlock = 256;
 
+// star: the white words, read and updated in place (one writer per word; a read sees the old or
+// the new word, both below the fixed point).
 template <int KQ>
 __global__ void white_round_kernel(const int4 *__restrict__ occ, const int32_t *__restrict__ occ_ptr,
                                    const uint32_t *__restrict__ X, int32_t xrows2, int32_t n,
-                                   int32_t W, const uint32_t *__restrict__ star, uint32_t *star_new,
-                                   int generalized, int32_t *changed) {
+                                   int32_t W, uint32_t *star, int generalized, int32_t *changed) {
   const long long total = (long long)n * W;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int v = (int)(i / W), w = (int)(i % W);
     const uint32_t s0 = star[i];
-    if (s0 == 0xFFFFFFFFu) {
-      star_new[i] = s0;
-      continue;
-    }
+    if (s0 == 0xFFFFFFFFu) continue;
     // truth word of literal id l (2u + neg): the state row of u, complemented when negated; the
     // padding literals 2n (false) and 2n+1 (true) address the constant rows / zero star row n
     auto lit = [&](int l) -> uint32_t {
@@ -56,8 +56,10 @@ __global__ void white_round_kernel(const int4 *__restrict__ occ, const int32_t *
       blocked |= b;
     }
     const uint32_t s1 = s0 | ~blocked;
-    star_new[i] = s1;
-    if (s1 != s0) *changed = 1;
+    if (s1 != s0) {
+      star[i] = s1;
+      *changed = 1;
+    }
   }
 }
 
@@ -110,7 +112,7 @@ unsigned white_blocks(long long work) {
 
 size_t whitening_scratch_bytes(int32_t n, int32_t W) {
   auto up = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
-  return 2 * up(sizeof(uint32_t) * (size_t)(n + 1) * W) + up(sizeof(int32_t));
+  return up(sizeof(uint32_t) * (size_t)(n + 1) * W) + up(sizeof(int32_t));
 }
 
 int whitening_run(const KsatDevice &I, const uint32_t *X, int32_t xrows2, int32_t R, int32_t W,
@@ -120,30 +122,25 @@ int whitening_run(const KsatDevice &I, const uint32_t *X, int32_t xrows2, int32_
   const int32_t n = I.n;
   char *p = static_cast<char *>(scratch);
   uint32_t *a = reinterpret_cast<uint32_t *>(p); p += up(sizeof(uint32_t) * (size_t)(n + 1) * W);
-  uint32_t *b = reinterpret_cast<uint32_t *>(p); p += up(sizeof(uint32_t) * (size_t)(n + 1) * W);
   int32_t *changed = reinterpret_cast<int32_t *>(p);
   cudaError_t e;
-  // rows 0..n of both buffers start clear (row n: the padding literals' variable, never white)
-  if ((e = cudaMemsetAsync(a, 0, sizeof(uint32_t) * (size_t)(n + 1) * W, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b, 0, sizeof(uint32_t) * (size_t)(n + 1) * W, st)) != cudaSuccess)
+  // rows 0..n start clear (row n: the padding literals' variable, never white)
+  if ((e = cudaMemsetAsync(a, 0, sizeof(uint32_t) * (size_t)(n + 1) * W, st)) != cudaSuccess)
     return (int)e;
   int32_t r = 0;
   for (; r <= n + 1; ++r) {
     if ((e = cudaMemsetAsync(changed, 0, sizeof(int32_t), st)) != cudaSuccess) return (int)e;
     if (I.kq == 1)
       white_round_kernel<1><<<white_blocks((long long)n * W), kWhiteBlock, 0, st>>>(
-          I.occ, I.occ_ptr, X, xrows2, n, W, a, b, generalized, changed);
+          I.occ, I.occ_ptr, X, xrows2, n, W, a, generalized, changed);
     else
       white_round_kernel<2><<<white_blocks((long long)n * W), kWhiteBlock, 0, st>>>(
-          I.occ, I.occ_ptr, X, xrows2, n, W, a, b, generalized, changed);
+          I.occ, I.occ_ptr, X, xrows2, n, W, a, generalized, changed);
     if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
     int32_t ch = 0;
     if ((e = cudaMemcpyAsync(&ch, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
       return (int)e;
-    uint32_t *t = a;
-    a = b;
-    b = t;
     if (!ch) break;
   }
   *rounds = r + 1;
