@@ -12,9 +12,11 @@
  * of the learning stage's exploratory runs.
  *
  * Dynamics (fixed here so that every result is reproducible bit for bit):
- *   - sweep order: greedy colouring of the variable-interaction graph in ascending variable
- *     id; one sweep visits colours in ascending order, every colour class (an independent
- *     set) updated against the state left by the earlier colours;
+ *   - sweep order: DSatur colouring of the variable-interaction graph (the uncoloured variable
+ *     whose coloured neighbours show the most distinct colours, then the one in more clauses,
+ *     then the smaller id, takes the smallest colour its neighbours leave free); one sweep
+ *     visits colours in ascending order, every colour class (an independent set) updated
+ *     against the state left by the earlier colours;
  *   - random numbers: Philox4x32-10 keyed by the 64-bit seed; replica r's attempt on variable
  *     v at sweep t uses word r&3 of the block for counter (v, t, r>>2, 0x4B535750);
  *   - acceptance: dE <= 0 always; otherwise with bq = round_half_even(beta * 2^16) and

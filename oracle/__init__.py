@@ -156,7 +156,7 @@ def ksat_delta(lits, n_vars: int, x, v: int) -> int:
 
 
 def ksat_colour(lits, n_vars: int):
-    """(colour int32[N], n_colours) of the greedy ascending-id colouring."""
+    """(colour int32[N], n_colours) of the DSatur colouring (the sweep order)."""
     lits, m, k = _cnf(lits)
     col = np.zeros(n_vars, dtype=np.int32)
     nc = _load().orc_ksat_colour(n_vars, m, k, _p(lits), _p(col))

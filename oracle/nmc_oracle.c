@@ -16,10 +16,13 @@
  *    of the system, Sec. "Nonequilibrium Nonlocal Monte Carlo"; two chains with the backbone
  *    heated 2-10x, Sec. "Nonequilibrium inhomogeneous sampling over subgraphs"): flip one
  *    variable v with its own beta_v[t]; accept with probability min(1, exp(-beta_v[t] dE)).
- *  Sweep order (the paper leaves a "sweep" undefined): greedy colouring of the
- *    variable-interaction graph in ascending id, colours visited in ascending order, each
- *    colour class (an independent set) updated against the state left by earlier colours.
- *    Within a class, ascending id (any order gives the same result).
+ *  Sweep order (the paper leaves a "sweep" undefined): a DSatur colouring of the
+ *    variable-interaction graph (Brelaz, CACM 1979: repeatedly colour the uncoloured variable
+ *    whose coloured neighbours show the most distinct colours, here ties broken by more clause
+ *    occurrences, then by the smaller id, giving it the smallest colour none of its neighbours
+ *    holds), colours visited in ascending order, each colour class (an independent set) updated
+ *    against the state left by earlier colours. Within a class, ascending id (any order gives
+ *    the same result).
  *  Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = seed, counter
  *    (v, t, r>>2, TAG_KSAT_SWEEP), output word r&3 for replica r's attempt on v at sweep t.
  *  Acceptance: dE <= 0 accepts with no draw. Otherwise bq = Q16 beta (round half even),
@@ -260,31 +263,106 @@ int64_t orc_ksat_delta(int32_t n, int32_t m, int32_t kmax, const int32_t *lits,
   return d;
 }
 
-/* Greedy colouring in ascending variable id: each variable takes the smallest colour not
- * already held by a variable it shares a clause with. Returns the number of colours. */
+/* DSatur colouring. Neighbours of v: the variables sharing a clause with v. Saturation of an
+ * uncoloured v: the number of distinct colours among its coloured neighbours. Each step picks
+ * the uncoloured variable of largest saturation, then of most clause occurrences, then of
+ * smallest id, and gives it the smallest colour held by none of its neighbours. The candidate
+ * is found with a binary max-heap of (saturation, occurrences, -id) entries; an entry whose
+ * saturation is out of date (the variable's saturation rose after it was pushed) or whose
+ * variable is coloured is dropped when it surfaces, so the top valid entry is always the
+ * variable the rule picks. Returns the number of colours. */
+typedef struct {
+  int32_t sat, deg, v;
+} col_entry;
+
+static int col_before(col_entry a, col_entry b) { /* a is picked before b */
+  if (a.sat != b.sat) return a.sat > b.sat;
+  if (a.deg != b.deg) return a.deg > b.deg;
+  return a.v < b.v;
+}
+
+static void heap_push(col_entry *h, int64_t *len, col_entry e) {
+  int64_t i = (*len)++;
+  h[i] = e;
+  while (i > 0) {
+    int64_t p = (i - 1) / 2;
+    if (!col_before(h[i], h[p])) break;
+    col_entry t = h[i];
+    h[i] = h[p];
+    h[p] = t;
+    i = p;
+  }
+}
+
+static col_entry heap_pop(col_entry *h, int64_t *len) {
+  col_entry top = h[0];
+  h[0] = h[--(*len)];
+  int64_t i = 0;
+  for (;;) {
+    int64_t l = 2 * i + 1, r = l + 1, b = i;
+    if (l < *len && col_before(h[l], h[b])) b = l;
+    if (r < *len && col_before(h[r], h[b])) b = r;
+    if (b == i) break;
+    col_entry t = h[i];
+    h[i] = h[b];
+    h[b] = t;
+    i = b;
+  }
+  return top;
+}
+
 static int32_t cnf_colour(const orc_cnf *f, int32_t *colour) {
-  int32_t ncol = 0;
-  int32_t *seen = (int32_t *)malloc(sizeof(int32_t) * ((size_t)f->n + 1));
-  for (int v = 0; v < f->n; ++v) seen[v] = -1;
-  seen[f->n] = -1;
-  for (int v = 0; v < f->n; ++v) colour[v] = -1;
-  for (int v = 0; v < f->n; ++v) {
-    /* mark colours of already-coloured neighbours with the stamp v */
+  const int32_t n = f->n;
+  /* a colour never exceeds a variable's count of neighbour slots, so `bound` colours suffice */
+  int64_t slots_max = 0, slots_all = 0;
+  for (int v = 0; v < n; ++v) {
+    int64_t s = 0;
     for (int32_t e = f->inc_ptr[v]; e < f->inc_ptr[v + 1]; ++e) {
       int64_t a = f->inc[e];
+      for (int q = 0; q < f->kmax; ++q)
+        if (f->lits[a * f->kmax + q] != 0) ++s;
+      --s; /* v itself */
+    }
+    if (s > slots_max) slots_max = s;
+    slots_all += s;
+  }
+  const int64_t bound = slots_max + 1, words = (bound + 63) / 64;
+  uint64_t *seen = (uint64_t *)calloc((size_t)n * (size_t)words, sizeof(uint64_t)); /* colours next to v */
+  int32_t *sat = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+  col_entry *heap = (col_entry *)malloc(sizeof(col_entry) * (size_t)(n + slots_all + 1));
+  int64_t len = 0;
+  int32_t ncol = 0;
+  for (int v = 0; v < n; ++v) {
+    colour[v] = -1;
+    col_entry e = {0, f->inc_ptr[v + 1] - f->inc_ptr[v], v};
+    heap_push(heap, &len, e);
+  }
+  while (len > 0) {
+    col_entry e = heap_pop(heap, &len);
+    const int v = e.v;
+    if (colour[v] >= 0 || e.sat != sat[v]) continue; /* coloured, or an out-of-date entry */
+    int32_t c = 0;
+    while (seen[(size_t)v * words + c / 64] >> (c % 64) & 1u) ++c;
+    colour[v] = c;
+    if (c + 1 > ncol) ncol = c + 1;
+    for (int32_t i = f->inc_ptr[v]; i < f->inc_ptr[v + 1]; ++i) {
+      int64_t a = f->inc[i];
       for (int q = 0; q < f->kmax; ++q) {
         int32_t l = f->lits[a * f->kmax + q];
         if (l == 0) continue;
         int u = lit_var(l);
-        if (u != v && colour[u] >= 0) seen[colour[u]] = v;
+        if (u == v || colour[u] >= 0) continue;
+        uint64_t *w = &seen[(size_t)u * words + c / 64];
+        if (*w >> (c % 64) & 1u) continue;
+        *w |= (uint64_t)1 << (c % 64);
+        col_entry g = {++sat[u], f->inc_ptr[u + 1] - f->inc_ptr[u], u};
+        heap_push(heap, &len, g);
       }
     }
-    int32_t c = 0;
-    while (seen[c] == v) ++c;
-    colour[v] = c;
-    if (c + 1 > ncol) ncol = c + 1;
   }
   free(seen);
+  free(sat);
+  free(heap);
   return ncol;
 }
 

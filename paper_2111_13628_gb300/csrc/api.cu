@@ -1,5 +1,5 @@
 // Host side of the C ABI declared in include/nmc.h: argument checks, the instance build
-// (greedy colouring, renumbering, occurrence lists), device residency of instances, schedules
+// (DSatur colouring, renumbering, occurrence lists), device residency of instances, schedules
 // and replica sets, and the dispatch to the kernels in ksat.cu and qap.cu.
 #include <algorithm>
 #include <cmath>
@@ -10,6 +10,7 @@
 #include <string>
 #include <thread>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "nmc.h"
@@ -657,24 +658,102 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
         }
       }
   });
-  // -- greedy colouring in ascending id: smallest colour absent among coloured neighbours
+  // -- DSatur colouring: repeatedly the uncoloured variable whose coloured neighbours show the
+  //    most distinct colours (then the one in more clauses, then the smaller id) takes the
+  //    smallest colour none of its neighbours holds. The tie order (occurrences, id) is fixed,
+  //    so every variable gets a rank in it, and the uncoloured variables sit in one bucket per
+  //    saturation: a bitset over ranks with a summary word per 64 words. A rising saturation
+  //    moves a variable to the next bucket; the pick is the lowest rank of the highest
+  //    non-empty bucket. The colours next to each variable are kept as a 64-bit word for
+  //    colours 0..63 and, beyond, in a map of further 64-bit words.
   std::vector<int32_t> colour(n, -1);
-  std::vector<int32_t> stamp(static_cast<size_t>(dmax) * (K > 1 ? K - 1 : 1) + 2, -1);
   int32_t n_colours = 0;
-  for (int32_t v = 0; v < n; ++v) {
-    const int32_t *p0 = &occ0[static_cast<size_t>(vptr[v]) * slots];
-    const int32_t *p1 = &occ0[static_cast<size_t>(vptr[v + 1]) * slots];
-    for (const int32_t *q = p0; q < p1; q += slots)
-      for (int z = 1; z < slots; ++z) {
-        const int32_t l = q[z];
-        if (l >= lit_false) continue;
-        const int32_t cu = colour[l >> 1];
-        if (cu >= 0 && cu < static_cast<int32_t>(stamp.size())) stamp[cu] = v;
+  {
+    std::vector<int32_t> ord(n), rank(n), sat(n, 0);
+    for (int32_t v = 0; v < n; ++v) ord[v] = v;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return deg[a] > deg[b]; });
+    for (int32_t r = 0; r < n; ++r) rank[ord[r]] = r;
+    const size_t nw = (static_cast<size_t>(n) + 63) / 64, ns = (nw + 63) / 64;
+    struct Bucket {
+      std::vector<uint64_t> bits, summary;
+      int64_t count = 0;
+    };
+    std::vector<Bucket> bucket;
+    auto insert = [&](int32_t s, int32_t r) {
+      if (static_cast<size_t>(s) >= bucket.size()) {
+        bucket.resize(s + 1);
+        for (auto &b : bucket)
+          if (b.bits.empty()) {
+            b.bits.assign(nw, 0u);
+            b.summary.assign(ns, 0u);
+          }
       }
-    int32_t c = 0;
-    while (c < static_cast<int32_t>(stamp.size()) && stamp[c] == v) ++c;
-    colour[v] = c;
-    if (c + 1 > n_colours) n_colours = c + 1;
+      Bucket &b = bucket[s];
+      b.bits[r >> 6] |= uint64_t(1) << (r & 63);
+      b.summary[r >> 12] |= uint64_t(1) << ((r >> 6) & 63);
+      ++b.count;
+    };
+    auto erase = [&](int32_t s, int32_t r) {
+      Bucket &b = bucket[s];
+      uint64_t &w = b.bits[r >> 6];
+      w &= ~(uint64_t(1) << (r & 63));
+      if (w == 0u) b.summary[r >> 12] &= ~(uint64_t(1) << ((r >> 6) & 63));
+      --b.count;
+    };
+    auto lowest = [&](const Bucket &b) -> int32_t {
+      for (size_t k = 0;; ++k)
+        if (b.summary[k]) {
+          const size_t wi = k * 64 + __builtin_ctzll(b.summary[k]);
+          return static_cast<int32_t>(wi * 64 + __builtin_ctzll(b.bits[wi]));
+        }
+    };
+    // per variable, side by side (one cache line per neighbour visit): its colour (-1 while
+    // uncoloured) and the colours 0..63 next to it
+    struct VState {
+      int32_t colour = -1;
+      uint64_t low = 0u;
+    };
+    std::vector<VState> vs(n);
+    std::unordered_map<int64_t, uint64_t> high;  // (v, block >= 1) -> colours 64 block ..
+    auto has = [&](int32_t v, int32_t c) -> bool {
+      if (c < 64) return (vs[v].low >> c) & 1u;
+      const auto it = high.find(static_cast<int64_t>(v) * 4096 + c / 64);
+      return it != high.end() && ((it->second >> (c % 64)) & 1u);
+    };
+    for (int32_t r = 0; r < n; ++r) insert(0, r);
+    int32_t top = 0;  // highest saturation with an uncoloured variable
+    for (int32_t left = n; left > 0; --left) {
+      while (bucket[top].count == 0) --top;
+      const int32_t v = ord[lowest(bucket[top])];
+      erase(top, rank[v]);
+      int32_t c = 0;
+      while (has(v, c)) ++c;
+      vs[v].colour = c;
+      colour[v] = c;
+      if (c + 1 > n_colours) n_colours = c + 1;
+      const int32_t *p0 = &occ0[static_cast<size_t>(vptr[v]) * slots];
+      const int32_t *p1 = &occ0[static_cast<size_t>(vptr[v + 1]) * slots];
+      const uint64_t cbit = c < 64 ? uint64_t(1) << c : 0u;
+      for (const int32_t *q = p0; q < p1; q += slots)
+        for (int z = 1; z < slots; ++z) {
+          const int32_t l = q[z];
+          if (l >= lit_false) continue;
+          const int32_t u = l >> 1;
+          VState &su = vs[u];
+          if (su.colour >= 0) continue;
+          if (c < 64) {
+            if (su.low & cbit) continue;
+            su.low |= cbit;
+          } else {
+            uint64_t &w = high[static_cast<int64_t>(u) * 4096 + c / 64];
+            if ((w >> (c % 64)) & 1u) continue;
+            w |= uint64_t(1) << (c % 64);
+          }
+          erase(sat[u], rank[u]);
+          insert(++sat[u], rank[u]);
+          if (sat[u] > top) top = sat[u];
+        }
+    }
   }
   // -- renumber: colour-major; inside a colour class by decreasing degree, then original id
   //    (the order inside a class does not change the dynamics; similar degrees side by side

@@ -215,16 +215,47 @@ def _adjacency(lits, n):
 
 
 @pytest.mark.parametrize("n,alpha,k", [(200, 9.6, 4), (500, 4.2, 3), (50, 2.0, 5)])
-def test_colouring_is_proper_and_greedy(n, alpha, k):
+def test_colouring_is_proper_and_minimal(n, alpha, k):
     lits = W.random_ksat(n, alpha, k, 99 + n)
     col, nc = O.ksat_colour(lits, n)
     adj = _adjacency(lits, n)
     assert col.min() == 0 and col.max() == nc - 1
     for v in range(n):
         assert all(col[u] != col[v] for u in adj[v])  # classes are independent sets
-        # greedy in ascending id: every smaller colour is held by a lower-id neighbour
-        lower = {int(col[u]) for u in adj[v] if u < v}
-        assert set(range(col[v])) <= lower
+        # a variable takes the smallest colour its earlier-coloured neighbours leave free, so
+        # every smaller colour is held by one of its neighbours
+        assert set(range(col[v])) <= {int(col[u]) for u in adj[v]}
+
+
+def _two_clauses(edges):
+    return np.array([[a + 1, b + 1] for a, b in edges], dtype=np.int32)
+
+
+def test_dsatur_textbook_cases():
+    # one clause of k variables is a k-clique: k colours
+    for k in (3, 5, 8):
+        col, nc = O.ksat_colour(np.arange(1, k + 1, dtype=np.int32)[None, :], k)
+        assert nc == k and sorted(col.tolist()) == list(range(k))
+    # cycles: 2 colours when even, 3 when odd
+    for length in (6, 7, 10, 11):
+        col, nc = O.ksat_colour(_two_clauses([(i, (i + 1) % length) for i in range(length)]), length)
+        assert nc == (2 if length % 2 == 0 else 3)
+    # DSatur colours bipartite graphs with 2 colours (Brelaz 1979). The crown graph (a_i ~ b_j
+    # for i != j) with ids interleaved a_0, b_0, a_1, b_1, ... is the classic case where greedy
+    # colouring in id order needs h colours.
+    for h in (4, 7):
+        edges = [(2 * i, 2 * j + 1) for i in range(h) for j in range(h) if i != j]
+        col, nc = O.ksat_colour(_two_clauses(edges), 2 * h)
+        assert nc == 2
+        assert all(col[a] != col[b] for a, b in edges)
+
+
+def test_dsatur_worked_path():
+    # path 0-1-2-3, worked by hand from the selection rule: 1 and 2 have two occurrences, 1 is
+    # smaller -> colour 0; 0 and 2 now see one colour, 2 has more occurrences -> colour 1; 0 and
+    # 3 tie on both, 0 is smaller -> colour 1; then 3 -> colour 0. (Id order would give 0,1,0,1.)
+    col, nc = O.ksat_colour(_two_clauses([(0, 1), (1, 2), (2, 3)]), 4)
+    assert nc == 2 and col.tolist() == [1, 0, 1, 0]
 
 
 # ---------------------------------------------------------------- closed forms of the chain
