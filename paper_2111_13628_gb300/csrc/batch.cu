@@ -607,8 +607,14 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
       int acc[32 / TL];
 #pragma unroll
       for (int i = 0; i < 32 / TL; ++i) acc[i] = 0;
+      // class bounds and first group: those of class c + 1 are requested during class c
+      int c0 = __ldg(B.col_ptr), c1 = __ldg(B.col_ptr + 1), cg = __ldg(B.cgrp);
       for (int c = 0; c < B.n_colours; ++c) {
-        const int c0 = __ldg(B.col_ptr + c), c1 = __ldg(B.col_ptr + c + 1), cg = __ldg(B.cgrp + c);
+        int c2 = 0, cgn = 0;
+        if (c + 1 < B.n_colours) {
+          c2 = __ldg(B.col_ptr + c + 2);
+          cgn = __ldg(B.cgrp + c + 1);
+        }
         // contiguous shares here (measured: round-robin groups are slower for the teams)
         const int part = ((c1 - c0 + CS - 1) / CS + 31) & ~31;
         const int v0 = c0 + rank * part, v1 = min(c1, v0 + part);
@@ -629,6 +635,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
           }
         }
         group_sync<CS>();
+        c0 = c1;
+        c1 = c2;
+        cg = cgn;
       }
 #pragma unroll
       for (int i = 0; i < 32 / TL; ++i)
