@@ -103,6 +103,12 @@ int nmc_unload(nmc_ctx *ctx, int32_t inst);
  * k-SAT instance. */
 int nmc_ksat_colouring(nmc_ctx *ctx, int32_t inst, int32_t *colour_out, int32_t *n_colours);
 
+/* The same colouring (the sweep order) of a formula given as for nmc_load_ksat, computed on the
+ * host alone: no context and no device. colour_out (nullable): int32 [n_vars]; n_colours
+ * (required). NMC_EINVAL for a formula nmc_load_ksat rejects. */
+int nmc_ksat_colour_host(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t *lits,
+                         int32_t *colour_out, int32_t *n_colours);
+
 /*
  * Sets the inverse-temperature profile beta[unit][step] of an instance (units = variables or
  * facilities): n_units * n_steps float32, row-major (row = one unit's schedule), host memory.

@@ -50,7 +50,8 @@ _lib = None
 
 # Exported C-ABI symbols (every function declared in include/nmc.h).
 SYMBOLS = ["nmc_create", "nmc_destroy", "nmc_last_error", "nmc_sync", "nmc_load_ksat",
-           "nmc_load_qap", "nmc_unload", "nmc_ksat_colouring", "nmc_set_schedule",
+           "nmc_load_qap", "nmc_unload", "nmc_ksat_colouring", "nmc_ksat_colour_host",
+           "nmc_set_schedule",
            "nmc_set_schedule_device", "nmc_set_schedule_factored", "nmc_replicas_create", "nmc_replicas_reset", "nmc_replicas_restore", "nmc_replicas_destroy",
            "nmc_replicas_run", "nmc_replicas_read", "nmc_replicas_read_device", "nmc_anneal",
            "nmc_threshold_table", "nmc_selftest_wait_timeout", "nmc_batch_run",
@@ -89,6 +90,7 @@ def load(build_if_missing: bool = True):
             "nmc_load_qap": ([P, i32, P, P, P], C.c_int),
             "nmc_unload": ([P, i32], C.c_int),
             "nmc_ksat_colouring": ([P, i32, P, P], C.c_int),
+            "nmc_ksat_colour_host": ([i32, i32, i32, P, P, P], C.c_int),
             "nmc_set_schedule": ([P, i32, i32, P], C.c_int),
             "nmc_set_schedule_device": ([P, i32, i32, P], C.c_int),
             "nmc_set_schedule_factored": ([P, i32, i32, P, P], C.c_int),
@@ -144,6 +146,19 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return C.c_void_p(a.data_ptr())
     return a.ctypes.data_as(C.c_void_p)
+
+
+def ksat_colour_host(lits, n_vars: int):
+    """(colour int32[N], n_colours): the library's sweep-order colouring, built on the host."""
+    lib = load()
+    lits = np.ascontiguousarray(lits, dtype=np.int32)
+    col = np.zeros(int(n_vars), dtype=np.int32)
+    nc = C.c_int32()
+    rc = lib.nmc_ksat_colour_host(int(n_vars), lits.shape[0], lits.shape[1], _ptr(lits), _ptr(col),
+                                  C.byref(nc))
+    if rc != 0:
+        raise NmcError(rc, "nmc_ksat_colour_host rejected the formula")
+    return col, int(nc.value)
 
 
 def threshold_table(cap: int = 8192):

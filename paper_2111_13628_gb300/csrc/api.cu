@@ -2215,3 +2215,13 @@ int nmc_anneal(nmc_ctx *ctx, int32_t inst, int32_t replicas, int32_t t0, int32_t
 }
 
 }  // extern "C"
+
+extern "C" int nmc_ksat_colour_host(int32_t n_vars, int32_t n_clauses, int32_t k_max,
+                                    const int32_t *lits, int32_t *colour_out, int32_t *n_colours) {
+  if (!n_colours) return NMC_EINVAL;
+  nmc::HostKsat h;
+  if (nmc::prepare_ksat(n_vars, n_clauses, k_max, lits, &h) != NMC_OK) return h.code;
+  if (colour_out) std::memcpy(colour_out, h.colour.data(), sizeof(int32_t) * h.colour.size());
+  *n_colours = h.n_colours;
+  return NMC_OK;
+}

@@ -57,3 +57,27 @@ def test_create_without_device_fails_cleanly():
     import paper_2111_13628_gb300 as nmc
     with pytest.raises(nmc.NmcError):
         nmc.Context(0)
+
+
+@pytest.mark.parametrize("n,alpha,k,seed", [(2000, 9.6, 4, 1), (3000, 4.2, 3, 2), (500, 30.0, 8, 9),
+                                            (300, 2.0, 5, 4)])
+def test_host_colouring_matches_oracle(n, alpha, k, seed):
+    """The library's sweep-order colouring (host code, no device) equals the oracle's; the last
+    case needs more than 64 colours."""
+    import nmc_inputs as W
+    import paper_2111_13628_gb300 as nmc
+    lits = W.random_ksat(n, alpha, k, seed)
+    col, nc = nmc.ksat_colour_host(lits, n)
+    ocol, onc = O.ksat_colour(lits, n)
+    assert nc == onc and np.array_equal(col, ocol)
+
+
+def test_host_colouring_crown_graph_and_rejects():
+    import paper_2111_13628_gb300 as nmc
+    h = 5
+    lits = np.array([[2 * i + 1, 2 * j + 2] for i in range(h) for j in range(h) if i != j],
+                    dtype=np.int32)
+    col, nc = nmc.ksat_colour_host(lits, 2 * h)
+    assert nc == 2 and np.array_equal(col, O.ksat_colour(lits, 2 * h)[0])
+    with pytest.raises(nmc.NmcError):
+        nmc.ksat_colour_host(np.array([[1, 1, 2]], dtype=np.int32), 3)  # repeated variable
