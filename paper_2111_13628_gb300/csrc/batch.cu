@@ -27,7 +27,8 @@ namespace nmc {
 
 namespace {
 
-constexpr int kBatchThreads = 640;
+constexpr int kBatchThreads = 640;  // one-thread kernel
+constexpr int kTeamThreads = 384;   // team kernel: 12 warps, so up to 168 registers
 
 template <int NB>
 __device__ __forceinline__ void csa4(uint32_t (&c)[NB], uint32_t a0, uint32_t a1, uint32_t a2,
@@ -216,7 +217,7 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
 // acceptance of replica groups [t*8/TL, (t+1)*8/TL) (one Philox block per group of 4 replicas)
 // and the team ORs the flip bits. A colour class of a few hundred variables then costs the
 // latency of a TL-th of one attempt instead of a whole one.
-template <int KQ, int TL, bool PT>
+template <int KQ, int TL, bool PT, bool PF = false>
 __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint32_t *xs,
                                                  const uint32_t *tab_s, int tab_len,
                                                  const uint32_t *mult_s, int cg, int c0, int v,
@@ -242,7 +243,8 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
     len = (__ldg(B.grp_base + g + 1) - gb) / (32 * KQ);
     ent = B.occ_t + gb + ln;
   }
-  for (int j0 = tl; j0 < len; j0 += 4 * TL) {
+  // occurrences j0 + i TL (i < 4) of the lane: break / make masks into the counters
+  auto eval4 = [&](const int4 (&qc)[4 * KQ], int j0) {
     uint32_t bb[4], mm[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -250,7 +252,7 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
       bb[i] = 0u;
       mm[i] = 0u;
       if (j < len) {
-        const int4 q = __ldg(ent + (size_t)(j * KQ) * 32);
+        const int4 q = qc[i * KQ];
         uint32_t o, own;
         if (KQ == 1) {
           const uint32_t sg = (uint32_t)q.x;
@@ -259,9 +261,9 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
               (xs_at(xs, q.w) ^ sign_mask<3>(sg));
           own = x ^ sign_mask<0>(sg);
         } else {
-          o = lit_word(xs, q.y) | lit_word(xs, q.z) | lit_word(xs, q.w);
-          const int4 q2 = __ldg(ent + (size_t)(j * KQ + 1) * 32);
-          o |= lit_word(xs, q2.x) | lit_word(xs, q2.y) | lit_word(xs, q2.z) | lit_word(xs, q2.w);
+          const int4 q2 = qc[i * KQ + 1];
+          o = lit_word(xs, q.y) | lit_word(xs, q.z) | lit_word(xs, q.w) | lit_word(xs, q2.x) |
+              lit_word(xs, q2.y) | lit_word(xs, q2.z) | lit_word(xs, q2.w);
           own = x ^ (uint32_t)q.x;
         }
         bb[i] = own & ~o;
@@ -270,6 +272,33 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
     }
     csa4<NB>(bc, bb[0], bb[1], bb[2], bb[3]);
     csa4<NB>(mc, mm[0], mm[1], mm[2], mm[3]);
+  };
+  auto load4 = [&](int4 (&q)[4 * KQ], int j0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = j0 + i * TL;
+#pragma unroll
+      for (int k = 0; k < KQ; ++k)
+        q[i * KQ + k] = j < len ? __ldg(ent + (size_t)(j * KQ + k) * 32) : make_int4(0, 0, 0, 0);
+    }
+  };
+  if constexpr (PF) {
+    // the next group of the lane's entries is requested before the current one is evaluated
+    int4 qn[4 * KQ];
+    if (tl < len) load4(qn, tl);
+    for (int j0 = tl; j0 < len; j0 += 4 * TL) {
+      int4 qc[4 * KQ];
+#pragma unroll
+      for (int i = 0; i < 4 * KQ; ++i) qc[i] = qn[i];
+      if (j0 + 4 * TL < len) load4(qn, j0 + 4 * TL);
+      eval4(qc, j0);
+    }
+  } else {
+    for (int j0 = tl; j0 < len; j0 += 4 * TL) {
+      int4 qc[4 * KQ];
+      load4(qc, j0);
+      eval4(qc, j0);
+    }
   }
 #pragma unroll
   for (int sft = 1; sft < TL; sft <<= 1) {
@@ -564,7 +593,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 
 
 template <int KQ, int CS, int TL, bool PT>
-__global__ void __launch_bounds__(kBatchThreads, 1)
+__global__ void __launch_bounds__(kTeamThreads, 1)
     ksat_team_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
                      const uint32_t *tab, int tab_len, int xs_words, int small_teams) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -623,7 +652,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
           const int v = vw + (lane / TL);
           const bool active = v < v1;
           const uint32_t xn =
-              attempt_team<KQ, TL, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, v, active, t, tl, acc);
+              attempt_team<KQ, TL, PT, true>(B, xs, tab_s, tab_len, mult_s, cg, c0, v, active, t, tl, acc);
           if (active && tl == 0) {
             if (CS == 1) {
               xs[v] = xn;
@@ -699,6 +728,7 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
   const int xs_words = max_n + 1;
   const size_t smem = sizeof(uint32_t) * (((size_t)xs_words + 31) / 32 * 32 + (size_t)tab_len + 1);
   auto kern = TL == 1 ? ksat_batch_kernel<KQ, CS, PT> : ksat_team_kernel<KQ, CS, (TL > 1 ? TL : 4), PT>;
+  constexpr int threads = TL == 1 ? kBatchThreads : kTeamThreads;
   static std::mutex mu;
   static std::map<std::pair<int, size_t>, int> shapes;  // (device, smem) -> resident clusters
   static std::map<int, int> sm_count;                    // device -> SMs
@@ -722,12 +752,12 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
       if (err != cudaSuccess) return err;
       if (CS == 1) {
         int per_sm = 0;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, smem);
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (err != cudaSuccess) return err;
         clusters = sms * per_sm;
       } else {
         cudaLaunchConfig_t q = {};
-        q.blockDim = dim3(kBatchThreads);
+        q.blockDim = dim3(threads);
         q.dynamicSmemBytes = smem;
         q.gridDim = dim3(CS * sms);
         cudaLaunchAttribute qa[1];
@@ -762,7 +792,7 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
   const int small_teams = (long long)n_items * CS <= sms ? 1 : 0;
   if (clusters > n_items) clusters = n_items;
   cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(kBatchThreads);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
