@@ -27,8 +27,15 @@ namespace nmc {
 
 namespace {
 
-constexpr int kBatchThreads = 640;  // one-thread kernel
-constexpr int kTeamThreads = 384;   // team kernel: 12 warps, so up to 168 registers
+constexpr int kBatchThreads = 640;  // one-thread kernel, and the team kernel with teams of 8
+constexpr int kTeamThreads = 384;   // team kernel with teams of 2 or 4: 12 warps, up to 168 registers
+
+// Threads of the sweep kernel with TL lanes per variable: 384 for teams of 2 or 4, which then
+// prefetch their occurrence entries a group ahead (measured at N = 5,000: 107 -> 102 us per
+// sweep); 640 for single threads and teams of 8 (the tiny classes of small instances, where 384
+// threads measured slower: N = 200, 37.3 -> 45.3 us).
+template <int TL>
+__host__ __device__ constexpr int sweep_threads() { return (TL == 2 || TL == 4) ? kTeamThreads : kBatchThreads; }
 
 template <int NB>
 __device__ __forceinline__ void csa4(uint32_t (&c)[NB], uint32_t a0, uint32_t a1, uint32_t a2,
@@ -294,10 +301,35 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
       eval4(qc, j0);
     }
   } else {
+    // each group's entries loaded where they are evaluated
     for (int j0 = tl; j0 < len; j0 += 4 * TL) {
-      int4 qc[4 * KQ];
-      load4(qc, j0);
-      eval4(qc, j0);
+      uint32_t bb[4], mm[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = j0 + i * TL;
+        bb[i] = 0u;
+        mm[i] = 0u;
+        if (j < len) {
+          const int4 q = __ldg(ent + (size_t)(j * KQ) * 32);
+          uint32_t o, own;
+          if (KQ == 1) {
+            const uint32_t sg = (uint32_t)q.x;
+            o = (xs_at(xs, q.y) ^ sign_mask<1>(sg)) |
+                (xs_at(xs, q.z) ^ sign_mask<2>(sg)) |
+                (xs_at(xs, q.w) ^ sign_mask<3>(sg));
+            own = x ^ sign_mask<0>(sg);
+          } else {
+            o = lit_word(xs, q.y) | lit_word(xs, q.z) | lit_word(xs, q.w);
+            const int4 q2 = __ldg(ent + (size_t)(j * KQ + 1) * 32);
+            o |= lit_word(xs, q2.x) | lit_word(xs, q2.y) | lit_word(xs, q2.z) | lit_word(xs, q2.w);
+            own = x ^ (uint32_t)q.x;
+          }
+          bb[i] = own & ~o;
+          mm[i] = ~(own | o);
+        }
+      }
+      csa4<NB>(bc, bb[0], bb[1], bb[2], bb[3]);
+      csa4<NB>(mc, mm[0], mm[1], mm[2], mm[3]);
     }
   }
 #pragma unroll
@@ -593,7 +625,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 
 
 template <int KQ, int CS, int TL, bool PT>
-__global__ void __launch_bounds__(kTeamThreads, 1)
+__global__ void __launch_bounds__(sweep_threads<TL>(), 1)
     ksat_team_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
                      const uint32_t *tab, int tab_len, int xs_words, int small_teams) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -636,11 +668,17 @@ __global__ void __launch_bounds__(kTeamThreads, 1)
       int acc[32 / TL];
 #pragma unroll
       for (int i = 0; i < 32 / TL; ++i) acc[i] = 0;
-      // class bounds and first group: those of class c + 1 are requested during class c
+      // class bounds and first group: for teams of 2 or 4 those of class c + 1 are requested
+      // during class c (the tiny classes of teams of 8 measured faster loading their own)
+      constexpr bool ahead = sweep_threads<TL>() == kTeamThreads;
       int c0 = __ldg(B.col_ptr), c1 = __ldg(B.col_ptr + 1), cg = __ldg(B.cgrp);
       for (int c = 0; c < B.n_colours; ++c) {
         int c2 = 0, cgn = 0;
-        if (c + 1 < B.n_colours) {
+        if (!ahead) {
+          c0 = __ldg(B.col_ptr + c);
+          c1 = __ldg(B.col_ptr + c + 1);
+          cg = __ldg(B.cgrp + c);
+        } else if (c + 1 < B.n_colours) {
           c2 = __ldg(B.col_ptr + c + 2);
           cgn = __ldg(B.cgrp + c + 1);
         }
@@ -652,7 +690,9 @@ __global__ void __launch_bounds__(kTeamThreads, 1)
           const int v = vw + (lane / TL);
           const bool active = v < v1;
           const uint32_t xn =
-              attempt_team<KQ, TL, PT, true>(B, xs, tab_s, tab_len, mult_s, cg, c0, v, active, t, tl, acc);
+              attempt_team<KQ, TL, PT, (sweep_threads<TL>() == kTeamThreads)>(B, xs, tab_s, tab_len,
+                                                                         mult_s, cg, c0, v, active,
+                                                                         t, tl, acc);
           if (active && tl == 0) {
             if (CS == 1) {
               xs[v] = xn;
@@ -728,7 +768,7 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
   const int xs_words = max_n + 1;
   const size_t smem = sizeof(uint32_t) * (((size_t)xs_words + 31) / 32 * 32 + (size_t)tab_len + 1);
   auto kern = TL == 1 ? ksat_batch_kernel<KQ, CS, PT> : ksat_team_kernel<KQ, CS, (TL > 1 ? TL : 4), PT>;
-  constexpr int threads = TL == 1 ? kBatchThreads : kTeamThreads;
+  constexpr int threads = sweep_threads<TL>();
   static std::mutex mu;
   static std::map<std::pair<int, size_t>, int> shapes;  // (device, smem) -> resident clusters
   static std::map<int, int> sm_count;                    // device -> SMs
