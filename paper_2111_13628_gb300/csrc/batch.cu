@@ -1,15 +1,17 @@
 // Batched k-SAT sweep: one persistent launch runs many replica sets of uneven instances
 // (sampling stage of Algorithm 1 for many problems at once).
 //
-// Work item = (replica set, word w of 32 replicas, sweep range). A CTA takes items from a
-// device counter, loads the item's word vector x[0..n) into shared memory, runs its sweeps
-// with the variables of one colour class spread over the threads (one thread = one variable
-// for the 32 replicas of the word) and a CTA barrier between classes, and writes the state
-// back. Words are independent chains, so no grid-wide synchronisation is needed and uneven
-// instances fill the GPU. The dynamics are identical to the single-instance kernels.
-// Occurrence lists are read in a warp-interleaved layout (one coalesced load per occurrence
-// for 32 variables); each thread keeps its share of the sweep's energy change as 16
-// bit-sliced planes and converts them to per-replica sums once per sweep.
+// Work item = (replica set, word w of 32 replicas, sweep range). A cluster of CS CTAs takes
+// items from a device counter; each CTA loads the item's word vector x[0..n) into its shared
+// memory, runs the sweeps with the variables of one colour class spread over the cluster's
+// threads (one thread, or a team of 2, 4 or 8 lanes, per variable for the 32 replicas of the
+// word), stores every new word into all CS copies, and meets the cluster barrier between
+// classes; the next class's bounds are requested before that barrier. Words are independent
+// chains, so no grid-wide synchronisation is needed and uneven instances fill the GPU. The
+// dynamics are identical to the single-instance kernels. Occurrence lists are read in a
+// warp-interleaved layout (one coalesced load per occurrence for 32 variables); each thread
+// keeps its share of the sweep's energy change as 16 bit-sliced planes and converts them to
+// per-replica sums once per sweep.
 #include <cooperative_groups.h>
 
 #include <cstdlib>
@@ -35,7 +37,9 @@ constexpr int kTeamThreads = 384;   // team kernel with teams of 2 or 4: 12 warp
 // sweep); 640 for single threads and teams of 8 (the tiny classes of small instances, where 384
 // threads measured slower: N = 200, 37.3 -> 45.3 us).
 template <int TL>
-__host__ __device__ constexpr int sweep_threads() { return (TL == 2 || TL == 4) ? kTeamThreads : kBatchThreads; }
+__host__ __device__ constexpr int sweep_threads() {
+  return (TL == 2 || TL == 4) ? kTeamThreads : kBatchThreads;
+}
 
 template <int NB>
 __device__ __forceinline__ void csa4(uint32_t (&c)[NB], uint32_t a0, uint32_t a1, uint32_t a2,
