@@ -185,10 +185,12 @@ int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t
  * context allocates. Limit: one call takes at most (1 MiB - 256 B) / 136 B = 7708 work items,
  * one per 32-replica word of each set (NMC_EINVAL beyond, with a message). The array is
  * reserved on every GPU that loads the library until the process exits. The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture. Every call shares the one array, which keeps
- * the last call's work list: calls whose launches overlap on the GPU (other streams, other
- * contexts, other host threads) race on it and must be serialised by the caller.
+ * device looks up the array's device address (cudaGetSymbolAddress, with that device current).
+ * Each call copies its work list into the array from host memory that lives only during the
+ * call, so the call is not for stream capture: a graph replay would copy from freed memory.
+ * Every call shares the one array, which keeps the last call's work list: calls whose launches
+ * overlap on the GPU (other streams, other contexts, other host threads) race on it and must be
+ * serialised by the caller.
  */
 int nmc_batch_run_noalloc(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
                           const int32_t *t1);
