@@ -157,8 +157,8 @@ def test_pt_argument_checks(ctx):
 
 @pytest.mark.parametrize("n,L,G,per", [(24, 8, 4, 2), (100, 16, 2, 3), (200, 12, 3, 1)])
 def test_qap_pt_parity(ctx, n, L, G, per):
-    """QAP replica exchange: 1, 4 and 7 registers per lane, several ladders, exchange rounds
-    between and across run boundaries."""
+    """QAP replica exchange: launch shapes of 2 and 7 facilities per lane on 16 lanes and of 7 on
+    32 lanes, several ladders, exchange rounds between and across run boundaries."""
     F, D = W.random_qap(n, 700 + n)
     T = 14
     beta = W.beta_scaled_linear(n, T, 0.01, 1.0, 0.5, 1.5, 9)

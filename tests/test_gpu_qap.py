@@ -23,9 +23,12 @@ def _same(got, want, ids=None):
         assert np.array_equal(g, want[b]), a
 
 
+# n picks the launch shape: 16 lanes per replica and n / 16 facilities per lane up to n = 128,
+# 32 lanes and n / 32 per lane beyond; the cases cover all twelve shapes and their edges
 @pytest.mark.parametrize("n,R,T", [(1, 3, 4), (2, 5, 6), (3, 33, 10), (31, 40, 8), (32, 32, 8),
-                                   (33, 17, 8), (64, 9, 6), (100, 35, 4), (129, 8, 3),
-                                   (256, 6, 2)])
+                                   (33, 17, 8), (64, 9, 6), (72, 19, 4), (90, 33, 3),
+                                   (100, 35, 4), (128, 64, 3), (129, 8, 3), (170, 10, 2),
+                                   (192, 7, 2), (224, 5, 2), (256, 6, 2)])
 def test_parity_shapes(ctx, n, R, T):
     F, D = W.random_qap(n, 300 + n)
     beta = W.beta_scaled_linear(n, T, 0.01, 1.0, 0.5, 1.5, 400 + n)
