@@ -1105,8 +1105,12 @@ static int set_schedule_impl(nmc_ctx *ctx, int32_t inst, int32_t n_steps, const 
   } else {
     NMC_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&src), sizeof(float) * count, ctx->stream),
              "allocate schedule staging");
-    NMC_CUDA(cudaMemcpyAsync(src, beta, sizeof(float) * count, cudaMemcpyHostToDevice, ctx->stream),
-             "copy schedule");
+    const cudaError_t ce =
+        cudaMemcpyAsync(src, beta, sizeof(float) * count, cudaMemcpyHostToDevice, ctx->stream);
+    if (ce != cudaSuccess) {
+      cudaFreeAsync(src, ctx->stream);
+      return cuda_fail(ctx, ce, "copy schedule");
+    }
   }
   uint32_t *bq = nullptr;
   cudaError_t e = cudaMalloc(&bq, sizeof(uint32_t) * count);
