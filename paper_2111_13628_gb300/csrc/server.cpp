@@ -168,8 +168,12 @@ void worker_loop(nmc_server *s) {
         incoming.push_back(r);
       }
     }
+    // the worker alone changes `active`, under the lock so that nmc_server_stats may read it
     for (auto &r : incoming)
-      if (admit(s, r)) s->active.push_back(r);
+      if (admit(s, r)) {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->active.push_back(r);
+      }
     if (s->active.empty()) continue;
     // one tick: equal-work slices, k-SAT in one batched launch, QAP after it
     const auto t0 = Clock::now();
@@ -215,6 +219,7 @@ void worker_loop(nmc_server *s) {
     if (rc != NMC_OK) {
       const std::string msg = nmc_last_error(s->ctx);
       for (auto &r : s->active) finish(s, r, rc, msg);
+      std::lock_guard<std::mutex> g(s->mu);
       s->active.clear();
       continue;
     }
@@ -246,9 +251,11 @@ void worker_loop(nmc_server *s) {
       const int rr = nmc_replicas_read(s->ctx, r->rs, &out);
       finish(s, r, rr == NMC_OK ? 2 : rr, rr == NMC_OK ? "" : nmc_last_error(s->ctx));
     }
+    std::lock_guard<std::mutex> g(s->mu);
     s->active.swap(keep);
   }
   for (auto &r : s->active) finish(s, r, NMC_ESTATE, "server stopped");
+  std::lock_guard<std::mutex> g(s->mu);
   s->active.clear();
 }
 
@@ -414,6 +421,7 @@ void nmc_server_destroy(nmc_server *s) {
     s->queue.clear();
   }
   s->cv_work.notify_all();
+  s->cv_done.notify_all();
   if (s->worker.joinable()) s->worker.join();
   nmc_destroy(s->ctx);
   delete s;
