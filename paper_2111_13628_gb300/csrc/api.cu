@@ -2,11 +2,13 @@
 // (DSatur colouring, renumbering, occurrence lists), device residency of instances, schedules
 // and replica sets, and the dispatch to the kernels in ksat.cu and qap.cu.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <tuple>
@@ -573,13 +575,18 @@ int prep_fail(HostKsat *out, int code, const std::string &msg) {
 }
 
 // Runs f(lo, hi) over [0, count) split into contiguous ranges on up to 16 host threads (inline
-// for small counts). Every range writes disjoint outputs, so the result does not depend on the
-// split.
+// below min_count items). Every range writes disjoint outputs, so the result does not depend
+// on the split.
+int host_threads() {
+  const unsigned hw = std::thread::hardware_concurrency();
+  return hw == 0 ? 1 : static_cast<int>(std::min<unsigned>(hw, 16u));
+}
+
 template <typename F>
-void parallel_ranges(int64_t count, F f) {
-  unsigned hw = std::thread::hardware_concurrency();
-  int64_t T = hw == 0 ? 1 : std::min<unsigned>(hw, 16u);
-  if (count < 8192) T = 1;
+void parallel_ranges(int64_t count, F f, int64_t min_count = 8192) {
+  int64_t T = host_threads();
+  if (count < min_count) T = 1;
+  if (T > count) T = count > 0 ? count : 1;
   if (T <= 1) {
     f(int64_t{0}, count);
     return;
@@ -598,40 +605,98 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
   if (k_max < 1 || k_max > 8) return prep_fail(out, NMC_EINVAL, "k_max must be in [1, 8]");
   if (n_clauses > 0 && !lits) return prep_fail(out, NMC_EINVAL, "lits is NULL");
   const int32_t n = n_vars, m = n_clauses, K = k_max;
-  // -- checks and variable -> clause incidence (clauses in ascending order)
-  std::vector<int32_t> deg(n + 1, 0);
-  for (int64_t a = 0; a < m; ++a) {
-    int used = 0;
-    for (int q = 0; q < K; ++q) {
-      const int32_t l = lits[a * K + q];
-      if (l == 0) continue;
-      if (l < -n || l > n) return prep_fail(out, NMC_EINVAL, "literal out of range in clause " + std::to_string(a));
-      const int32_t v = (l > 0 ? l : -l) - 1;
-      for (int q2 = 0; q2 < q; ++q2) {
-        const int32_t l2 = lits[a * K + q2];
-        if (l2 != 0 && ((l2 > 0 ? l2 : -l2) - 1) == v)
-          return prep_fail(out, NMC_EINVAL, "variable repeated in clause " + std::to_string(a));
+  // -- checks, clause ranges in parallel; the first failing clause is the one reported
+  {
+    std::mutex fm;
+    int64_t first = INT64_MAX;
+    int first_kind = 0;  // 1 literal out of range, 2 variable repeated, 3 empty clause
+    parallel_ranges(m, [&](int64_t a0, int64_t a1) {
+      for (int64_t a = a0; a < a1; ++a) {
+        int kind = 0, used = 0;
+        for (int q = 0; q < K && kind == 0; ++q) {
+          const int32_t l = lits[a * K + q];
+          if (l == 0) continue;
+          if (l < -n || l > n) {
+            kind = 1;
+            break;
+          }
+          const int32_t v = (l > 0 ? l : -l) - 1;
+          for (int q2 = 0; q2 < q; ++q2) {
+            const int32_t l2 = lits[a * K + q2];
+            if (l2 != 0 && ((l2 > 0 ? l2 : -l2) - 1) == v) kind = 2;
+          }
+          ++used;
+        }
+        if (kind == 0 && used == 0) kind = 3;
+        if (kind != 0) {
+          std::lock_guard<std::mutex> g(fm);
+          if (a < first) {
+            first = a;
+            first_kind = kind;
+          }
+          return;
+        }
       }
-      ++used;
-      ++deg[v];
-    }
-    if (used == 0) return prep_fail(out, NMC_EINVAL, "empty clause " + std::to_string(a));
+    });
+    if (first_kind == 1)
+      return prep_fail(out, NMC_EINVAL, "literal out of range in clause " + std::to_string(first));
+    if (first_kind == 2)
+      return prep_fail(out, NMC_EINVAL, "variable repeated in clause " + std::to_string(first));
+    if (first_kind == 3) return prep_fail(out, NMC_EINVAL, "empty clause " + std::to_string(first));
   }
+  // -- variable -> clause incidence, clauses in ascending order. Clause ranges in parallel:
+  //    thread t counts its clauses' occurrences of every variable; variable v's entries from
+  //    thread t follow those of threads 0..t-1, so every list stays in clause order. (One
+  //    thread when the per-thread counts would exceed 2^26 entries.)
+  int64_t TC = host_threads();
+  if (m < 8192 || TC * static_cast<int64_t>(n) > (int64_t(1) << 26)) TC = 1;
+  std::vector<int32_t> cnt(static_cast<size_t>(TC) * n, 0);
+  auto by_clause_range = [&](auto &&body) {
+    parallel_ranges(TC, [&](int64_t t0, int64_t t1) {
+      for (int64_t t = t0; t < t1; ++t) body(t, m * t / TC, m * (t + 1) / TC);
+    }, 1);
+  };
+  by_clause_range([&](int64_t t, int64_t a0, int64_t a1) {
+    int32_t *c = &cnt[static_cast<size_t>(t) * n];
+    for (int64_t i = a0 * K; i < a1 * K; ++i) {
+      const int32_t l = lits[i];
+      if (l != 0) ++c[(l > 0 ? l : -l) - 1];
+    }
+  });
+  std::vector<int32_t> deg(n, 0);
+  parallel_ranges(n, [&](int64_t v0, int64_t v1) {
+    for (int64_t v = v0; v < v1; ++v) {
+      int32_t d = 0;
+      for (int64_t t = 0; t < TC; ++t) d += cnt[static_cast<size_t>(t) * n + v];
+      deg[v] = d;
+    }
+  });
   int32_t dmax = 0;
   for (int32_t v = 0; v < n; ++v) dmax = deg[v] > dmax ? deg[v] : dmax;
   if (dmax > kMaxDegree)
     return prep_fail(out, NMC_EINVAL, "a variable occurs in more than 1023 clauses");
   std::vector<int32_t> vptr(n + 1, 0);
   for (int32_t v = 0; v < n; ++v) vptr[v + 1] = vptr[v] + deg[v];
-  std::vector<int32_t> vcl(vptr[n] > 0 ? vptr[n] : 1);
-  {
-    std::vector<int32_t> fill(vptr.begin(), vptr.end() - 1);
-    for (int64_t a = 0; a < m; ++a)
+  parallel_ranges(n, [&](int64_t v0, int64_t v1) {  // counts -> each thread's first slot
+    for (int64_t v = v0; v < v1; ++v) {
+      int32_t o = vptr[v];
+      for (int64_t t = 0; t < TC; ++t) {
+        int32_t &c = cnt[static_cast<size_t>(t) * n + v];
+        const int32_t k = c;
+        c = o;
+        o += k;
+      }
+    }
+  });
+  HostVec vcl(vptr[n] > 0 ? vptr[n] : 1);
+  by_clause_range([&](int64_t t, int64_t a0, int64_t a1) {
+    int32_t *c = &cnt[static_cast<size_t>(t) * n];
+    for (int64_t a = a0; a < a1; ++a)
       for (int q = 0; q < K; ++q) {
         const int32_t l = lits[a * K + q];
-        if (l != 0) vcl[fill[(l > 0 ? l : -l) - 1]++] = static_cast<int32_t>(a);
+        if (l != 0) vcl[c[(l > 0 ? l : -l) - 1]++] = static_cast<int32_t>(a);
       }
-  }
+  });
   // -- occurrence entries in original ids, one per (variable, clause containing it): slot 0
   //    the variable's own sign (0 or -1), slots 1.. the clause's other literals 2u + neg, the
   //    rest lit_false. One pass of random clause reads, spread over threads; the colouring and
@@ -639,7 +704,7 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
   const int kq = K <= 4 ? 1 : 2;
   const int slots = 4 * kq;
   const int32_t lit_false = 2 * n, lit_true = 2 * n + 1;
-  std::vector<int32_t> occ0(static_cast<size_t>(vptr[n] > 0 ? vptr[n] : 1) * slots, lit_false);
+  HostVec occ0(static_cast<size_t>(vptr[n] > 0 ? vptr[n] : 1) * slots);
   parallel_ranges(n, [&](int64_t v0, int64_t v1) {
     for (int64_t ov = v0; ov < v1; ++ov)
       for (int32_t e = vptr[ov]; e < vptr[ov + 1]; ++e) {
@@ -656,126 +721,152 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
           else
             slot[s++] = 2 * u + neg;
         }
+        for (; s < slots; ++s) slot[s] = lit_false;
       }
   });
+  // the tie order of the colouring: more occurrences first, then the smaller id (a counting
+  // sort by degree, stable in id)
+  std::vector<int32_t> ord(n);
+  {
+    std::vector<int32_t> start(dmax + 2, 0);
+    for (int32_t v = 0; v < n; ++v) ++start[dmax - deg[v] + 1];
+    for (int32_t d = 0; d <= dmax; ++d) start[d + 1] += start[d];
+    for (int32_t v = 0; v < n; ++v) ord[start[dmax - deg[v]]++] = v;
+  }
   // -- DSatur colouring: repeatedly the uncoloured variable whose coloured neighbours show the
   //    most distinct colours (then the one in more clauses, then the smaller id) takes the
-  //    smallest colour none of its neighbours holds. The tie order (occurrences, id) is fixed,
-  //    so every variable gets a rank in it, and the uncoloured variables sit in one bucket per
-  //    saturation: a bitset over ranks with a summary word per 64 words. A rising saturation
-  //    moves a variable to the next bucket; the pick is the lowest rank of the highest
-  //    non-empty bucket. The colours next to each variable are kept as a 64-bit word for
-  //    colours 0..63 and, beyond, in a map of further 64-bit words.
+  //    smallest colour none of its neighbours holds. Every variable has a rank in the fixed tie
+  //    order, and the uncoloured variables sit in one bucket per saturation: a bitset over
+  //    ranks with a summary word per 64 words and the index below which a bucket's summary
+  //    words are all zero (the scan for its lowest rank starts there, so a sparse instance
+  //    does not rescan empty words on every pick). The buckets are interleaved word by word
+  //    (word w of bucket s at w * S + s), so moving a variable from saturation s to s + 1
+  //    touches one cache line. The pick is the lowest rank of the highest non-empty bucket.
+  //    The colours next to each variable are kept as a 64-bit word for colours 0..63 and,
+  //    beyond, in a map of further 64-bit words.
   std::vector<int32_t> colour(n, -1);
   int32_t n_colours = 0;
   {
-    std::vector<int32_t> ord(n), rank(n), sat(n, 0);
-    for (int32_t v = 0; v < n; ++v) ord[v] = v;
-    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return deg[a] > deg[b]; });
-    for (int32_t r = 0; r < n; ++r) rank[ord[r]] = r;
-    const size_t nw = (static_cast<size_t>(n) + 63) / 64, ns = (nw + 63) / 64;
-    struct Bucket {
-      std::vector<uint64_t> bits, summary;
-      int64_t count = 0;
+    // per variable: the colours 0..63 its neighbours hold (all ones once it is coloured
+    // itself, so one test skips both cases), and its saturation with its rank in the tie order
+    std::vector<uint64_t> low(n, 0u);
+    struct SatRank {
+      int32_t sat;   // distinct colours among its coloured neighbours
+      int32_t rank;  // position in the tie order
     };
-    std::vector<Bucket> bucket;
+    std::vector<SatRank> sr(n);
+    for (int32_t r = 0; r < n; ++r) sr[ord[r]] = SatRank{0, r};
+    const size_t nw = (static_cast<size_t>(n) + 63) / 64, ns = (nw + 63) / 64;
+    size_t S = 16;  // bucket capacity (saturations 0..S-1), doubled on demand
+    std::vector<uint64_t> bits(nw * S, 0u), summary(ns * S, 0u);
+    std::vector<int64_t> count(S, 0);
+    std::vector<size_t> from(S, 0);  // per bucket: its summary words below this index are zero
+    auto grow = [&]() {
+      const size_t S2 = 2 * S;
+      std::vector<uint64_t> b2(nw * S2, 0u), s2(ns * S2, 0u);
+      for (size_t w = 0; w < nw; ++w)
+        for (size_t s = 0; s < S; ++s) b2[w * S2 + s] = bits[w * S + s];
+      for (size_t k = 0; k < ns; ++k)
+        for (size_t s = 0; s < S; ++s) s2[k * S2 + s] = summary[k * S + s];
+      bits.swap(b2);
+      summary.swap(s2);
+      count.resize(S2, 0);
+      from.resize(S2, 0);
+      S = S2;
+    };
     auto insert = [&](int32_t s, int32_t r) {
-      if (static_cast<size_t>(s) >= bucket.size()) {
-        bucket.resize(s + 1);
-        for (auto &b : bucket)
-          if (b.bits.empty()) {
-            b.bits.assign(nw, 0u);
-            b.summary.assign(ns, 0u);
-          }
-      }
-      Bucket &b = bucket[s];
-      b.bits[r >> 6] |= uint64_t(1) << (r & 63);
-      b.summary[r >> 12] |= uint64_t(1) << ((r >> 6) & 63);
-      ++b.count;
+      if (static_cast<size_t>(s) >= S) grow();
+      bits[static_cast<size_t>(r >> 6) * S + s] |= uint64_t(1) << (r & 63);
+      summary[static_cast<size_t>(r >> 12) * S + s] |= uint64_t(1) << ((r >> 6) & 63);
+      if (static_cast<size_t>(r >> 12) < from[s]) from[s] = static_cast<size_t>(r >> 12);
+      ++count[s];
     };
     auto erase = [&](int32_t s, int32_t r) {
-      Bucket &b = bucket[s];
-      uint64_t &w = b.bits[r >> 6];
+      uint64_t &w = bits[static_cast<size_t>(r >> 6) * S + s];
       w &= ~(uint64_t(1) << (r & 63));
-      if (w == 0u) b.summary[r >> 12] &= ~(uint64_t(1) << ((r >> 6) & 63));
-      --b.count;
+      if (w == 0u) summary[static_cast<size_t>(r >> 12) * S + s] &= ~(uint64_t(1) << ((r >> 6) & 63));
+      --count[s];
     };
-    auto lowest = [&](const Bucket &b) -> int32_t {
-      for (size_t k = 0;; ++k)
-        if (b.summary[k]) {
-          const size_t wi = k * 64 + __builtin_ctzll(b.summary[k]);
-          return static_cast<int32_t>(wi * 64 + __builtin_ctzll(b.bits[wi]));
+    auto lowest = [&](int32_t s) -> int32_t {
+      for (size_t k = from[s];; ++k)
+        if (const uint64_t sw = summary[k * S + s]) {
+          from[s] = k;
+          const size_t wi = k * 64 + __builtin_ctzll(sw);
+          return static_cast<int32_t>(wi * 64 + __builtin_ctzll(bits[wi * S + s]));
         }
     };
-    // per variable, side by side (one cache line per neighbour visit): its colour (-1 while
-    // uncoloured) and the colours 0..63 next to it
-    struct VState {
-      int32_t colour = -1;
-      uint64_t low = 0u;
-    };
-    std::vector<VState> vs(n);
     std::unordered_map<int64_t, uint64_t> high;  // (v, block >= 1) -> colours 64 block ..
-    auto has = [&](int32_t v, int32_t c) -> bool {
-      if (c < 64) return (vs[v].low >> c) & 1u;
+    auto has_high = [&](int32_t v, int32_t c) -> bool {
       const auto it = high.find(static_cast<int64_t>(v) * 4096 + c / 64);
       return it != high.end() && ((it->second >> (c % 64)) & 1u);
     };
     for (int32_t r = 0; r < n; ++r) insert(0, r);
     int32_t top = 0;  // highest saturation with an uncoloured variable
     for (int32_t left = n; left > 0; --left) {
-      while (bucket[top].count == 0) --top;
-      const int32_t v = ord[lowest(bucket[top])];
-      erase(top, rank[v]);
-      int32_t c = 0;
-      while (has(v, c)) ++c;
-      vs[v].colour = c;
+      while (count[top] == 0) --top;
+      const int32_t v = ord[lowest(top)];
+      erase(top, sr[v].rank);
+      int32_t c;
+      if (low[v] != ~uint64_t(0)) {
+        c = __builtin_ctzll(~low[v]);
+      } else {
+        c = 64;
+        while (has_high(v, c)) ++c;
+      }
       colour[v] = c;
+      low[v] = ~uint64_t(0);
       if (c + 1 > n_colours) n_colours = c + 1;
       const int32_t *p0 = &occ0[static_cast<size_t>(vptr[v]) * slots];
       const int32_t *p1 = &occ0[static_cast<size_t>(vptr[v + 1]) * slots];
-      const uint64_t cbit = c < 64 ? uint64_t(1) << c : 0u;
-      for (const int32_t *q = p0; q < p1; q += slots)
-        for (int z = 1; z < slots; ++z) {
-          const int32_t l = q[z];
-          if (l >= lit_false) continue;
-          const int32_t u = l >> 1;
-          VState &su = vs[u];
-          if (su.colour >= 0) continue;
-          if (c < 64) {
-            if (su.low & cbit) continue;
-            su.low |= cbit;
-          } else {
-            uint64_t &w = high[static_cast<int64_t>(u) * 4096 + c / 64];
+      auto raise = [&](int32_t u) {
+        SatRank &x = sr[u];
+        erase(x.sat, x.rank);
+        insert(++x.sat, x.rank);
+        if (x.sat > top) top = x.sat;
+      };
+      if (c < 64) {
+        const uint64_t cbit = uint64_t(1) << c;
+        for (const int32_t *q = p0; q < p1; q += slots)
+          for (int z = 1; z < slots; ++z) {
+            const int32_t l = q[z];
+            if (l >= lit_false) continue;
+            uint64_t &lw = low[l >> 1];
+            if (lw & cbit) continue;  // coloured, or colour c already next to it
+            lw |= cbit;
+            raise(l >> 1);
+          }
+      } else {
+        for (const int32_t *q = p0; q < p1; q += slots)
+          for (int z = 1; z < slots; ++z) {
+            const int32_t l = q[z];
+            if (l >= lit_false || colour[l >> 1] >= 0) continue;
+            uint64_t &w = high[static_cast<int64_t>(l >> 1) * 4096 + c / 64];
             if ((w >> (c % 64)) & 1u) continue;
             w |= uint64_t(1) << (c % 64);
+            raise(l >> 1);
           }
-          erase(sat[u], rank[u]);
-          insert(++sat[u], rank[u]);
-          if (sat[u] > top) top = sat[u];
-        }
+      }
     }
   }
   // -- renumber: colour-major; inside a colour class by decreasing degree, then original id
   //    (the order inside a class does not change the dynamics; similar degrees side by side
-  //    keep the warp-interleaved occurrence groups below nearly free of padding)
+  //    keep the warp-interleaved occurrence groups below nearly free of padding). The tie
+  //    order above is already (degree down, id up): a stable counting sort of it by colour.
   std::vector<int32_t> col_ptr(n_colours + 1, 0);
   for (int32_t v = 0; v < n; ++v) ++col_ptr[colour[v] + 1];
   for (int32_t c = 0; c < n_colours; ++c) col_ptr[c + 1] += col_ptr[c];
   std::vector<int32_t> orig(n), newid(n);
   {
-    for (int32_t v = 0; v < n; ++v) orig[v] = v;
-    std::stable_sort(orig.begin(), orig.end(), [&](int32_t a, int32_t b) {
-      if (colour[a] != colour[b]) return colour[a] < colour[b];
-      if (deg[a] != deg[b]) return deg[a] > deg[b];
-      return a < b;
-    });
+    std::vector<int32_t> pos(col_ptr.begin(), col_ptr.end() - 1);
+    for (int32_t r = 0; r < n; ++r) orig[pos[colour[ord[r]]]++] = ord[r];
     for (int32_t p = 0; p < n; ++p) newid[orig[p]] = p;
   }
   // -- occurrence lists in new ids, each padded to a multiple of 4 occurrences
   std::vector<int32_t> occ_ptr(n + 1, 0);
   for (int32_t v = 0; v < n; ++v) occ_ptr[v + 1] = occ_ptr[v] + ((deg[orig[v]] + 3) & ~3);
   const int64_t n_occ = occ_ptr[n];
-  std::vector<int32_t> occ(static_cast<size_t>(n_occ > 0 ? n_occ : 1) * slots, lit_false);
+  HostVec occ(static_cast<size_t>(n_occ > 0 ? n_occ : 1) * slots);
+  if (n_occ == 0) std::fill(occ.begin(), occ.end(), lit_false);
   parallel_ranges(n, [&](int64_t v0, int64_t v1) {
     for (int64_t v = v0; v < v1; ++v) {
       const int32_t ov = orig[v];
@@ -793,6 +884,7 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
         int32_t *slot = &occ[static_cast<size_t>(o) * slots];
         slot[0] = 0;
         slot[1] = lit_true;
+        for (int z = 2; z < slots; ++z) slot[z] = lit_false;
       }
     }
   });
@@ -820,7 +912,9 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
   std::vector<int32_t> grp_end(grp_v0.size());
   for (int32_t c = 0; c < n_colours; ++c)
     for (int32_t g = cgrp[c]; g < cgrp[c + 1]; ++g) grp_end[g] = col_ptr[c + 1];
-  std::vector<int32_t> occ_t(static_cast<size_t>(std::max<int64_t>(grp_base.back(), 1)) * 4);
+  // every entry of every group is written below (lanes x occurrences x kq int4)
+  HostVec occ_t(static_cast<size_t>(std::max<int64_t>(grp_base.back(), 1)) * 4);
+  if (grp_base.back() == 0) std::fill(occ_t.begin(), occ_t.end(), 0);
   parallel_ranges(static_cast<int64_t>(grp_v0.size()), [&](int64_t ga, int64_t gz) {
     for (int64_t g = ga; g < gz; ++g) {
       const int32_t g0 = grp_v0[g], cend = grp_end[g];
@@ -853,13 +947,17 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
           }
       }
     }
-  });
-  std::vector<int32_t> clits(static_cast<size_t>(m > 0 ? m : 1) * K, lit_false);
+  }, 64);  // a group is 32 variables' lists: split from a few dozen groups on
+  HostVec clits(static_cast<size_t>(m > 0 ? m : 1) * K);
+  if (m == 0) std::fill(clits.begin(), clits.end(), lit_false);
   parallel_ranges(m, [&](int64_t a0, int64_t a1) {
     for (int64_t a = a0; a < a1; ++a)
       for (int q = 0; q < K; ++q) {
         const int32_t l = lits[a * K + q];
-        if (l == 0) continue;
+        if (l == 0) {
+          clits[a * K + q] = lit_false;
+          continue;
+        }
         const int32_t u = (l > 0 ? l : -l) - 1;
         clits[a * K + q] = 2 * newid[u] + (l < 0 ? 1 : 0);
       }
@@ -892,8 +990,9 @@ int upload_ksat(nmc_ctx *ctx, HostKsat &h, int32_t *inst_out) {
   if (h.code != NMC_OK) return fail(ctx, h.code, h.err);
   const int32_t n = h.n, m = h.m, K = h.K, n_colours = h.n_colours, kq = h.kq, nb = h.nb;
   const int64_t n_occ = h.n_occ;
-  std::vector<int32_t> &occ = h.occ, &occ_ptr = h.occ_ptr, &col_ptr = h.col_ptr, &orig = h.orig,
-                       &newid = h.newid, &clits = h.clits, &occ_t = h.occ_t,
+  HostVec &occ = h.occ, &clits = h.clits, &occ_t = h.occ_t;
+  std::vector<int32_t> &occ_ptr = h.occ_ptr, &col_ptr = h.col_ptr, &orig = h.orig,
+                       &newid = h.newid,
                        &grp_base = h.grp_base, &cgrp = h.cgrp, &colour = h.colour;
   DeviceGuard g(ctx->device);
   Instance I;

@@ -4,7 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
+#include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 struct nmc_ctx;
@@ -158,6 +161,29 @@ int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t
 // Records an error message on the context; returns `code`.
 int set_ctx_error(nmc_ctx *ctx, int code, const char *msg);
 
+// Allocator whose elements start uninitialised: the large host arrays of an instance are
+// written element by element by several threads, so a serial zero fill first is wasted work.
+// Every element of a vector using it must be written before it is read.
+template <typename T>
+struct UninitAlloc : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = UninitAlloc<U>;
+  };
+  UninitAlloc() = default;
+  template <typename U>
+  UninitAlloc(const UninitAlloc<U> &) noexcept {}
+  template <typename U>
+  void construct(U *p) noexcept {
+    ::new (static_cast<void *>(p)) U;
+  }
+  template <typename U, typename... A>
+  void construct(U *p, A &&...a) {
+    ::new (static_cast<void *>(p)) U(std::forward<A>(a)...);
+  }
+};
+using HostVec = std::vector<int32_t, UninitAlloc<int32_t>>;
+
 // A k-SAT instance prepared on the host (checks, colouring, renumbering, occurrence lists),
 // ready to upload. prepare_ksat needs no context or device, so callers can run it on any
 // thread; upload_ksat makes it resident on the context's device (nmc_load_ksat = both).
@@ -165,7 +191,8 @@ struct HostKsat {
   int code = 0;
   std::string err;
   int32_t n = 0, m = 0, K = 0, n_colours = 0, kq = 1, nb = 2, n_occ = 0;
-  std::vector<int32_t> occ, occ_ptr, col_ptr, orig, newid, clits, occ_t, grp_base, cgrp, colour;
+  HostVec occ, clits, occ_t;
+  std::vector<int32_t> occ_ptr, col_ptr, orig, newid, grp_base, cgrp, colour;
 };
 int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t *lits,
                  HostKsat *out);
