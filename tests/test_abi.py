@@ -81,3 +81,27 @@ def test_host_colouring_crown_graph_and_rejects():
     assert nc == 2 and np.array_equal(col, O.ksat_colour(lits, 2 * h)[0])
     with pytest.raises(nmc.NmcError):
         nmc.ksat_colour_host(np.array([[1, 1, 2]], dtype=np.int32), 3)  # repeated variable
+
+
+@pytest.mark.parametrize("fault", ["repeat", "range", "empty", "degree"])
+def test_host_build_rejects_a_late_fault_in_a_large_formula(fault):
+    """Checks run over clause ranges on several threads: a fault in the last clauses of a
+    20,000-clause formula is still found, and the valid formula itself is accepted."""
+    import nmc_inputs as W
+    import paper_2111_13628_gb300 as nmc
+    n = 4000
+    lits = W.random_ksat(n, 5.0, 4, 77).copy()
+    assert lits.shape[0] == 20000
+    nmc.ksat_colour_host(lits, n)
+    if fault == "repeat":
+        lits[19990, 2] = lits[19990, 0]
+    elif fault == "range":
+        lits[19999, 3] = n + 1
+    elif fault == "empty":
+        lits[19998, :] = 0
+    else:  # variable 1 in 1,024 clauses (rows that do not hold it elsewhere)
+        rows = np.flatnonzero(~np.any(np.abs(lits[:, 1:]) == 1, axis=1))[:1024]
+        lits[rows, 0] = 1
+        assert (np.abs(lits) == 1).sum() >= 1024
+    with pytest.raises(nmc.NmcError):
+        nmc.ksat_colour_host(lits, n)
