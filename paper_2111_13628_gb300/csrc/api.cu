@@ -741,7 +741,9 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
   //    words are all zero (the scan for its lowest rank starts there, so a sparse instance
   //    does not rescan empty words on every pick). The buckets are interleaved word by word
   //    (word w of bucket s at w * S + s), so moving a variable from saturation s to s + 1
-  //    touches one cache line. The pick is the lowest rank of the highest non-empty bucket.
+  //    touches one cache line. A rising saturation only sets the variable's bit in its new
+  //    bucket; the old bit goes stale and is dropped when a pick meets it (count[s] counts the
+  //    live entries). The pick is the lowest live rank of the highest non-empty bucket.
   //    The colours next to each variable are kept as a 64-bit word for colours 0..63 and,
   //    beyond, in a map of further 64-bit words.
   std::vector<int32_t> colour(n, -1);
@@ -759,7 +761,7 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
     const size_t nw = (static_cast<size_t>(n) + 63) / 64, ns = (nw + 63) / 64;
     size_t S = 16;  // bucket capacity (saturations 0..S-1), doubled on demand
     std::vector<uint64_t> bits(nw * S, 0u), summary(ns * S, 0u);
-    std::vector<int64_t> count(S, 0);
+    std::vector<int64_t> count(S, 0);  // live entries per bucket
     std::vector<size_t> from(S, 0);  // per bucket: its summary words below this index are zero
     auto grow = [&]() {
       const size_t S2 = 2 * S;
@@ -781,11 +783,10 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
       if (static_cast<size_t>(r >> 12) < from[s]) from[s] = static_cast<size_t>(r >> 12);
       ++count[s];
     };
-    auto erase = [&](int32_t s, int32_t r) {
+    auto clear = [&](int32_t s, int32_t r) {
       uint64_t &w = bits[static_cast<size_t>(r >> 6) * S + s];
       w &= ~(uint64_t(1) << (r & 63));
       if (w == 0u) summary[static_cast<size_t>(r >> 12) * S + s] &= ~(uint64_t(1) << ((r >> 6) & 63));
-      --count[s];
     };
     auto lowest = [&](int32_t s) -> int32_t {
       for (size_t k = from[s];; ++k)
@@ -804,8 +805,14 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
     int32_t top = 0;  // highest saturation with an uncoloured variable
     for (int32_t left = n; left > 0; --left) {
       while (count[top] == 0) --top;
-      const int32_t v = ord[lowest(top)];
-      erase(top, sr[v].rank);
+      int32_t v;
+      while (true) {  // stale bits (variables that have moved up since) are dropped here
+        const int32_t r = lowest(top);
+        clear(top, r);
+        v = ord[r];
+        if (sr[v].sat == top) break;
+      }
+      --count[top];
       int32_t c;
       if (low[v] != ~uint64_t(0)) {
         c = __builtin_ctzll(~low[v]);
@@ -818,9 +825,9 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
       if (c + 1 > n_colours) n_colours = c + 1;
       const int32_t *p0 = &occ0[static_cast<size_t>(vptr[v]) * slots];
       const int32_t *p1 = &occ0[static_cast<size_t>(vptr[v + 1]) * slots];
-      auto raise = [&](int32_t u) {
+      auto raise = [&](int32_t u) {  // its bit at the old saturation stays, now stale
         SatRank &x = sr[u];
-        erase(x.sat, x.rank);
+        --count[x.sat];
         insert(++x.sat, x.rank);
         if (x.sat > top) top = x.sat;
       };
