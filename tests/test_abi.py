@@ -81,6 +81,12 @@ def test_host_colouring_crown_graph_and_rejects():
     assert nc == 2 and np.array_equal(col, O.ksat_colour(lits, 2 * h)[0])
     with pytest.raises(nmc.NmcError):
         nmc.ksat_colour_host(np.array([[1, 1, 2]], dtype=np.int32), 3)  # repeated variable
+    for rim in (10, 11):  # wheels: 3 / 4 colours, as the oracle
+        lits = np.array([[1, i + 1] for i in range(1, rim + 1)] +
+                        [[i + 1, i % rim + 2] for i in range(1, rim + 1)], dtype=np.int32)
+        col, nc = nmc.ksat_colour_host(lits, rim + 1)
+        assert nc == (3 if rim % 2 == 0 else 4)
+        assert np.array_equal(col, O.ksat_colour(lits, rim + 1)[0])
 
 
 @pytest.mark.parametrize("fault", ["repeat", "range", "empty", "degree"])

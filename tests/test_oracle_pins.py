@@ -248,6 +248,14 @@ def test_dsatur_textbook_cases():
         col, nc = O.ksat_colour(_two_clauses(edges), 2 * h)
         assert nc == 2
         assert all(col[a] != col[b] for a, b in edges)
+    # DSatur is also exact on wheels (a hub joined to every vertex of a cycle): 3 colours
+    # around an even rim, 4 around an odd one; the hub, of highest degree, comes first
+    for rim in (6, 7, 10, 11):
+        edges = [(0, i) for i in range(1, rim + 1)] + \
+                [(i, i % rim + 1) for i in range(1, rim + 1)]
+        col, nc = O.ksat_colour(_two_clauses(edges), rim + 1)
+        assert nc == (3 if rim % 2 == 0 else 4) and col[0] == 0
+        assert all(col[a] != col[b] for a, b in edges)
 
 
 def test_dsatur_worked_path():
