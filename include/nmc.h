@@ -79,8 +79,9 @@ int nmc_sync(nmc_ctx *ctx);
  * +(v+1) / -(v+1) for x_v / not x_v, 0 for an unused slot. Requirements (else NMC_EINVAL):
  * 1 <= n_vars < 2^28, 0 <= n_clauses < 2^31, 1 <= k_max <= 8, every |literal| <= n_vars,
  * at least one literal per clause, no variable twice in one clause, every variable in at most
- * 1023 clauses. Builds, on the host, the colouring and the occurrence lists, and uploads them.
- * *inst_out receives the instance id.
+ * 1023 clauses (a rejected formula names the first clause at fault). Builds, on the host, the
+ * colouring and the occurrence lists (with up to 16 short-lived host threads; the colouring
+ * itself is sequential), and uploads them. *inst_out receives the instance id.
  */
 int nmc_load_ksat(nmc_ctx *ctx, int32_t n_vars, int32_t n_clauses, int32_t k_max,
                   const int32_t *lits, int32_t *inst_out);
