@@ -574,19 +574,17 @@ int prep_fail(HostKsat *out, int code, const std::string &msg) {
   return code;
 }
 
-// Runs f(lo, hi) over [0, count) split into contiguous ranges on up to 16 host threads (inline
-// below min_count items). Every range writes disjoint outputs, so the result does not depend
-// on the split.
+// Runs f(lo, hi) over [0, count) split into contiguous ranges on up to 16 host threads, each
+// taking at least per_thread items (inline when there are fewer). Every range writes disjoint
+// outputs, so the result does not depend on the split.
 int host_threads() {
   const unsigned hw = std::thread::hardware_concurrency();
   return hw == 0 ? 1 : static_cast<int>(std::min<unsigned>(hw, 16u));
 }
 
 template <typename F>
-void parallel_ranges(int64_t count, F f, int64_t min_count = 8192) {
-  int64_t T = host_threads();
-  if (count < min_count) T = 1;
-  if (T > count) T = count > 0 ? count : 1;
+void parallel_ranges(int64_t count, F f, int64_t per_thread = 8192) {
+  const int64_t T = std::max<int64_t>(1, std::min<int64_t>(host_threads(), count / per_thread));
   if (T <= 1) {
     f(int64_t{0}, count);
     return;
@@ -648,8 +646,8 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
   //    thread t counts its clauses' occurrences of every variable; variable v's entries from
   //    thread t follow those of threads 0..t-1, so every list stays in clause order. (One
   //    thread when the per-thread counts would exceed 2^26 entries.)
-  int64_t TC = host_threads();
-  if (m < 8192 || TC * static_cast<int64_t>(n) > (int64_t(1) << 26)) TC = 1;
+  int64_t TC = std::max<int64_t>(1, std::min<int64_t>(host_threads(), m / 8192));
+  if (TC * static_cast<int64_t>(n) > (int64_t(1) << 26)) TC = 1;
   std::vector<int32_t> cnt(static_cast<size_t>(TC) * n, 0);
   auto by_clause_range = [&](auto &&body) {
     parallel_ranges(TC, [&](int64_t t0, int64_t t1) {
@@ -670,7 +668,7 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
       for (int64_t t = 0; t < TC; ++t) d += cnt[static_cast<size_t>(t) * n + v];
       deg[v] = d;
     }
-  });
+  }, 4096);
   int32_t dmax = 0;
   for (int32_t v = 0; v < n; ++v) dmax = deg[v] > dmax ? deg[v] : dmax;
   if (dmax > kMaxDegree)
@@ -687,7 +685,7 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
         o += k;
       }
     }
-  });
+  }, 4096);
   HostVec vcl(vptr[n] > 0 ? vptr[n] : 1);
   by_clause_range([&](int64_t t, int64_t a0, int64_t a1) {
     int32_t *c = &cnt[static_cast<size_t>(t) * n];
@@ -723,7 +721,7 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
         }
         for (; s < slots; ++s) slot[s] = lit_false;
       }
-  });
+  }, 1024);
   // the tie order of the colouring: more occurrences first, then the smaller id (a counting
   // sort by degree, stable in id)
   std::vector<int32_t> ord(n);
@@ -894,7 +892,7 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
         for (int z = 2; z < slots; ++z) slot[z] = lit_false;
       }
     }
-  });
+  }, 1024);
   // -- the same lists interleaved per group of 32 consecutive variables of a colour class
   //    (group g covers new ids [col_ptr[c] + 32k, +32)): occurrence j of the group's lane l
   //    sits at grp_base[g] + (j*kq + q)*32 + l (int4 units), so one warp load of occurrence j
@@ -954,7 +952,7 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
           }
       }
     }
-  }, 64);  // a group is 32 variables' lists: split from a few dozen groups on
+  }, 32);  // a group is 32 variables' lists
   HostVec clits(static_cast<size_t>(m > 0 ? m : 1) * K);
   if (m == 0) std::fill(clits.begin(), clits.end(), lit_false);
   parallel_ranges(m, [&](int64_t a0, int64_t a1) {
