@@ -677,6 +677,39 @@ def test_frozen_qap_facility_holds_and_the_rest_is_conditionally_boltzmann():
     assert _chi2_pvalue(counts, w / w.sum()) > 1e-4
 
 
+def test_schedule_is_read_at_the_sweep_and_the_variable_it_names():
+    """beta[v][t] is 0 (every attempt flips) or +inf (held), alternating in t with a phase of its
+    own per variable: after t1 sweeps variable v has flipped once for every free sweep t < t1,
+    so reading another sweep's column or another variable's row changes the final state."""
+    n, T, R = 40, 9, 33
+    lits = W.random_ksat(n, 4.2, 3, 19)
+    phase = W.seeded_subset(n, 0.5, 21).astype(np.int64)  # variable v is held when t % 2 == phase
+    t = np.arange(T)
+    held = (t[None, :] % 2) == phase[:, None]
+    beta = np.where(held, np.float32(np.inf), np.float32(0.0)).astype(np.float32)
+    x0 = O.ksat_anneal(lits, n, beta, 0, 0, seed=4, replicas=R)["states"]
+    for t1 in (1, 2, 5, 9):
+        res = O.ksat_anneal(lits, n, beta, 0, t1, seed=4, replicas=R)
+        free = (~held[:, :t1]).sum(axis=1) % 2
+        assert np.array_equal(res["states"], x0 ^ free[None, :].astype(np.uint8)), t1
+        assert np.array_equal(res["energies"], energies_numpy(lits, res["states"]))
+
+
+def test_qap_schedule_is_read_at_the_step_it_names():
+    """Every facility free at beta = 0 on even steps and held on odd ones: an odd step changes
+    no permutation, an even one changes almost all of them."""
+    n, R, T = 9, 64, 8
+    F, D = W.random_qap(n, 23)
+    beta = np.zeros((n, T), dtype=np.float32)
+    beta[:, 1::2] = np.inf
+    perms = [O.qap_anneal(F, D, beta, 0, t1, 6, replicas=R)["perms"] for t1 in range(T + 1)]
+    for t in range(T):
+        if t % 2:
+            assert np.array_equal(perms[t + 1], perms[t]), t
+        else:
+            assert (perms[t + 1] != perms[t]).any(axis=1).mean() > 0.9, t
+
+
 def _chain_of(lits, n, states):
     e = energies_numpy(lits, states)
     return dict(states=states.copy(), energies=e, best_states=states.copy(), best_energies=e.copy())
