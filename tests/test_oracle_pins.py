@@ -710,6 +710,35 @@ def test_qap_schedule_is_read_at_the_step_it_names():
             assert (perms[t + 1] != perms[t]).any(axis=1).mean() > 0.9, t
 
 
+def _perm_parity(p):
+    p, seen, odd = list(p), set(), 0
+    for i in range(len(p)):
+        if i in seen:
+            continue
+        j, length = i, 0
+        while j not in seen:
+            seen.add(j)
+            j, length = p[j], length + 1
+        odd ^= (length - 1) & 1
+    return odd
+
+
+def test_qap_step_is_n_transpositions_at_beta_zero():
+    """At beta = 0 every swap attempt is accepted and every attempt exchanges two distinct
+    facilities, so one step of n attempts multiplies the permutation's sign by (-1)^n. A step of
+    another length, or a proposal that can pick r = s, breaks the closed form."""
+    for n in (3, 4, 5, 7):
+        F, D = W.random_qap(n, 50 + n)
+        T, R = 6, 50
+        beta = np.zeros((n, T), dtype=np.float32)
+        p0 = O.qap_anneal(F, D, beta, 0, 0, 8, replicas=R)["perms"]
+        par0 = np.array([_perm_parity(p) for p in p0])
+        for t1 in range(1, T + 1):
+            pt = O.qap_anneal(F, D, beta, 0, t1, 8, replicas=R)["perms"]
+            part = np.array([_perm_parity(p) for p in pt])
+            assert np.array_equal(part, par0 ^ ((n * t1) & 1)), (n, t1)
+
+
 def _chain_of(lits, n, states):
     e = energies_numpy(lits, states)
     return dict(states=states.copy(), energies=e, best_states=states.copy(), best_energies=e.copy())
