@@ -4,8 +4,11 @@ TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the b
 CPU-baseline / reference leg. The product path (the CUDA library and its binding) never
 imports this package, and this package never imports the product.
 
-The definitions it implements are stated at the top of nmc_oracle.c. Every function here is
-a thin argument marshaller; all arithmetic is in the C file.
+The definitions it implements are stated at the top of nmc_oracle.c. Most functions here are
+thin argument marshallers over the C files. Four hold arithmetic of their own, in plain Python
+and numpy: `adaptive_ladder` and `qap_adaptive_ladder` (each level's sigma from the C anneal's
+energy sums, and the next beta = beta + alpha / sigma), `clause_degrees` (the default eps_i of the
+surrogate Hamiltonian) and `backbone_schedule` (the two-chain schedule as an array).
 
 Parity status: every function is pinned by tests/test_oracle_pins.py (brute-force
 enumeration, recomputation, closed forms, a chi-square against the exact Boltzmann law and an
@@ -57,6 +60,8 @@ def _load():
             lib.orc_uphill_threshold.restype = u32
             lib.orc_ksat_energy.argtypes = [i32, i32, i32, P, P]
             lib.orc_ksat_energy.restype = i64
+            lib.orc_ksat_energies.argtypes = [i32, i32, i32, P, i64, P, P]
+            lib.orc_ksat_energies.restype = None
             lib.orc_ksat_delta.argtypes = [i32, i32, i32, P, P, i32]
             lib.orc_ksat_delta.restype = i64
             lib.orc_ksat_colour.argtypes = [i32, i32, i32, P, P]
@@ -149,6 +154,15 @@ def ksat_energy(lits, n_vars: int, x) -> int:
     return int(_load().orc_ksat_energy(n_vars, m, k, _p(lits), _p(x)))
 
 
+def ksat_energies(lits, n_vars: int, X) -> np.ndarray:
+    """int64[S]: the energy of every row of X (S x N, 0/1)."""
+    lits, m, k = _cnf(lits)
+    X = _c(X, np.uint8).reshape(-1, n_vars)
+    e = np.zeros(X.shape[0], dtype=np.int64)
+    _load().orc_ksat_energies(n_vars, m, k, _p(lits), X.shape[0], _p(X), _p(e))
+    return e
+
+
 def ksat_delta(lits, n_vars: int, x, v: int) -> int:
     lits, m, k = _cnf(lits)
     x = _c(x, np.uint8)
@@ -235,8 +249,9 @@ def ksat_pt_anneal(lits, n_vars, beta, ladder, t0, t1, sweeps_per_round, seed, r
 def ksat_cluster_flip(lits, n_vars, chain, mask, beta, move_id, seed, replica_ids=None):
     """Collective move of every replica of `chain` (a dict as ksat_anneal returns: states,
     energies, best_states, best_energies): replica r proposes x xor mask_r (mask [1 or R, N] 0/1)
-    and accepts by the Metropolis rule at beta[r]. replica_ids: the id (Philox stream, mask row)
-    of each row, default 0..R-1. Returns a new dict of the same form plus `accepted` uint8[R]."""
+    and accepts by the Metropolis rule at beta[r]. A per-replica mask has one row per row of
+    `chain` (row r goes with states row r, like beta[r]). replica_ids: the id (Philox stream) of
+    each row, default 0..R-1. Returns a new dict of the same form plus `accepted` uint8[R]."""
     lits, m, k = _cnf(lits)
     st = np.array(chain["states"], dtype=np.uint8, order="C")
     bs = np.array(chain["best_states"], dtype=np.uint8, order="C")

@@ -236,6 +236,12 @@ int64_t orc_ksat_energy(int32_t n, int32_t m, int32_t kmax, const int32_t *lits,
   return e;
 }
 
+/* E of each of S assignments (rows of X, S x n uint8) into e[S]: orc_ksat_energy row by row. */
+void orc_ksat_energies(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, int64_t S,
+                       const uint8_t *X, int64_t *e) {
+  for (int64_t s = 0; s < S; ++s) e[s] = orc_ksat_energy(n, m, kmax, lits, X + s * n);
+}
+
 /* dE of flipping v, from the clauses that contain v: a clause whose only true literal is v's
  * becomes violated (+1); a violated clause becomes satisfied (-1). */
 static int64_t cnf_delta(const orc_cnf *f, const uint8_t *x, int v) {
@@ -856,8 +862,9 @@ int orc_qap_anneal(int32_t n, const int32_t *F, const int32_t *D, int32_t n_step
 /*
  * states: R*n uint8 in/out; energies, best_energies: R int64 in/out; best_states: R*n in/out.
  * mask: mask_rows*n uint8 (mask_rows 1: one mask for all replicas, or R). beta: R floats.
- * accepted: R uint8 out (nullable). rep_ids: the replica id of each row (its Philox stream and
- * mask row; NULL = 0..R-1). Returns 0 or -1 on a bad argument.
+ * accepted: R uint8 out (nullable). rep_ids: the replica id of each row, which picks its Philox
+ * stream (NULL = 0..R-1). Row r of a per-replica mask belongs to row r of the states, like beta[r],
+ * whatever its id. Returns 0 or -1 on a bad argument.
  */
 int orc_ksat_cluster_flip(int32_t n, int32_t m, int32_t kmax, const int32_t *lits, int32_t R,
                           uint8_t *states, int64_t *energies, uint8_t *best_states,
@@ -871,7 +878,7 @@ int orc_ksat_cluster_flip(int32_t n, int32_t m, int32_t kmax, const int32_t *lit
   for (int32_t r = 0; r < R; ++r) {
     const uint32_t id = rep_ids ? (uint32_t)rep_ids[r] : (uint32_t)r;
     uint8_t *x = states + (size_t)r * n;
-    const uint8_t *mr = mask + (size_t)(mask_rows == 1 ? 0 : id) * n;
+    const uint8_t *mr = mask + (size_t)(mask_rows == 1 ? 0 : r) * n;
     for (int32_t v = 0; v < n; ++v) y[v] = (uint8_t)(x[v] ^ (mr[v] & 1u));
     const int64_t e0 = orc_ksat_energy(n, m, kmax, lits, x);
     const int64_t e1 = orc_ksat_energy(n, m, kmax, lits, y);

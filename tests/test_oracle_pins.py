@@ -179,6 +179,51 @@ def test_energy_matches_enumeration(n, m, k, pad):
     assert want.min() >= 0
 
 
+def _energies_numpy_chunked(lits, n, chunk=1 << 15):
+    out = []
+    for s0 in range(0, 1 << n, chunk):
+        idx = np.arange(s0, min(s0 + chunk, 1 << n), dtype=np.int64)
+        X = ((idx[:, None] >> np.arange(n)[None, :]) & 1).astype(np.uint8)
+        out.append(energies_numpy(lits, X))
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("case", ["planted_3sat", "unsat_4sat", "padded_mixed"])
+def test_energy_and_ground_states_by_enumeration_n20(case):
+    """All 2^20 assignments of a 20-variable formula: the oracle's energy equals the independent
+    evaluator on every one, and the ground-state energy and the set of ground states agree. A
+    formula with a planted solution (clauses that solution violates are dropped) has ground
+    energy 0 with the planted state among its ground states, each of which satisfies every clause
+    when checked literal by literal; an over-constrained 4-SAT formula has no solution."""
+    n = 20
+    rng = np.random.default_rng({"planted_3sat": 1, "unsat_4sat": 2, "padded_mixed": 3}[case])
+    if case == "planted_3sat":
+        lits = small_cnf(n, 140, 3, seed=201)
+        plant = rng.integers(0, 2, size=n, dtype=np.uint8)
+        keep = [energies_numpy(row[None], plant[None])[0] == 0 for row in lits]
+        lits = lits[np.array(keep)]
+    elif case == "unsat_4sat":
+        lits = small_cnf(n, 400, 4, seed=202)
+    else:
+        lits = small_cnf(n, 180, 5, seed=203, pad_some=True)
+    X = all_states(n)
+    got = O.ksat_energies(lits, n, X)
+    want = _energies_numpy_chunked(lits, n)
+    assert np.array_equal(got, want)
+    e0 = int(want.min())
+    ground = set(np.nonzero(got == e0)[0].tolist())
+    assert ground == set(np.nonzero(want == e0)[0].tolist())
+    if case == "planted_3sat":
+        assert e0 == 0
+        assert int((plant.astype(np.int64) << np.arange(n)).sum()) in ground
+        for s in list(ground)[:64]:
+            x = X[s]
+            for row in lits:
+                assert any(x[abs(l) - 1] == (l > 0) for l in row if l != 0)
+    if case == "unsat_4sat":
+        assert e0 > 0
+
+
 def test_energy_of_generated_instance_matches_independent_count():
     lits = W.random_ksat(300, 9.6, 4, 11)
     rng = np.random.default_rng(1)
@@ -378,16 +423,23 @@ def _qap_cost_numpy(F, D, p):
     return int((F * D[np.ix_(p, p)]).sum())
 
 
-@pytest.mark.parametrize("n", [3, 5, 7])
+@pytest.mark.parametrize("n", [3, 5, 7, 8])
 def test_qap_cost_matches_enumeration(n):
+    """All n! permutations (n <= 8): the oracle's cost equals the independent evaluator on every
+    one, and so do the optimum and the set of optimal permutations."""
     F, D = W.random_qap(n, 40 + n)
-    costs = []
-    for perm in itertools.permutations(range(n)):
-        p = np.array(perm, dtype=np.int16)
-        c = O.qap_cost(F, D, p)
-        assert c == _qap_cost_numpy(F, D, p)
-        costs.append(c)
-    assert min(costs) >= 0
+    perms = np.array(list(itertools.permutations(range(n))), dtype=np.int16)
+    got = np.array([O.qap_cost(F, D, p) for p in perms])
+    # independent evaluator, vectorised over the permutations: sum_ij F_ij D_{p(i) p(j)}
+    P = perms.astype(np.int64)
+    want = (F[None, :, :] * D[P[:, :, None], P[:, None, :]]).sum(axis=(1, 2))
+    assert np.array_equal(got, want)
+    assert want.min() >= 0
+    best = int(want.min())
+    assert set(np.nonzero(got == best)[0].tolist()) == set(np.nonzero(want == best)[0].tolist())
+    # F and D symmetric with zero diagonals: every unordered pair is counted twice, so every
+    # cost is even
+    assert np.all(got % 2 == 0)
 
 
 def test_qap_swap_delta_matches_recomputation():
@@ -766,6 +818,29 @@ def test_cluster_flip_limits():
     # one shared mask row acts on every replica
     one = O.ksat_cluster_flip(lits, n, ch, M[:1], 0.0, 1, 9)
     assert np.array_equal(one["states"], X ^ M[:1])
+
+
+def test_cluster_flip_sampled_replicas_with_their_own_masks():
+    """A sample of replicas, given by id with one mask row per row passed, moves exactly as the
+    same replicas do inside the whole set (ids far beyond the sample's size included): the id
+    picks the Philox stream, row r of the mask goes with row r of the states."""
+    n, R = 40, 64
+    lits = W.random_ksat(n, 4.2, 3, 32)
+    rng = np.random.default_rng(6)
+    X = rng.integers(0, 2, size=(R, n), dtype=np.uint8)
+    M = rng.integers(0, 2, size=(R, n), dtype=np.uint8)
+    beta = np.linspace(0.2, 1.5, R).astype(np.float32)
+    whole = O.ksat_cluster_flip(lits, n, _chain_of(lits, n, X), M, beta, 7, 11)
+    assert 0 < int(whole["accepted"].sum()) < R  # both outcomes occur
+    ids = np.array([63, 5, 40, 0, 62])
+    part = O.ksat_cluster_flip(lits, n, _chain_of(lits, n, X[ids]), M[ids], beta[ids], 7, 11,
+                               replica_ids=ids)
+    for key in ("states", "energies", "best_energies", "best_states", "accepted"):
+        assert np.array_equal(part[key], whole[key][ids]), key
+    # a mask with neither one row nor one per row passed is rejected
+    with pytest.raises(ValueError):
+        O.ksat_cluster_flip(lits, n, _chain_of(lits, n, X[ids]), M, beta[ids], 7, 11,
+                            replica_ids=ids)
 
 
 def test_cluster_flip_accepts_with_the_boltzmann_factor():
