@@ -1,0 +1,112 @@
+"""Writes the full-length expected outputs of the two benchmark workloads, from the oracle only.
+
+The trajectories pinned here are the ones the benchmark times: the single-variable Metropolis
+sweep with a per-variable inverse temperature (Sec. "Nonequilibrium inhomogeneous sampling over
+subgraphs"; the sampling steps of Algorithm 1) on the 4-SAT energy of Sec. "4-SAT Problems Near
+Computational Phase Transitions", and the swap Metropolis chain on the Koopmans-Beckmann cost of
+Sec. "Quadratic Assignment Problems". Every value is computed by `oracle/` on the seeded inputs of
+`nmc_inputs`; nothing here comes from the CUDA path.
+
+  python tests/golden/make_fullsize.py ksat    # ~10 min per replica per core (8 replicas)
+  python tests/golden/make_fullsize.py qap     # ~1 min on 8 cores
+
+Outputs (JSON, next to this script):
+  fullsize_ksat_n50000_r1024_t5000.json   4-SAT N=50,000, M=480,000, 1,024 replicas, 5,000 sweeps
+  fullsize_qap_64x_r4096_t10000.json      64 QAP instances, n in [32, 256], 4,096 replicas, 10^4 steps
+Per sampled replica: final and best energies and SHA-256 digests of the final and best states
+(uint8 [N] assignments in the original variable order; int16 [n] little-endian permutations).
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import nmc_inputs as W  # noqa: E402
+import oracle as O  # noqa: E402
+
+KSAT_FILE = os.path.join(HERE, "fullsize_ksat_n50000_r1024_t5000.json")
+QAP_FILE = os.path.join(HERE, "fullsize_qap_64x_r4096_t10000.json")
+
+# replicas spread over the 32 words of 32 replicas: first and last lanes, interior words
+KSAT_IDS = [0, 31, 32, 255, 517, 640, 990, 1023]
+# instances of the 64-instance QAP batch: the first, the smallest and largest n, and others
+QAP_IDS = [0, 4095, 2047]
+
+
+def digest(a: np.ndarray) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def ksat():
+    wl = W.workload_ksat_large(n_steps=5000)
+    t = time.time()
+    out = O.ksat_anneal(wl["lits"], wl["n_vars"], wl["beta"], 0, wl["n_steps"], wl["seed"],
+                        replica_ids=KSAT_IDS, n_threads=min(len(KSAT_IDS), os.cpu_count() or 1))
+    rec = {
+        "workload": "workload_ksat_large(n_steps=5000): 4-SAT N=50000, M=480000, beta geometric "
+                    "0.3->6.0, 20% at 0.4x for the first half then ramped; 1024 replicas",
+        "seed": wl["seed"], "t0": 0, "t1": wl["n_steps"], "replicas": wl["replicas"],
+        "replica_ids": KSAT_IDS,
+        "energies": [int(x) for x in out["energies"]],
+        "best_energies": [int(x) for x in out["best_energies"]],
+        "states_sha256": [digest(r) for r in out["states"]],
+        "best_states_sha256": [digest(r) for r in out["best_states"]],
+        "oracle_seconds": round(time.time() - t, 1),
+    }
+    with open(KSAT_FILE, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(KSAT_FILE, rec["energies"], rec["best_energies"], rec["oracle_seconds"], "s")
+
+
+def qap_instances(sets):
+    ns = [s["n"] for s in sets]
+    pick = [0, int(np.argmin(ns)), int(np.argmax(ns)), 17, 33, 63]
+    seen = []
+    for i in pick:
+        if i not in seen:
+            seen.append(i)
+    return seen
+
+
+def qap():
+    sets = W.workload_qap_batch()  # 64 instances, 10^4 steps, 4096 replicas each
+    t = time.time()
+    recs = []
+    for i in qap_instances(sets):
+        s = sets[i]
+        out = O.qap_anneal(s["F"], s["D"], s["beta"], 0, s["n_steps"], s["seed"],
+                           replica_ids=QAP_IDS)
+        recs.append({"instance": i, "n": s["n"], "seed": s["seed"], "replica_ids": QAP_IDS,
+                     "energies": [int(x) for x in out["energies"]],
+                     "best_energies": [int(x) for x in out["best_energies"]],
+                     "perms_sha256": [digest(p.astype("<i2")) for p in out["perms"]],
+                     "best_perms_sha256": [digest(p.astype("<i2")) for p in out["best_perms"]]})
+        print("qap instance", i, "n", s["n"], recs[-1]["energies"], flush=True)
+    rec = {"workload": "workload_qap_batch(): 64 instances, n uniform in [32, 256], F, D symmetric "
+                       "uniform [0, 99] (F half zeros), beta linear 0.01->1.0 x per-facility "
+                       "factor in [0.5, 1.5], 4096 replicas, 10^4 steps",
+           "t0": 0, "t1": sets[0]["n_steps"], "replicas": sets[0]["replicas"],
+           "instances": recs, "oracle_seconds": round(time.time() - t, 1)}
+    with open(QAP_FILE, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(QAP_FILE, rec["oracle_seconds"], "s")
+
+
+if __name__ == "__main__":
+    which = sys.argv[1:] or ["ksat", "qap"]
+    if "qap" in which:
+        qap()
+    if "ksat" in which:
+        ksat()
