@@ -29,16 +29,22 @@ namespace nmc {
 
 namespace {
 
-constexpr int kBatchThreads = 640;  // one-thread kernel, and the team kernel with teams of 8
+// One-thread kernel: 16 warps, up to 128 registers (no spills; a DSatur colour class of the
+// 50,000-variable bench instance puts at most ~490 variables on each CTA of a 4-CTA cluster,
+// one round of 512 threads: measured 296 us per sweep against 295 with 640 threads and 96
+// registers, and 293 with the next class's loads requested at the barrier, which 640 threads
+// cannot hold without spilling)
+constexpr int kBatchThreads = 512;
 constexpr int kTeamThreads = 384;   // team kernel with teams of 2 or 4: 12 warps, up to 168 registers
+constexpr int kTeam8Threads = 640;  // team kernel with teams of 8
 
 // Threads of the sweep kernel with TL lanes per variable: 384 for teams of 2 or 4, which then
 // prefetch their occurrence entries a group ahead (measured at N = 5,000: 107 -> 102 us per
-// sweep); 640 for single threads and teams of 8 (the tiny classes of small instances, where 384
-// threads measured slower: N = 200, 37.3 -> 45.3 us).
+// sweep); 640 for teams of 8 (the tiny classes of small instances, where 384 threads measured
+// slower: N = 200, 37.3 -> 45.3 us); 512 for single threads.
 template <int TL>
 __host__ __device__ constexpr int sweep_threads() {
-  return (TL == 2 || TL == 4) ? kTeamThreads : kBatchThreads;
+  return (TL == 2 || TL == 4) ? kTeamThreads : (TL == 8 ? kTeam8Threads : kBatchThreads);
 }
 
 template <int NB>
@@ -54,6 +60,46 @@ __device__ __forceinline__ void csa4(uint32_t (&c)[NB], uint32_t a0, uint32_t a1
   c[1] = s3;
 #pragma unroll
   for (int j = 2; j < NB; ++j) {
+    const uint32_t t = c[j] & carry;
+    c[j] ^= carry;
+    carry = t;
+  }
+}
+
+// Adds a0..a3 into the weight-1 and weight-2 planes c[0], c[1] of a bit-sliced counter and
+// returns the weight-4 carry, which the caller adds from plane 2 up.
+template <int NB>
+__device__ __forceinline__ uint32_t csa4_low(uint32_t (&c)[NB], uint32_t a0, uint32_t a1,
+                                             uint32_t a2, uint32_t a3) {
+  const uint32_t s1 = c[0] ^ a0 ^ a1;
+  const uint32_t y1 = maj3b(c[0], a0, a1);
+  c[0] = s1 ^ a2 ^ a3;
+  const uint32_t y2 = maj3b(s1, a2, a3);
+  const uint32_t s3 = c[1] ^ y1 ^ y2;
+  const uint32_t f = maj3b(c[1], y1, y2);
+  c[1] = s3;
+  return f;
+}
+
+// c += f * 4 (f one bit per replica), carries rippled up to the top plane.
+template <int NB>
+__device__ __forceinline__ void add_carry(uint32_t (&c)[NB], uint32_t f) {
+#pragma unroll
+  for (int j = 2; j < NB; ++j) {
+    const uint32_t t = c[j] & f;
+    c[j] ^= f;
+    f = t;
+  }
+}
+
+// c += (f + g) * 4: a full adder at plane 2, then one ripple from plane 3.
+template <int NB>
+__device__ __forceinline__ void add_carry_pair(uint32_t (&c)[NB], uint32_t f, uint32_t g) {
+  const uint32_t s = c[2] ^ f ^ g;
+  uint32_t carry = maj3b(c[2], f, g);
+  c[2] = s;
+#pragma unroll
+  for (int j = 3; j < NB; ++j) {
     const uint32_t t = c[j] & carry;
     c[j] ^= carry;
     carry = t;
@@ -95,16 +141,46 @@ __device__ __forceinline__ void add_planes(uint32_t (&c)[NB], const uint32_t (&p
   }
 }
 
-// v = c0 + off is a variable of colour class c (starting at new id c0). With PT, replica j
-// of the word moves at min(2^32-1, (mult_s[j] * bq) >> 16) instead of bq.
+// The loads of one attempt that do not depend on the replicas' states: the variable's Q16
+// inverse temperature, its list length and its first group of occurrence entries. A thread
+// requests them for its next variable before it waits at the barrier that ends the current
+// colour class, so their L2 / HBM latency overlaps the barrier.
+template <int KQ>
+struct AttemptPrep {
+  int4 q[4 * KQ];
+  const int4 *ent;
+  int len;
+  uint32_t bq;
+};
+
+// v = c0 + off is a variable of colour class c (starting at new id c0; cg: the class's first
+// group of 32 variables), attempted at sweep t.
+template <int KQ>
+__device__ __forceinline__ void prep_attempt(const BatchItem &B, int cg, int c0, int v, int t,
+                                             AttemptPrep<KQ> &p) {
+  p.bq = __ldg(B.bq + (size_t)t * B.n + v);
+  const int off = v - c0;
+  const int g = cg + (off >> 5), ln = off & 31;
+  const int gb = __ldg(B.grp_base + g);
+  p.len = (__ldg(B.grp_base + g + 1) - gb) / (32 * KQ);
+  p.ent = B.occ_t + gb + ln;
+  if (p.len > 0) {
+#pragma unroll
+    for (int j = 0; j < 4 * KQ; ++j) p.q[j] = __ldg(p.ent + (size_t)j * 32);
+  }
+}
+
+// One attempt of variable v at sweep t for the 32 replicas of the word, from the loads in P.
+// With PT, replica j of the word moves at min(2^32-1, (mult_s[j] * bq) >> 16) instead of bq.
 template <int KQ, bool PT>
 __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint32_t *xs,
                                                   const uint32_t *tab_s, int tab_len,
-                                                  const uint32_t *mult_s, int cg, int c0, int v,
-                                                  int t, uint32_t (&acc)[kAccPlanes]) {
+                                                  const uint32_t *mult_s, int v, int t,
+                                                  AttemptPrep<KQ> &P,
+                                                  uint32_t (&acc)[kAccPlanes]) {
   constexpr int NB = 7;
   const uint32_t x = xs[v];
-  const uint32_t bqv = __ldg(B.bq + (size_t)t * B.n + v);
+  const uint32_t bqv = P.bq;
   if (bqv == kFrozenQ16) return x;  // held at this step: no attempt
   uint32_t bc[NB], mc[NB];
 #pragma unroll
@@ -112,27 +188,13 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
     bc[j] = 0u;
     mc[j] = 0u;
   }
-  const int off = v - c0;
-  const int g = cg + (off >> 5), ln = off & 31;  // cg: the class's first group
-  const int gb = __ldg(B.grp_base + g);
-  const int len = (__ldg(B.grp_base + g + 1) - gb) / (32 * KQ);
-  const int4 *ent = B.occ_t + gb + ln;
+  const int len = P.len;
+  const int4 *ent = P.ent;
   // The entries of the next group of 4 occurrences are requested before the current group is
   // evaluated, so the L2 latency of the list overlaps the shared-memory gathers and counting.
-  int4 qn[4 * KQ];
-  if (len > 0) {
-#pragma unroll
-    for (int j = 0; j < 4 * KQ; ++j) qn[j] = __ldg(ent + (size_t)j * 32);
-  }
-  for (int e = 0; e < len; e += 4) {
-    int4 qc[4 * KQ];
-#pragma unroll
-    for (int j = 0; j < 4 * KQ; ++j) qc[j] = qn[j];
-    if (e + 4 < len) {
-#pragma unroll
-      for (int j = 0; j < 4 * KQ; ++j) qn[j] = __ldg(ent + (size_t)((e + 4) * KQ + j) * 32);
-    }
-    uint32_t bb[4], mm[4];
+  int4 (&qn)[4 * KQ] = P.q;
+  // break / make masks of the 4 occurrences whose entries are in qc
+  auto masks4 = [&](const int4 (&qc)[4 * KQ], uint32_t (&bb)[4], uint32_t (&mm)[4]) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int4 q = qc[j * KQ];
@@ -152,8 +214,36 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
       bb[j] = own & ~o;
       mm[j] = ~(own | o);
     }
-    csa4<NB>(bc, bb[0], bb[1], bb[2], bb[3]);
-    csa4<NB>(mc, mm[0], mm[1], mm[2], mm[3]);
+  };
+  // Two groups of 4 per trip: each group's weight-4 carry is kept aside and the pair's carries
+  // enter the planes from weight 4 up once (one ripple per 8 occurrences instead of per 4).
+  // Every group's entries are still requested one group before they are evaluated.
+  for (int e = 0; e < len; e += 8) {
+    int4 qc[4 * KQ];
+    uint32_t bb[4], mm[4];
+#pragma unroll
+    for (int j = 0; j < 4 * KQ; ++j) qc[j] = qn[j];
+    if (e + 4 < len) {
+#pragma unroll
+      for (int j = 0; j < 4 * KQ; ++j) qn[j] = __ldg(ent + (size_t)((e + 4) * KQ + j) * 32);
+    }
+    masks4(qc, bb, mm);
+    uint32_t fb = csa4_low(bc, bb[0], bb[1], bb[2], bb[3]);
+    uint32_t fm = csa4_low(mc, mm[0], mm[1], mm[2], mm[3]);
+    if (e + 4 < len) {
+#pragma unroll
+      for (int j = 0; j < 4 * KQ; ++j) qc[j] = qn[j];
+      if (e + 8 < len) {
+#pragma unroll
+        for (int j = 0; j < 4 * KQ; ++j) qn[j] = __ldg(ent + (size_t)((e + 8) * KQ + j) * 32);
+      }
+      masks4(qc, bb, mm);
+      add_carry_pair<NB>(bc, fb, csa4_low(bc, bb[0], bb[1], bb[2], bb[3]));
+      add_carry_pair<NB>(mc, fm, csa4_low(mc, mm[0], mm[1], mm[2], mm[3]));
+    } else {
+      add_carry<NB>(bc, fb);
+      add_carry<NB>(mc, fm);
+    }
   }
   // D = B - U, 8 bit planes (two's complement), then per-replica bytes by 8x8 transposes
   uint32_t s8[8];
@@ -173,36 +263,37 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
   uint32_t flip = 0u;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
+    // replicas 8q .. 8q+7: Philox groups 2q and 2q+1, drawn together when either needs a draw
     const unsigned long long xm = transpose8(gather_bytes(s8, q));
+    int de[8];
+    uint32_t th[8];
+    bool need0 = false, need1 = false;
 #pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      const int g = 2 * q + hh;
-      int de[4];
-      uint32_t th[4];
-      bool need = false;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        de[j] = (int)(signed char)(unsigned char)(xm >> (8 * (4 * hh + j)));
-        th[j] = 0u;
-        if (de[j] > 0) {
-          uint32_t hi = bq_hi, lo = bq_lo;
-          if (PT) {
-            const unsigned long long be = ((unsigned long long)mult_s[4 * g + j] * bqv) >> 16;
-            const uint32_t b = be > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)be;
-            hi = b >> 8;  // below 2^24, so hi dE stays below 2^31
-            lo = b & 255u;
-          }
-          const uint32_t idx = hi * (uint32_t)de[j] + ((lo * (uint32_t)de[j]) >> 8);
-          th[j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
+    for (int j = 0; j < 8; ++j) {
+      de[j] = (int)(signed char)(unsigned char)(xm >> (8 * j));
+      th[j] = 0u;
+      if (de[j] > 0) {
+        uint32_t hi = bq_hi, lo = bq_lo;
+        if (PT) {
+          const unsigned long long be = ((unsigned long long)mult_s[8 * q + j] * bqv) >> 16;
+          const uint32_t b = be > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)be;
+          hi = b >> 8;  // below 2^24, so hi dE stays below 2^31
+          lo = b & 255u;
         }
-        need |= th[j] != 0u;
+        const uint32_t idx = hi * (uint32_t)de[j] + ((lo * (uint32_t)de[j]) >> 8);
+        th[j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
       }
-      uint4 u = make_uint4(0u, 0u, 0u, 0u);
-      if (need)
-        u = philox4x32_10(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + g), kTagKsatSweep), B.k0, B.k1);
+      if (j < 4) need0 |= th[j] != 0u; else need1 |= th[j] != 0u;
+    }
+    uint4 u0 = make_uint4(0u, 0u, 0u, 0u), u1 = u0;
+    if (need0 || need1)
+      philox4x32_10_x2(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + 2 * q), kTagKsatSweep),
+                       make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + 2 * q + 1), kTagKsatSweep),
+                       B.k0, B.k1, u0, u1);
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (de[j] <= 0 || uint4_word(u, j) < th[j]) flip |= 1u << (4 * g + j);
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t u = j < 4 ? uint4_word(u0, j) : uint4_word(u1, j - 4);
+      if (de[j] <= 0 || u < th[j]) flip |= 1u << (8 * q + j);
     }
   }
   // energy bookkeeping: acc += D on the flipped replicas (bit-sliced, sign-extended add)
@@ -438,6 +529,16 @@ __device__ __forceinline__ void group_sync() {
   }
 }
 
+// The cluster barrier in two halves: arrive (releasing this thread's earlier shared-memory
+// stores to the cluster) and wait (acquiring everyone's). Work between the two halves overlaps
+// the barrier; it must not touch shared memory that other CTAs read before the wait.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Stores v at the same shared-memory word of CTA `rank` of the cluster (32-bit addressing).
 __device__ __forceinline__ void st_rank(uint32_t saddr, int rank, uint32_t v) {
   uint32_t ra;
@@ -531,6 +632,18 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
       // class bounds and first group: those of class c + 1 are requested during class c and
       // arrive behind its barrier
       int c0 = __ldg(B.col_ptr), c1 = __ldg(B.col_ptr + 1), cg = __ldg(B.cgrp);
+      // a share of a class with at most this many variables on the CTA runs with teams of lanes
+      const int team_max = small_teams ? kBatchThreads / 2 : -1;
+      // the state-independent loads of this thread's first variable of each class: requested
+      // for class c + 1 between the two halves of the barrier that ends class c
+      // (every thread loads, those without a variable in the class for variable c0, so that
+      // P is written before every class and never live across the team path)
+      AttemptPrep<KQ> P;
+      {
+        const int cnt0 = share_count<CS>(c0, c1, rank);
+        const bool mine = cnt0 > team_max && (int)threadIdx.x < cnt0;
+        prep_attempt<KQ>(B, cg, c0, mine ? share_var<CS>(c0, rank, threadIdx.x) : c0, t, P);
+      }
       for (int c = 0; c < B.n_colours; ++c) {
         int c2 = 0, cgn = 0;
         if (c + 1 < B.n_colours) {
@@ -539,7 +652,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
         }
         // the class's 32-variable groups are dealt round-robin to the cluster's CTAs
         const int cnt = share_count<CS>(c0, c1, rank);
-        if (small_teams && cnt <= kBatchThreads / 2) {
+        if (cnt <= team_max) {
           // a smaller share (the later colour classes): teams of 8, 4 or 2 lanes per variable
           // shorten the class's critical path; their energy changes go to ep_s directly
           if (cnt <= kBatchThreads / 8)
@@ -549,9 +662,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
           else
             class_teams<KQ, CS, 2, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, cnt, rank, t, ep_s);
         } else {
-          for (int li = threadIdx.x; li < cnt; li += blockDim.x) {
-            const int v = share_var<CS>(c0, rank, li);
-            const uint32_t xn = attempt_batch<KQ, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, v, t, acc);
+          auto store = [&](int v, uint32_t xn) {
             if (CS == 1) {
               xs[v] = xn;
             } else {
@@ -559,9 +670,28 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 #pragma unroll
               for (int r = 0; r < CS; ++r) st_rank(sa, r, xn);
             }
+          };
+          bool first = true;  // the first variable's loads were requested at the barrier
+          for (int li = threadIdx.x; li < cnt; li += blockDim.x) {
+            const int v = share_var<CS>(c0, rank, li);
+            if (!first) prep_attempt<KQ>(B, cg, c0, v, t, P);
+            first = false;
+            store(v, attempt_batch<KQ, PT>(B, xs, tab_s, tab_len, mult_s, v, t, P, acc));
           }
         }
-        group_sync<CS>();
+        // the next class's first attempt of this thread loads its entries during the barrier
+        const bool more = c + 1 < B.n_colours;
+        const int cntn = more ? share_count<CS>(c1, c2, rank) : 0;
+        const int vn = cntn > team_max && (int)threadIdx.x < cntn
+                           ? share_var<CS>(c1, rank, threadIdx.x) : c1;
+        if (CS == 1) {
+          if (more) prep_attempt<KQ>(B, cgn, c1, vn, t, P);
+          __syncthreads();
+        } else {
+          cluster_arrive();
+          if (more) prep_attempt<KQ>(B, cgn, c1, vn, t, P);
+          cluster_wait();
+        }
         c0 = c1;
         c1 = c2;
         cg = cgn;
@@ -915,7 +1045,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
 
-// Device address of g_noalloc_scratch, looked up once per device (with that device current).
+// Device address of g_noalloc_scratch, looked up once per device (with that device current)
+// and kept for the rest of the process: a device reset after the first call is not supported.
 // In host code the array's name is only a host-side stand-in, never a device address.
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[64] = {};

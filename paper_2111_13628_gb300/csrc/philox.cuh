@@ -24,6 +24,27 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// Two Philox4x32-10 blocks under one key, their rounds interleaved (the same definition as
+// philox4x32_10, twice: more independent work per thread than two calls in sequence).
+__device__ __forceinline__ void philox4x32_10_x2(uint4 a, uint4 b, uint32_t k0, uint32_t k1,
+                                                 uint4 &ua, uint4 &ub) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t alo0 = 0xD2511F53u * a.x, ahi0 = __umulhi(0xD2511F53u, a.x);
+    const uint32_t alo1 = 0xCD9E8D57u * a.z, ahi1 = __umulhi(0xCD9E8D57u, a.z);
+    const uint32_t blo0 = 0xD2511F53u * b.x, bhi0 = __umulhi(0xD2511F53u, b.x);
+    const uint32_t blo1 = 0xCD9E8D57u * b.z, bhi1 = __umulhi(0xCD9E8D57u, b.z);
+    a = make_uint4(ahi1 ^ a.y ^ k0, alo1, ahi0 ^ a.w ^ k1, alo0);
+    b = make_uint4(bhi1 ^ b.y ^ k0, blo1, bhi0 ^ b.w ^ k1, blo0);
+  }
+  ua = a;
+  ub = b;
+}
+
 __device__ __forceinline__ uint32_t uint4_word(const uint4 &u, int j) {
   return j == 0 ? u.x : (j == 1 ? u.y : (j == 2 ? u.z : u.w));
 }
