@@ -152,7 +152,10 @@ int nmc_replicas_restore(nmc_ctx *ctx, int32_t rs, const nmc_result *in);
 int nmc_replicas_destroy(nmc_ctx *ctx, int32_t rs);
 /*
  * Runs sweeps (k-SAT) or steps (QAP) t0..t1-1 of the schedule on the resident replica set,
- * asynchronously on the context's stream. A k-SAT set that nmc_batch_run accepts runs on that
+ * asynchronously on the context's stream: the single-variable Metropolis dynamics with each
+ * variable (facility) at its own inverse temperature beta[unit][t] of the sampling stage
+ * (Sec. "Nonequilibrium inhomogeneous sampling over subgraphs"; the sampling and unlearning
+ * sweeps of Algorithm 1; swap moves on the cost of Sec. "Quadratic Assignment Problems"). A k-SAT set that nmc_batch_run accepts runs on that
  * (shared-memory, cluster) kernel, any other on the grid-barrier kernel; the results are the
  * same bit for bit (the environment variable NMC_RUN_PATH=grid forces the grid kernel). t is absolute, so [t0,t1) then [t1,t2) equals
  * [t0,t2) bit for bit. Requires 0 <= t0 <= t1 <= n_steps of the current schedule
@@ -186,12 +189,13 @@ int nmc_batch_run(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t
  * context allocates. Limit: one call takes at most (1 MiB - 256 B) / 136 B = 7708 work items,
  * one per 32-replica word of each set (NMC_EINVAL beyond, with a message). The array is
  * reserved on every GPU that loads the library until the process exits. The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress, with that device current).
- * Each call copies its work list into the array from host memory that lives only during the
- * call, so the call is not for stream capture: a graph replay would copy from freed memory.
- * Every call shares the one array, which keeps the last call's work list: calls whose launches
- * overlap on the GPU (other streams, other contexts, other host threads) race on it and must be
- * serialised by the caller.
+ * device does the set-up: it looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and keeps it for the rest of the process, so make that first call
+ * before any stream capture, and do not reset the device (cudaDeviceReset) after it. Each call
+ * copies its work list into the array from host memory and clears the counters on the stream
+ * before its launches. Every call shares the one array, which keeps the last call's work
+ * list: calls whose launches overlap on the GPU (other streams, other contexts, other host
+ * threads) race on it and must be serialised by the caller.
  */
 int nmc_batch_run_noalloc(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t0,
                           const int32_t *t1);
@@ -357,8 +361,10 @@ int nmc_adaptive_ladder(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t s
                         int32_t *n_temps_out);
 
 /*
- * One-shot anneal through host memory: creates a replica set, runs [t0, t1), copies the
- * results to the host buffers in *out and frees the set. Arguments as above.
+ * One-shot anneal through host memory: creates a replica set, runs [t0, t1) of the sampling
+ * stage's inhomogeneous Metropolis dynamics (Sec. "Nonequilibrium inhomogeneous sampling over
+ * subgraphs"; Algorithm 1's sampling sweeps; as nmc_replicas_run), copies the results to the
+ * host buffers in *out and frees the set. Arguments as above.
  */
 int nmc_anneal(nmc_ctx *ctx, int32_t inst, int32_t replicas, int32_t t0, int32_t t1,
                uint64_t seed, const void *init_states, const nmc_result *out);
@@ -408,7 +414,8 @@ int nmc_server_submit_qap(nmc_server *srv, int32_t n, const int32_t *F, const in
  * up to wait_ms for completion (0: no wait). */
 int nmc_server_poll(nmc_server *srv, int64_t req, int32_t wait_ms, int32_t *status);
 /* Copies a finished request's results to host buffers (layout as nmc_replicas_read; fields may
- * be NULL), reports its latency from submission to completion in seconds, and forgets it.
+ * be NULL), reports its latency in seconds from the start of its submit call (so the host-side
+ * build of a k-SAT instance, done inside that call, is included) to completion, and forgets it.
  * Returns the request's error code if it failed, NMC_ESTATE if it is not finished. */
 int nmc_server_result(nmc_server *srv, int64_t req, const nmc_result *out, double *latency_s);
 /* Asks for a request to be dropped at the next tick (its status becomes NMC_ESTATE). */

@@ -259,9 +259,12 @@ void worker_loop(nmc_server *s) {
   s->active.clear();
 }
 
-int submit(nmc_server *s, std::shared_ptr<Request> r, int64_t *id_out) {
+// t_arrive: when the submit call began, so that a request's latency includes the host-side
+// build of its instance (checks, colouring, lists) as well as its queueing and device time.
+int submit(nmc_server *s, std::shared_ptr<Request> r, Clock::time_point t_arrive,
+           int64_t *id_out) {
   r->mem = estimate_bytes(*r);
-  r->t_submit = Clock::now();
+  r->t_submit = t_arrive;
   std::lock_guard<std::mutex> g(s->mu);
   if (s->stop) return NMC_ESTATE;
   r->id = s->next_id++;
@@ -311,6 +314,7 @@ int nmc_server_create(int device, const nmc_server_config *cfg, nmc_server **out
 int nmc_server_submit_ksat(nmc_server *s, int32_t n_vars, int32_t n_clauses, int32_t k_max,
                            const int32_t *lits, const nmc_schedule *sched, int32_t replicas,
                            uint64_t seed, int64_t *req_out) {
+  const auto t_arrive = Clock::now();
   if (!s || !req_out || n_vars < 1 || n_clauses < 0 || k_max < 1 || k_max > 8 ||
       (n_clauses > 0 && !lits) || replicas < 1 || replicas > 4096)
     return NMC_EINVAL;
@@ -326,12 +330,13 @@ int nmc_server_submit_ksat(nmc_server *s, int32_t n_vars, int32_t n_clauses, int
   // formula is reported by the request's status, as any admission failure
   nmc::prepare_ksat(n_vars, n_clauses, k_max, lits, &r->prep);
   r->batchable = r->prep.code == NMC_OK && r->prep.nb <= 7 && n_vars <= s->batch_max_vars;
-  return submit(s, r, req_out);
+  return submit(s, r, t_arrive, req_out);
 }
 
 int nmc_server_submit_qap(nmc_server *s, int32_t n, const int32_t *F, const int32_t *D,
                           const nmc_schedule *sched, int32_t replicas, uint64_t seed,
                           int64_t *req_out) {
+  const auto t_arrive = Clock::now();
   if (!s || !req_out || n < 1 || !F || !D || replicas < 1 || replicas > 4096) return NMC_EINVAL;
   auto r = std::make_shared<Request>();
   r->kind = NMC_KIND_QAP;
@@ -341,7 +346,7 @@ int nmc_server_submit_qap(nmc_server *s, int32_t n, const int32_t *F, const int3
   if (!copy_schedule(*r, sched, n)) return NMC_EINVAL;
   r->F.assign(F, F + static_cast<size_t>(n) * n);
   r->D.assign(D, D + static_cast<size_t>(n) * n);
-  return submit(s, r, req_out);
+  return submit(s, r, t_arrive, req_out);
 }
 
 int nmc_server_poll(nmc_server *s, int64_t req, int32_t wait_ms, int32_t *status) {

@@ -1,4 +1,5 @@
-"""Serving loop: requests that overlap on the device give, each, exactly what they give alone."""
+"""Serving loop: requests that overlap on the device give, each, exactly what they give alone,
+and that is the oracle's result for the request (bit for bit: all outputs are integers)."""
 import threading
 import time
 
@@ -6,6 +7,7 @@ import numpy as np
 import pytest
 
 import nmc_inputs as W
+import oracle as O
 
 pytestmark = pytest.mark.gpu
 KEYS = ("states", "energies", "best_energies", "best_states")
@@ -24,6 +26,16 @@ def _requests():
         beta = W.beta_scaled_linear(n, T, 0.01, 1.0, 0.5, 1.5, 700 + i)
         reqs.append(("qap", dict(F=F, D=D, beta=beta, replicas=R, seed=800 + i)))
     return reqs
+
+
+def _oracle(kind, r):
+    T = r["beta"].shape[1]
+    if kind == "ksat":
+        return O.ksat_anneal(r["lits"], r["n_vars"], r["beta"], 0, T, r["seed"],
+                             replicas=r["replicas"])
+    o = O.qap_anneal(r["F"], r["D"], r["beta"], 0, T, r["seed"], replicas=r["replicas"])
+    return dict(states=o["perms"], energies=o["energies"], best_energies=o["best_energies"],
+                best_states=o["best_perms"])
 
 
 def _alone(kind, r):
@@ -67,8 +79,10 @@ def test_mixed_requests_match_alone():
     for (kind, r), (got, lat) in zip(reqs, outs):
         assert lat > 0
         want = _alone(kind, r)
+        orc = _oracle(kind, r)
         for key in KEYS:
             assert np.array_equal(got[key], want[key]), (kind, key)
+            assert np.array_equal(got[key], orc[key]), (kind, key)
 
 
 def test_factored_requests_match_alone():
@@ -88,9 +102,12 @@ def test_factored_requests_match_alone():
             outs.append(srv.result(i)[0])
     beta = (factor[:, None] * base[None, :]).astype(np.float32)
     for s, got in enumerate(outs):
-        want = _alone("ksat", dict(lits=lits, n_vars=n, beta=beta, replicas=32, seed=s))
+        req = dict(lits=lits, n_vars=n, beta=beta, replicas=32, seed=s)
+        want = _alone("ksat", req)
+        orc = _oracle("ksat", req)
         for key in KEYS:
             assert np.array_equal(got[key], want[key]), key
+            assert np.array_equal(got[key], orc[key]), key
 
 
 def test_admission_limits_cancel_and_errors():

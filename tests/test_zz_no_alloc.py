@@ -61,9 +61,17 @@ def test_noalloc_rejects_more_items_than_its_array_holds():
     rc = _noalloc(ctx, sets, [0] * 61, [1] * 61)
     assert rc == nmc.NMC_EINVAL
     assert b"scratch" in ctx._lib.nmc_last_error(ctx._h)
-    assert _noalloc(ctx, sets[:60], [0] * 60, [1] * 60) == nmc.NMC_OK  # 7680 words fit
+    # 7680 words fit: the items near the top of the array give what nmc_batch_run gives for
+    # twin sets (same seeds), set by set
+    twins = [ctx.replicas_create(inst, 4096, seed=s) for s in range(60)]
+    assert _noalloc(ctx, sets[:60], [0] * 60, [1] * 60) == nmc.NMC_OK
+    ctx.batch_run(twins, 0, 1)
+    for a, b in zip(sets[:60], twins):
+        ga, gb = ctx.replicas_read(a), ctx.replicas_read(b)
+        for key in KEYS:
+            assert np.array_equal(ga[key], gb[key]), key
     ctx.sync()
-    for s in sets:
+    for s in sets + twins:
         ctx.replicas_destroy(s)
     ctx.unload(inst)
     ctx.close()
