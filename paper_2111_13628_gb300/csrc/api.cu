@@ -315,6 +315,7 @@ int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t
       B.best_energy = S->ks.best_energy;
       B.n = I->ks.n;
       B.n_colours = I->ks.n_colours;
+      B.n_groups = I->ks.n_groups;
       B.W = S->ks.W;
       B.w = w;
       B.t0 = t0[i];
@@ -417,6 +418,7 @@ BatchItem ksat_item(const Instance &I, const ReplicaSet &S, int32_t w, int32_t t
   B.best_energy = S.ks.best_energy;
   B.n = I.ks.n;
   B.n_colours = I.ks.n_colours;
+  B.n_groups = I.ks.n_groups;
   B.W = S.ks.W;
   B.w = w;
   B.t0 = t0;
@@ -606,10 +608,12 @@ void parallel_ranges(int64_t count, F f, int64_t per_thread = 8192) {
 // of its three literals that add the fewest distinct words to banks already used in this slot
 // (first found on ties; a lane with none left takes an inert entry). Simulated on the
 // 50,000-variable bench formula: 3.39 -> 1.98 passes per load on average (1.94 with every
-// remaining occurrence a candidate, at several times the host time).
+// remaining occurrence a candidate, at several times the host time). A lane's occurrences in
+// which its own literal is positive come first, those where it is negated next, so that the
+// kernel can count each kind with one bit-sliced counter outside the slots where lanes differ.
 struct BankOrder {
-  std::vector<int32_t> pend[32];  // per lane: indices of occurrences not yet placed
-  int32_t addr[3][32][32];        // per literal position and bank: distinct words this slot
+  std::vector<int32_t> pend[2][32];  // per lane: own-positive / own-negative occurrences to place
+  int32_t addr[3][32][32];           // per literal position and bank: distinct words this slot
   int32_t cnt[3][32];
 
   int cost(int p, int32_t w) const {
@@ -624,32 +628,41 @@ struct BankOrder {
       if (addr[p][b][i] == w) return;
     addr[p][b][cnt[p][b]++] = w;
   }
-  // Writes the group's len x 32 entries (int4 each: sign bytes, three word byte offsets).
+  // Writes the group's len x 32 entries (int4 each: sign bytes, three word byte offsets). A
+  // lane's own-positive occurrences fill its first npos slots, its own-negative ones the next.
   void build(int32_t g0, int32_t cend, int32_t len, int32_t n, const HostVec &occ,
              const std::vector<int32_t> &occ_ptr, const std::vector<int32_t> &orig,
-             const std::vector<int32_t> &deg, int32_t *dst0) {
+             const std::vector<int32_t> &deg, const std::vector<int32_t> &npos, int32_t *dst0) {
     static const int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    int32_t np[32];
     for (int32_t l = 0; l < 32; ++l) {
-      pend[l].clear();
+      pend[0][l].clear();
+      pend[1][l].clear();
+      np[l] = 0;
       const int32_t v = g0 + l;
-      if (v < cend)
-        for (int32_t j = 0; j < deg[orig[v]]; ++j) pend[l].push_back(occ_ptr[v] + j);
+      if (v >= cend) continue;
+      np[l] = npos[orig[v]];
+      for (int32_t j = 0; j < deg[orig[v]]; ++j) {
+        const int32_t e = occ_ptr[v] + j;
+        pend[occ[static_cast<size_t>(e) * 4] != 0 ? 1 : 0][l].push_back(e);
+      }
     }
     for (int32_t j = 0; j < len; ++j) {
       for (int p = 0; p < 3; ++p)
         for (int b = 0; b < 32; ++b) cnt[p][b] = 0;
       for (int32_t l = 0; l < 32; ++l) {
         int32_t *dst = dst0 + (static_cast<size_t>(j) * 32 + l) * 4;
-        if (pend[l].empty()) {  // inert: own sign 0, one always-true literal (word n)
+        std::vector<int32_t> &pool = pend[j < np[l] ? 0 : 1][l];
+        if (pool.empty()) {  // inert: own sign 0, one always-true literal (word n)
           dst[0] = static_cast<int32_t>(1u << 15);
           dst[1] = dst[2] = dst[3] = n * 4;
           for (int p = 0; p < 3; ++p) add(p, n);
           continue;
         }
         int best = -1, best_i = 0, best_pm = 0;
-        const size_t window = std::min<size_t>(pend[l].size(), 8);  // next 8 candidates
+        const size_t window = std::min<size_t>(pool.size(), 8);  // next 8 candidates
         for (size_t i = 0; i < window && best != 0; ++i) {
-          const int32_t *src = &occ[static_cast<size_t>(pend[l][i]) * 4];
+          const int32_t *src = &occ[static_cast<size_t>(pool[i]) * 4];
           int cm[3][3];  // cm[p][k]: cost of literal k at position p
           for (int p = 0; p < 3; ++p)
             for (int k = 0; k < 3; ++k) cm[p][k] = cost(p, src[1 + k] >> 1);
@@ -663,8 +676,8 @@ struct BankOrder {
             }
           }
         }
-        const int32_t *src = &occ[static_cast<size_t>(pend[l][best_i]) * 4];
-        pend[l].erase(pend[l].begin() + best_i);
+        const int32_t *src = &occ[static_cast<size_t>(pool[best_i]) * 4];
+        pool.erase(pool.begin() + best_i);
         uint32_t signs = static_cast<uint32_t>(src[0] != 0) << 7;
         for (int p = 0; p < 3; ++p) {
           const int32_t lit = src[1 + kPerm[best_pm][p]];
@@ -943,9 +956,28 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
   for (int32_t v = 0; v < n; ++v) ++col_ptr[colour[v] + 1];
   for (int32_t c = 0; c < n_colours; ++c) col_ptr[c + 1] += col_ptr[c];
   std::vector<int32_t> orig(n), newid(n);
+  // own-positive occurrences of each variable (k <= 4 layout: a group's lanes keep those first)
+  std::vector<int32_t> npos(kq == 1 ? n : 0, 0);
+  if (kq == 1)
+    parallel_ranges(n, [&](int64_t v0, int64_t v1) {
+      for (int64_t v = v0; v < v1; ++v)
+        for (int32_t e = vptr[v]; e < vptr[v + 1]; ++e)
+          npos[v] += occ0[static_cast<size_t>(e) * slots] == 0 ? 1 : 0;
+    });
   {
     std::vector<int32_t> pos(col_ptr.begin(), col_ptr.end() - 1);
     for (int32_t r = 0; r < n; ++r) orig[pos[colour[ord[r]]]++] = ord[r];
+    if (kq == 1) {
+      // inside a class: degree down, then own-positive count down (a group's lanes then have
+      // similar splits between positive and negative occurrences), then id up
+      parallel_ranges(n_colours, [&](int64_t c0, int64_t c1) {
+        for (int64_t c = c0; c < c1; ++c)
+          std::stable_sort(orig.begin() + col_ptr[c], orig.begin() + col_ptr[c + 1],
+                           [&](int32_t a, int32_t b) {
+                             return deg[a] != deg[b] ? deg[a] > deg[b] : npos[a] > npos[b];
+                           });
+      }, 1);
+    }
     for (int32_t p = 0; p < n; ++p) newid[orig[p]] = p;
   }
   // -- occurrence lists in new ids, each padded to a multiple of 4 occurrences
@@ -995,20 +1027,35 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
       grp_v0.push_back(g0);
     }
   }
+  // sign regions of every group (k <= 4): slots [0, a) hold own-positive occurrences in every
+  // lane, slots from b on none; stored as a | b << 16 after the G + 1 offsets
+  const int32_t n_groups = static_cast<int32_t>(grp_v0.size());
+  grp_base.resize(static_cast<size_t>(2) * n_groups + 1, 0);
+  if (kq == 1)
+    for (int32_t c = 0; c < n_colours; ++c)
+      for (int32_t g = cgrp[c]; g < cgrp[c + 1]; ++g) {
+        int32_t lo = INT32_MAX, hi = 0;
+        for (int32_t v = grp_v0[g]; v < std::min(grp_v0[g] + 32, col_ptr[c + 1]); ++v) {
+          lo = std::min(lo, npos[orig[v]]);
+          hi = std::max(hi, npos[orig[v]]);
+        }
+        grp_base[n_groups + 1 + g] = (lo & ~3) | (((hi + 3) & ~3) << 16);
+      }
   // the class end of every group's first variable
   std::vector<int32_t> grp_end(grp_v0.size());
   for (int32_t c = 0; c < n_colours; ++c)
     for (int32_t g = cgrp[c]; g < cgrp[c + 1]; ++g) grp_end[g] = col_ptr[c + 1];
   // every entry of every group is written below (lanes x occurrences x kq int4)
-  HostVec occ_t(static_cast<size_t>(std::max<int64_t>(grp_base.back(), 1)) * 4);
-  if (grp_base.back() == 0) std::fill(occ_t.begin(), occ_t.end(), 0);
+  const int64_t n_rows = grp_base[n_groups];
+  HostVec occ_t(static_cast<size_t>(std::max<int64_t>(n_rows, 1)) * 4);
+  if (n_rows == 0) std::fill(occ_t.begin(), occ_t.end(), 0);
   parallel_ranges(static_cast<int64_t>(grp_v0.size()), [&](int64_t ga, int64_t gz) {
     BankOrder bo;
     for (int64_t g = ga; g < gz; ++g) {
       const int32_t g0 = grp_v0[g], cend = grp_end[g];
       const int32_t len = (grp_base[g + 1] - grp_base[g]) / (kq * 32);
       if (kq == 1) {
-        bo.build(g0, cend, len, n, occ, occ_ptr, orig, deg,
+        bo.build(g0, cend, len, n, occ, occ_ptr, orig, deg, npos,
                  &occ_t[static_cast<size_t>(grp_base[g]) * 4]);
         continue;
       }
@@ -1095,6 +1142,7 @@ int upload_ksat(nmc_ctx *ctx, HostKsat &h, int32_t *inst_out) {
   I.ks.m = m;
   I.ks.kmax = K;
   I.ks.n_colours = n_colours;
+  I.ks.n_groups = cgrp.back();
   I.ks.kq = kq;
   I.ks.nb = nb;
   I.ks.n_occ = static_cast<int32_t>(n_occ);

@@ -124,6 +124,14 @@ __device__ __forceinline__ uint32_t sign_mask(uint32_t sg) {
   return r;
 }
 
+// Byte b (0..3) of x as a signed value: prmt replicates the byte's sign into the upper three
+// bytes (selector nibbles 8-15).
+__device__ __forceinline__ int sext_byte(uint32_t x, int b) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(0u), "r"(0x8880u + 0x1111u * (uint32_t)b));
+  return (int)r;
+}
+
 // Truth value (32 replicas) of literal id l = 2u + neg from the word vector in shared memory.
 __device__ __forceinline__ uint32_t lit_word(const uint32_t *xs, int l) {
   return xs[l >> 1] ^ (0u - (uint32_t)(l & 1));
@@ -150,6 +158,7 @@ struct AttemptPrep {
   int4 q[4 * KQ];
   const int4 *ent;
   int len;
+  int regions;  // k <= 4: own-sign regions of the variable's group (a | b << 16)
   uint32_t bq;
 };
 
@@ -164,6 +173,7 @@ __device__ __forceinline__ void prep_attempt(const BatchItem &B, int cg, int c0,
   const int gb = __ldg(B.grp_base + g);
   p.len = (__ldg(B.grp_base + g + 1) - gb) / (32 * KQ);
   p.ent = B.occ_t + gb + ln;
+  p.regions = KQ == 1 ? __ldg(B.grp_base + B.n_groups + 1 + g) : 0;
   if (p.len > 0) {
 #pragma unroll
     for (int j = 0; j < 4 * KQ; ++j) p.q[j] = __ldg(p.ent + (size_t)j * 32);
@@ -215,34 +225,92 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
       mm[j] = ~(own | o);
     }
   };
-  // Two groups of 4 per trip: each group's weight-4 carry is kept aside and the pair's carries
-  // enter the planes from weight 4 up once (one ripple per 8 occurrences instead of per 4).
-  // Every group's entries are still requested one group before they are evaluated.
-  for (int e = 0; e < len; e += 8) {
-    int4 qc[4 * KQ];
-    uint32_t bb[4], mm[4];
+  if constexpr (KQ == 1) {
+    // Own-sign split (k <= 4): in a lane's list the occurrences where its own literal is positive
+    // come first. With z = "every other literal of the clause false", a replica's energy change
+    // is x ? Zp - Zn : Zn - Zp, Zp / Zn counting z over the positive / negated occurrences; slots
+    // [0, ra) are positive in every lane of the group and slots from rb on negated (or inert), so
+    // only [ra, rb) needs both counters, split by the own sign. bc counts Zp, mc counts Zn; each
+    // keeps one weight-4 carry pending so that the carries of two groups enter it together.
+    const int ra = P.regions & 0xFFFF, rb = P.regions >> 16;
+    uint32_t fp = 0u, fn = 0u;
+    bool pp = false, pn = false;
+    auto add4 = [&](uint32_t (&c)[NB], uint32_t &f, bool &pend, const uint32_t (&z)[4]) {
+      const uint32_t g = csa4_low(c, z[0], z[1], z[2], z[3]);
+      if (pend) add_carry_pair<NB>(c, f, g);
+      else f = g;
+      pend = !pend;
+    };
+    for (int e = 0; e < len; e += 4) {
+      int4 qc[4];
 #pragma unroll
-    for (int j = 0; j < 4 * KQ; ++j) qc[j] = qn[j];
-    if (e + 4 < len) {
+      for (int j = 0; j < 4; ++j) qc[j] = qn[j];
+      if (e + 4 < len) {
 #pragma unroll
-      for (int j = 0; j < 4 * KQ; ++j) qn[j] = __ldg(ent + (size_t)((e + 4) * KQ + j) * 32);
+        for (int j = 0; j < 4; ++j) qn[j] = __ldg(ent + (size_t)(e + 4 + j) * 32);
+      }
+      uint32_t z[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t sg = (uint32_t)qc[j].x;
+        z[j] = ~((xs_at(xs, qc[j].y) ^ sign_mask<1>(sg)) | (xs_at(xs, qc[j].z) ^ sign_mask<2>(sg)) |
+                 (xs_at(xs, qc[j].w) ^ sign_mask<3>(sg)));
+      }
+      if (e + 4 <= ra) {
+        add4(bc, fp, pp, z);
+      } else if (e >= rb) {
+        add4(mc, fn, pn, z);
+      } else {
+        uint32_t zp[4], zn[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t neg = sign_mask<0>((uint32_t)qc[j].x);
+          zp[j] = z[j] & ~neg;
+          zn[j] = z[j] & neg;
+        }
+        add4(bc, fp, pp, zp);
+        add4(mc, fn, pn, zn);
+      }
     }
-    masks4(qc, bb, mm);
-    uint32_t fb = csa4_low(bc, bb[0], bb[1], bb[2], bb[3]);
-    uint32_t fm = csa4_low(mc, mm[0], mm[1], mm[2], mm[3]);
-    if (e + 4 < len) {
+    if (pp) add_carry<NB>(bc, fp);
+    if (pn) add_carry<NB>(mc, fn);
+    // (bc, mc) <- (Zp, Zn) where x = 1, (Zn, Zp) where x = 0: the subtraction below is the dE
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const uint32_t a = (bc[j] & x) | (mc[j] & ~x), c = (mc[j] & x) | (bc[j] & ~x);
+      bc[j] = a;
+      mc[j] = c;
+    }
+  } else {
+    // Two groups of 4 per trip: each group's weight-4 carry is kept aside and the pair's carries
+    // enter the planes from weight 4 up once (one ripple per 8 occurrences instead of per 4).
+    // Every group's entries are still requested one group before they are evaluated.
+    for (int e = 0; e < len; e += 8) {
+      int4 qc[4 * KQ];
+      uint32_t bb[4], mm[4];
 #pragma unroll
       for (int j = 0; j < 4 * KQ; ++j) qc[j] = qn[j];
-      if (e + 8 < len) {
+      if (e + 4 < len) {
 #pragma unroll
-        for (int j = 0; j < 4 * KQ; ++j) qn[j] = __ldg(ent + (size_t)((e + 8) * KQ + j) * 32);
+        for (int j = 0; j < 4 * KQ; ++j) qn[j] = __ldg(ent + (size_t)((e + 4) * KQ + j) * 32);
       }
       masks4(qc, bb, mm);
-      add_carry_pair<NB>(bc, fb, csa4_low(bc, bb[0], bb[1], bb[2], bb[3]));
-      add_carry_pair<NB>(mc, fm, csa4_low(mc, mm[0], mm[1], mm[2], mm[3]));
-    } else {
-      add_carry<NB>(bc, fb);
-      add_carry<NB>(mc, fm);
+      uint32_t fb = csa4_low(bc, bb[0], bb[1], bb[2], bb[3]);
+      uint32_t fm = csa4_low(mc, mm[0], mm[1], mm[2], mm[3]);
+      if (e + 4 < len) {
+#pragma unroll
+        for (int j = 0; j < 4 * KQ; ++j) qc[j] = qn[j];
+        if (e + 8 < len) {
+#pragma unroll
+          for (int j = 0; j < 4 * KQ; ++j) qn[j] = __ldg(ent + (size_t)((e + 8) * KQ + j) * 32);
+        }
+        masks4(qc, bb, mm);
+        add_carry_pair<NB>(bc, fb, csa4_low(bc, bb[0], bb[1], bb[2], bb[3]));
+        add_carry_pair<NB>(mc, fm, csa4_low(mc, mm[0], mm[1], mm[2], mm[3]));
+      } else {
+        add_carry<NB>(bc, fb);
+        add_carry<NB>(mc, fm);
+      }
     }
   }
   // D = B - U, 8 bit planes (two's complement), then per-replica bytes by 8x8 transposes
@@ -267,10 +335,10 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
     const unsigned long long xm = transpose8(gather_bytes(s8, q));
     int de[8];
     uint32_t th[8];
-    bool need0 = false, need1 = false;
+    const uint32_t xlo = (uint32_t)xm, xhi = (uint32_t)(xm >> 32);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      de[j] = (int)(signed char)(unsigned char)(xm >> (8 * j));
+      de[j] = sext_byte(j < 4 ? xlo : xhi, j & 3);
       th[j] = 0u;
       if (de[j] > 0) {
         uint32_t hi = bq_hi, lo = bq_lo;
@@ -283,10 +351,9 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
         const uint32_t idx = hi * (uint32_t)de[j] + ((lo * (uint32_t)de[j]) >> 8);
         th[j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
       }
-      if (j < 4) need0 |= th[j] != 0u; else need1 |= th[j] != 0u;
     }
     uint4 u0 = make_uint4(0u, 0u, 0u, 0u), u1 = u0;
-    if (need0 || need1)
+    if ((th[0] | th[1] | th[2] | th[3] | th[4] | th[5] | th[6] | th[7]) != 0u)
       philox4x32_10_x2(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + 2 * q), kTagKsatSweep),
                        make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + 2 * q + 1), kTagKsatSweep),
                        B.k0, B.k1, u0, u1);

@@ -48,6 +48,7 @@ struct KsatDevice {
   int32_t n, m, kmax, n_colours, kq;  // kq = int4 words per occurrence (1: k<=4, 2: k<=8)
   int32_t nb;                         // bits of the sliced counters (covers the max degree)
   int32_t n_occ;                      // occurrences incl. padding (multiple of 4 per variable)
+  int32_t n_groups;                   // groups of 32 variables of the interleaved lists
   int4 *occ;                          // n_occ * kq: {own sign mask, other literal ids...}
   int32_t *occ_ptr;                   // n+1
   int32_t *col_ptr;                   // n_colours+1 (device copy)
@@ -101,7 +102,7 @@ struct BatchItem {
   const uint32_t *mult;  // 32W Q16 temperature multipliers of the replicas, or null
   long long *stats;      // 64W: per-replica sums of E (first 32W) and E^2 (next 32W), or null
   int32_t stats_t0;      // sweeps t >= stats_t0 add their end-of-sweep energies to stats
-  int32_t pad_;
+  int32_t n_groups;      // groups of 32 variables; grp_base[n_groups + 1 + g]: g's sign regions
 };
 
 // ---- k-SAT launchers (ksat.cu); all asynchronous on `st` -------------------------------
