@@ -29,22 +29,27 @@ namespace nmc {
 
 namespace {
 
-// One-thread kernel: 16 warps, up to 128 registers (no spills; a DSatur colour class of the
-// 50,000-variable bench instance puts at most ~490 variables on each CTA of a 4-CTA cluster,
-// one round of 512 threads: measured 296 us per sweep against 295 with 640 threads and 96
-// registers, and 293 with the next class's loads requested at the barrier, which 640 threads
-// cannot hold without spilling)
-constexpr int kBatchThreads = 512;
+// One-thread kernel for k <= 4: 16 warps, up to 128 registers (no spills; a DSatur colour class
+// of the 50,000-variable bench instance puts at most ~490 variables on each CTA of a 4-CTA
+// cluster, one round of 512 threads: measured 296 us per sweep against 295 with 640 threads and
+// 96 registers, and 293 with the next class's loads requested at the barrier, which 640 threads
+// cannot hold without spilling). For k <= 8 (two int4 list entries per occurrence, twice the
+// prefetched registers) 12 warps with up to 168 registers, so that nothing spills.
+template <int KQ>
+__host__ __device__ constexpr int one_thread_threads() {
+  return KQ == 1 ? 512 : 384;
+}
 constexpr int kTeamThreads = 384;   // team kernel with teams of 2 or 4: 12 warps, up to 168 registers
-constexpr int kTeam8Threads = 640;  // team kernel with teams of 8
+constexpr int kTeam8Threads = 512;  // team kernel with teams of 8: up to 128 registers
 
 // Threads of the sweep kernel with TL lanes per variable: 384 for teams of 2 or 4, which then
 // prefetch their occurrence entries a group ahead (measured at N = 5,000: 107 -> 102 us per
-// sweep); 640 for teams of 8 (the tiny classes of small instances, where 384 threads measured
-// slower: N = 200, 37.3 -> 45.3 us); 512 for single threads.
-template <int TL>
+// sweep); 512 for teams of 8 (the tiny classes of small instances, where 384 threads measured
+// slower: N = 200, 37.3 -> 45.3 us; 640 spilled with the replica-exchange multipliers); single
+// threads as one_thread_threads.
+template <int KQ, int TL>
 __host__ __device__ constexpr int sweep_threads() {
-  return (TL == 2 || TL == 4) ? kTeamThreads : (TL == 8 ? kTeam8Threads : kBatchThreads);
+  return (TL == 2 || TL == 4) ? kTeamThreads : (TL == 8 ? kTeam8Threads : one_thread_threads<KQ>());
 }
 
 template <int NB>
@@ -656,7 +661,7 @@ __device__ __forceinline__ void class_teams(const BatchItem &B, uint32_t *xs, co
 // PT: every item carries per-replica temperature multipliers and, optionally, accumulates the
 // end-of-sweep energies of sweeps t >= stats_t0 (sums of E and E^2 per replica).
 template <int KQ, int CS, bool PT>
-__global__ void __launch_bounds__(kBatchThreads, 1)
+__global__ void __launch_bounds__(one_thread_threads<KQ>(), 1)
     ksat_batch_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
                       const uint32_t *tab, int tab_len, int xs_words, int small_teams) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -700,7 +705,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
       // arrive behind its barrier
       int c0 = __ldg(B.col_ptr), c1 = __ldg(B.col_ptr + 1), cg = __ldg(B.cgrp);
       // a share of a class with at most this many variables on the CTA runs with teams of lanes
-      const int team_max = small_teams ? kBatchThreads / 2 : -1;
+      constexpr int kThreads = one_thread_threads<KQ>();
+      const int team_max = small_teams ? kThreads / 2 : -1;
       // the state-independent loads of this thread's first variable of each class: requested
       // for class c + 1 between the two halves of the barrier that ends class c
       // (every thread loads, those without a variable in the class for variable c0, so that
@@ -722,9 +728,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
         if (cnt <= team_max) {
           // a smaller share (the later colour classes): teams of 8, 4 or 2 lanes per variable
           // shorten the class's critical path; their energy changes go to ep_s directly
-          if (cnt <= kBatchThreads / 8)
+          if (cnt <= kThreads / 8)
             class_teams<KQ, CS, 8, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, cnt, rank, t, ep_s);
-          else if (cnt <= kBatchThreads / 4)
+          else if (cnt <= kThreads / 4)
             class_teams<KQ, CS, 4, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, cnt, rank, t, ep_s);
           else
             class_teams<KQ, CS, 2, PT>(B, xs, tab_s, tab_len, mult_s, cg, c0, cnt, rank, t, ep_s);
@@ -826,7 +832,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 
 
 template <int KQ, int CS, int TL, bool PT>
-__global__ void __launch_bounds__(sweep_threads<TL>(), 1)
+__global__ void __launch_bounds__(sweep_threads<KQ, TL>(), 1)
     ksat_team_kernel(const BatchItem *__restrict__ items, int n_items, int *next_item,
                      const uint32_t *tab, int tab_len, int xs_words, int small_teams) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -871,7 +877,7 @@ __global__ void __launch_bounds__(sweep_threads<TL>(), 1)
       for (int i = 0; i < 32 / TL; ++i) acc[i] = 0;
       // class bounds and first group: for teams of 2 or 4 those of class c + 1 are requested
       // during class c (the tiny classes of teams of 8 measured faster loading their own)
-      constexpr bool ahead = sweep_threads<TL>() == kTeamThreads;
+      constexpr bool ahead = sweep_threads<KQ, TL>() == kTeamThreads;
       int c0 = __ldg(B.col_ptr), c1 = __ldg(B.col_ptr + 1), cg = __ldg(B.cgrp);
       for (int c = 0; c < B.n_colours; ++c) {
         int c2 = 0, cgn = 0;
@@ -891,7 +897,7 @@ __global__ void __launch_bounds__(sweep_threads<TL>(), 1)
           const int v = vw + (lane / TL);
           const bool active = v < v1;
           const uint32_t xn =
-              attempt_team<KQ, TL, PT, (sweep_threads<TL>() == kTeamThreads)>(B, xs, tab_s, tab_len,
+              attempt_team<KQ, TL, PT, (sweep_threads<KQ, TL>() == kTeamThreads)>(B, xs, tab_s, tab_len,
                                                                          mult_s, cg, c0, v, active,
                                                                          t, tl, acc);
           if (active && tl == 0) {
@@ -969,7 +975,7 @@ cudaError_t launch_batch(const BatchItem *items, int n_items, int *next_item,
   const int xs_words = max_n + 1;
   const size_t smem = sizeof(uint32_t) * (((size_t)xs_words + 31) / 32 * 32 + (size_t)tab_len + 1);
   auto kern = TL == 1 ? ksat_batch_kernel<KQ, CS, PT> : ksat_team_kernel<KQ, CS, (TL > 1 ? TL : 4), PT>;
-  constexpr int threads = sweep_threads<TL>();
+  constexpr int threads = sweep_threads<KQ, TL>();
   static std::mutex mu;
   static std::map<std::pair<int, size_t>, int> shapes;  // (device, smem) -> resident clusters
   static std::map<int, int> sm_count;                    // device -> SMs
