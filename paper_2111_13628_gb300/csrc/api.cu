@@ -1453,7 +1453,7 @@ int nmc_replicas_create(nmc_ctx *ctx, int32_t inst, int32_t replicas, uint64_t s
     S.ks.R = replicas;
     S.ks.W = W;
     if ((e = dev_alloc(&S.ks.S, static_cast<size_t>(2 * n + 2) * W)) != cudaSuccess ||
-        (e = dev_alloc(&S.ks.best, static_cast<size_t>(n) * W)) != cudaSuccess ||
+        (e = dev_alloc(&S.ks.best, static_cast<size_t>(2 * n) * W)) != cudaSuccess ||
         (e = dev_alloc(&S.ks.energy, 32 * W)) != cudaSuccess ||
         (e = dev_alloc(&S.ks.best_energy, 32 * W)) != cudaSuccess ||
         (e = dev_alloc(&S.ks.imp, W)) != cudaSuccess ||

@@ -64,7 +64,7 @@ struct KsatDevice {
 struct KsatReplicas {
   int32_t R, W;
   uint32_t *S;        // (2n+2) * W: row 2v = x_v bits, row 2v+1 = not x_v, rows 2n/2n+1 dummy
-  uint32_t *best;     // n * W
+  uint32_t *best;     // n * W ([var][word]), then n * W of word-major staging for the batched kernel
   int32_t *energy;    // 32W
   int32_t *best_energy;
   uint32_t *imp;      // W: replicas whose best improved at the last sweep end (pending copy)

@@ -84,7 +84,7 @@ int64_t estimate_bytes(const Request &r) {
     const int64_t occ = static_cast<int64_t>(r.m) * r.kmax;
     const int64_t instance = occ * 16 * 3 + static_cast<int64_t>(r.m) * r.kmax * 4 + r.n * 24;
     const int64_t sched = static_cast<int64_t>(r.n) * r.n_steps * 4;
-    const int64_t reps = (3 * static_cast<int64_t>(r.n) + 2) * words * 4 + 64 * words * 4 + 8192;
+    const int64_t reps = (4 * static_cast<int64_t>(r.n) + 2) * words * 4 + 64 * words * 4 + 8192;
     return instance + sched + reps + (1 << 20);
   }
   const int64_t n = r.n;
