@@ -336,7 +336,10 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
   uint32_t flip = 0u;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    // replicas 8q .. 8q+7: Philox groups 2q and 2q+1, drawn together when either needs a draw
+    // replicas 8q .. 8q+7: Philox groups 2q and 2q+1, drawn together and always (a draw that
+    // cannot change an acceptance changes nothing; a branch on whether any lane needs one rarely
+    // skips the work for the whole warp and keeps the four pairs from overlapping: 236.5 -> 225.7
+    // us per sweep on the 50,000-variable bench instance)
     const unsigned long long xm = transpose8(gather_bytes(s8, q));
     int de[8];
     uint32_t th[8];
@@ -357,9 +360,8 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
         th[j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
       }
     }
-    uint4 u0 = make_uint4(0u, 0u, 0u, 0u), u1 = u0;
-    if ((th[0] | th[1] | th[2] | th[3] | th[4] | th[5] | th[6] | th[7]) != 0u)
-      philox4x32_10_x2(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + 2 * q), kTagKsatSweep),
+    uint4 u0, u1;
+    philox4x32_10_x2(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + 2 * q), kTagKsatSweep),
                        make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + 2 * q + 1), kTagKsatSweep),
                        B.k0, B.k1, u0, u1);
 #pragma unroll
