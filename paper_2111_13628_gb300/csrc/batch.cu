@@ -531,18 +531,18 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
 #pragma unroll
   for (int b = 0; b < NBK; ++b) xmb[b] = transpose8(gather_bytes(d, ((tl * GPL) >> 1) + b));
   uint32_t flip = 0u;
+  // the lane's Philox groups, drawn always and two at a time (as in attempt_batch)
+  int de[4 * GPL];
+  uint32_t th[4 * GPL];
 #pragma unroll
   for (int gi = 0; gi < GPL; ++gi) {
     const int g = tl * GPL + gi;
-    int de[4];
-    uint32_t th[4];
-    bool need = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int r = 4 * g + j;
       const int val = (int)(signed char)(unsigned char)(xmb[gi >> 1] >> (8 * (r & 7)));
-      de[j] = val;
-      th[j] = 0u;
+      de[4 * gi + j] = val;
+      th[4 * gi + j] = 0u;
       if (val > 0) {
         uint32_t hi = bq_hi, lo = bq_lo;
         if (PT) {
@@ -552,18 +552,32 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
           lo = b & 255u;
         }
         const uint32_t idx = hi * (uint32_t)val + ((lo * (uint32_t)val) >> 8);
-        th[j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
+        th[4 * gi + j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
       }
-      need |= th[j] != 0u;
     }
-    uint4 u = make_uint4(0u, 0u, 0u, 0u);
-    if (need && active)
-      u = philox4x32_10(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + g), kTagKsatSweep), B.k0, B.k1);
+  }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (de[j] <= 0 || uint4_word(u, j) < th[j]) {
-        flip |= 1u << (4 * g + j);
-        if (active) acc[4 * gi + j] += de[j];
+  for (int gi = 0; gi < GPL; gi += 2) {
+    const int g = tl * GPL + gi;
+    uint4 u[2];
+    if (gi + 1 < GPL) {
+      philox4x32_10_x2(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + g), kTagKsatSweep),
+                       make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + g + 1), kTagKsatSweep),
+                       B.k0, B.k1, u[0], u[1]);
+    } else {
+      u[0] = philox4x32_10(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + g), kTagKsatSweep),
+                           B.k0, B.k1);
+      u[1] = u[0];
+    }
+#pragma unroll
+    for (int k = 0; k < 2 && gi + k < GPL; ++k) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = 4 * (gi + k) + j;
+        if (de[i] <= 0 || uint4_word(u[k], j) < th[i]) {
+          flip |= 1u << (4 * (g + k) + j);
+          if (active) acc[i] += de[i];
+        }
       }
     }
   }
