@@ -976,7 +976,7 @@ def main():
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--pool", type=int, default=256)
     ap.add_argument("--max-active", type=int, default=4096)
-    ap.add_argument("--slice-log2", type=int, default=27)
+    ap.add_argument("--slice-log2", type=int, default=30)
     ap.add_argument("--memory-budget-gb", type=float, default=200.0)
     ap.add_argument("--plain-seconds", type=float, default=90.0)
     ap.add_argument("--path", default="run", choices=["run", "batch", "grid"],

@@ -379,7 +379,9 @@ int nmc_anneal(nmc_ctx *ctx, int32_t inst, int32_t replicas, int32_t t0, int32_t
  * replica state resident on the device until they finish. Every tick advances all active
  * requests by a slice of about 2^slice_log2 units of work each (one unit: one clause
  * occurrence of one variable for 32 replicas; a QAP swap attempt on one replica counts as n/3
- * units), so that requests progress at similar wall-clock rates, k-SAT requests together
+ * units), but by no more sweeps than fit about 0.1 s of GPU time by an estimate of the request's
+ * time per sweep (small instances are bound by the per-colour-class latency, not by their
+ * work), so that requests progress at similar wall-clock rates, k-SAT requests together
  * in one batched launch (nmc_batch_run), so requests that arrive while others run share the
  * following launches. Results are bit for bit those of nmc_anneal on the same inputs
  * (segment invariance). All nmc_server_* calls are thread-safe.

@@ -257,6 +257,17 @@ int set_ctx_error(nmc_ctx *ctx, int code, const char *msg) {
 // Mean colour-class size of a k-SAT instance (variables per class, rounded up).
 int class_size(const Instance &I) { return (I.ks.n + I.ks.n_colours - 1) / std::max(1, I.ks.n_colours); }
 
+double ksat_sweep_us(int32_t n, int32_t n_colours) {
+  const double nc = std::max(1, n_colours);
+  const double per_class = std::max(1.0, n / nc);
+  const double rounds = std::ceil(per_class / 512.0);
+  const double last = per_class - 512.0 * (rounds - 1.0);  // variables in the last round
+  const double cycles = nc * (2200.0 + 16000.0 * (rounds - 1.0) + 27.0 * last);
+  return cycles / 2070.0;  // SM clock in MHz
+}
+
+double qap_step_us(int32_t n) { return 0.008 * static_cast<double>(n) * n + 1.0; }
+
 // CTAs per work item: few items are spread over the SMs (each cluster keeps its own copy of the
 // word vector), but a colour class is not split below about 32 variables per CTA, where a
 // cluster barrier per class costs more than the work it spreads (measured: 4-SAT N = 200 with 64
@@ -323,7 +334,10 @@ int batch_plan(nmc_ctx *ctx, int32_t n_sets, const int32_t *rs, const int32_t *t
       B.k0 = static_cast<uint32_t>(S->seed);
       B.k1 = static_cast<uint32_t>(S->seed >> 32);
       by_kq[q].push_back(B);
-      cost[q].push_back(static_cast<long long>(I->ks.n_occ + I->ks.n) * (t1[i] - t0[i]));
+      // longest-first by estimated time (small instances are bound by the per-class latency,
+      // not by their work)
+      cost[q].push_back(static_cast<long long>(
+          1000.0 * ksat_sweep_us(I->ks.n, I->ks.n_colours) * (t1[i] - t0[i])));
       if (I->ks.n > plan->max_n[q]) plan->max_n[q] = I->ks.n;
     }
     per_class[q] = std::max(per_class[q], class_size(*I));

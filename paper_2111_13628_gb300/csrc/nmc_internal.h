@@ -136,6 +136,15 @@ size_t batch_max_vars(int tab_len, int device);
 // per item; next_item is a device int. With pt, every item carries temperature multipliers
 // (mult) and may carry energy statistics. lanes: lanes per variable (1, 4, 8; 0 = the built-in
 // choice from cs and max_n).
+// Estimated GPU time, in microseconds, of one sweep of one 32-replica word of a k-SAT instance
+// with n variables in n_colours classes on one CTA (the shape of a launch with many items): per
+// class a latency floor plus the variables' share of a 512-thread round, rounds beyond 512
+// variables in full (from measured sweeps: ~2.4k cycles per class of a few variables, ~16k per
+// full round). Used to order work items and to size serving slices by time, not for results.
+double ksat_sweep_us(int32_t n, int32_t n_colours);
+// The same for one swap step (n attempts) of one 32-replica block of a QAP instance.
+double qap_step_us(int32_t n);
+
 cudaError_t ksat_batch(const BatchItem *items_dev, int n_items, int kq, int cs, int max_n,
                        int *next_item, const uint32_t *tab, int tab_len, int device,
                        cudaStream_t st, bool pt = false, int lanes = 0);

@@ -7,8 +7,10 @@
 //      then resident on the device until the request finishes);
 //   2. advance every active request by one slice of sweeps in a single batched launch (k-SAT
 //      words of all requests share the persistent kernel; the QAP launch shapes run beside it
-//      on auxiliary streams),
-//      the slice sized so that every request gets about the same amount of work per tick;
+//      on auxiliary streams), the slice being the smaller of about the same amount of work per
+//      request (2^slice_log2 units) and the sweeps that fit kTickUs by the request's estimated
+//      time per sweep, so that a small instance, whose sweeps are bound by the per-class latency
+//      rather than by its work, does not stretch the tick for everyone;
 //   3. read back and release the requests that reached the end of their schedule.
 // A request that arrives while others run joins at the next tick. Because sweeps are
 // segment-invariant (absolute sweep index in every random-number counter), a request's result
@@ -33,10 +35,13 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Target GPU time of one tick's slice of a request (estimated, microseconds).
+constexpr double kTickUs = 100000.0;
+
 struct Request {
   int64_t id = 0;
   int kind = 0;
-  int32_t n = 0, m = 0, kmax = 0, n_steps = 0, replicas = 0;
+  int32_t n = 0, m = 0, kmax = 0, n_steps = 0, replicas = 0, n_colours = 0;
   uint64_t seed = 0;
   std::vector<int32_t> F, D;
   nmc::HostKsat prep;  // k-SAT instance prepared on the submitting thread
@@ -188,7 +193,11 @@ void worker_loop(nmc_server *s) {
           r->kind == NMC_KIND_KSAT
               ? static_cast<int64_t>(r->m) * r->kmax * ((r->replicas + 31) / 32)
               : static_cast<int64_t>(r->n) * r->n * r->replicas / 3;
-      const int64_t sweeps = std::max<int64_t>(1, slice / std::max<int64_t>(1, per_sweep));
+      const double t_us = r->kind == NMC_KIND_KSAT ? nmc::ksat_sweep_us(r->n, r->n_colours)
+                                                   : nmc::qap_step_us(r->n);
+      const int64_t by_time = std::max<int64_t>(1, static_cast<int64_t>(kTickUs / t_us));
+      const int64_t sweeps =
+          std::min(by_time, std::max<int64_t>(1, slice / std::max<int64_t>(1, per_sweep)));
       const int32_t t1 = static_cast<int32_t>(std::min<int64_t>(r->n_steps, r->t + sweeps));
       if (r->kind == NMC_KIND_KSAT && r->batchable) {
         rs.push_back(r->rs);
@@ -329,6 +338,7 @@ int nmc_server_submit_ksat(nmc_server *s, int32_t n_vars, int32_t n_clauses, int
   // host-side build (checks, colouring, lists) here, on the caller's thread; a malformed
   // formula is reported by the request's status, as any admission failure
   nmc::prepare_ksat(n_vars, n_clauses, k_max, lits, &r->prep);
+  r->n_colours = r->prep.n_colours;
   r->batchable = r->prep.code == NMC_OK && r->prep.nb <= 7 && n_vars <= s->batch_max_vars;
   return submit(s, r, t_arrive, req_out);
 }
