@@ -213,6 +213,31 @@ def test_full_size_sampled_replicas(ctx, run_path):
     assert np.all(got["best_energies"] <= got["energies"])
 
 
+@pytest.mark.parametrize("extra", [0, 1])
+def test_largest_shared_memory_instance(ctx, extra):
+    """The largest formula whose word vector fits one CTA's shared memory (next to the acceptance
+    table) runs on the cluster kernel; one variable more goes to the grid-barrier kernel. Both
+    give the oracle's trajectories on sampled replicas, and every replica's energy matches a
+    recount of its state."""
+    n = ctx.batch_max_vars() + extra
+    assert 40_000 < n < 60_000
+    T, R = 8, 64
+    lits = W.random_ksat(n, 9.6, 4, 900 + extra)
+    beta = W.beta_inhomogeneous_linear(n, T, 0.5, 4.0, 0.3, 0.5, 901 + extra)
+    inst = ctx.load_ksat(lits, n)
+    ctx.set_schedule(inst, beta)
+    rs = ctx.replicas_create(inst, R, seed=11)
+    ctx.replicas_run(rs, 0, T)
+    got = ctx.replicas_read(rs)
+    ctx.replicas_destroy(rs)
+    ctx.unload(inst)
+    ids = np.array([0, 31, 32, 63], dtype=np.int32)
+    want = O.ksat_anneal(lits, n, beta, 0, T, 11, replica_ids=ids)
+    _same(got, want, ids)
+    assert np.array_equal(O.ksat_energies(lits, n, got["states"]), got["energies"])
+    assert np.array_equal(O.ksat_energies(lits, n, got["best_states"]), got["best_energies"])
+
+
 @pytest.mark.parametrize("warps", [0, 1, 2, 4])
 @pytest.mark.parametrize("n,alpha,k,R,T", [
     (500, 9.6, 4, 1024, 20),    # one 32-word group
