@@ -42,12 +42,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
+TRAFFIC_FILE = "ksat_batch_4sat_n50000_r1024_traffic.json"  # under profiles/
+
+
 def captured_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu capture, or None if the kernel source has
     changed since the counters were taken (or the workload differs)."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", TRAFFIC_FILE)) as f:
             rec = json.load(f)[kernel]
         with open(os.path.join(ROOT, rec["source"]), "rb") as f:
             h = hashlib.sha256(f.read()).hexdigest()[:16]

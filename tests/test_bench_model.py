@@ -41,7 +41,7 @@ def test_traffic_record_dropped_when_source_changes(tmp_path, monkeypatch):
     (tmp_path / "profiles").mkdir()
     rec = {"k": {"workload": "w", "source_sha256_16": h, "source": "k.cu",
                  "dram_bytes_read": 1000, "dram_bytes_write": 24}}
-    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    (tmp_path / "profiles" / bench.TRAFFIC_FILE).write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.captured_traffic("k", "w") == 1024
     assert bench.captured_traffic("k", "other workload") is None
@@ -51,8 +51,9 @@ def test_traffic_record_dropped_when_source_changes(tmp_path, monkeypatch):
 
 
 def test_committed_traffic_record_names_an_existing_source():
+    import bench
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    with open(os.path.join(root, "profiles", "traffic.json")) as f:
+    with open(os.path.join(root, "profiles", bench.TRAFFIC_FILE)) as f:
         rec = json.load(f)
     for r in rec.values():
         assert os.path.exists(os.path.join(root, r["source"]))
