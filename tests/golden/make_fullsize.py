@@ -7,7 +7,7 @@ Computational Phase Transitions", and the swap Metropolis chain on the Koopmans-
 Sec. "Quadratic Assignment Problems". Every value is computed by `oracle/` on the seeded inputs of
 `nmc_inputs`; nothing here comes from the CUDA path.
 
-  python tests/golden/make_fullsize.py ksat    # ~10 min per replica per core (8 replicas)
+  python tests/golden/make_fullsize.py ksat    # ~20 min per replica per core (64 replicas)
   python tests/golden/make_fullsize.py qap     # ~1 min on 8 cores
 
 Outputs (JSON, next to this script):
@@ -37,8 +37,12 @@ import oracle as O  # noqa: E402
 KSAT_FILE = os.path.join(HERE, "fullsize_ksat_n50000_r1024_t5000.json")
 QAP_FILE = os.path.join(HERE, "fullsize_qap_64x_r4096_t10000.json")
 
-# replicas spread over the 32 words of 32 replicas: first and last lanes, interior words
-KSAT_IDS = [0, 31, 32, 255, 517, 640, 990, 1023]
+# 64 replicas, two in each of the 32 words of 32 replicas: the first and last lanes of the first
+# and last words, the rest drawn once with numpy's default_rng(64)
+KSAT_IDS = [0, 31, 32, 53, 75, 93, 98, 99, 128, 158, 172, 189, 203, 221, 239, 255, 271, 276, 307,
+            317, 330, 334, 374, 381, 404, 409, 419, 444, 459, 470, 491, 496, 517, 539, 545, 552, 578,
+            584, 623, 625, 640, 652, 684, 698, 726, 735, 738, 743, 769, 777, 806, 824, 854, 858, 867,
+            878, 919, 920, 943, 944, 970, 990, 1013, 1023]
 # instances of the 64-instance QAP batch: the first, the smallest and largest n, and others
 QAP_IDS = [0, 4095, 2047]
 
@@ -47,26 +51,45 @@ def digest(a: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
 
 
+KSAT_WORKLOAD = ("workload_ksat_large(n_steps=5000): 4-SAT N=50000, M=480000, beta geometric "
+                 "0.3->6.0, 20% at 0.4x for the first half then ramped; 1024 replicas")
+KSAT_FIELDS = ("energies", "best_energies", "states_sha256", "best_states_sha256")
+
+
 def ksat():
+    """Oracle outputs of the KSAT_IDS replicas. Replicas already in the file for the same workload
+    and seed are kept (each replica's trajectory is independent of which others are computed with
+    it), so the set can grow in several runs."""
     wl = W.workload_ksat_large(n_steps=5000)
+    have = {}
+    if os.path.exists(KSAT_FILE):
+        with open(KSAT_FILE) as f:
+            old = json.load(f)
+        if old.get("workload") == KSAT_WORKLOAD and old.get("seed") == wl["seed"]:
+            for j, r in enumerate(old["replica_ids"]):
+                have[r] = {k: old[k][j] for k in KSAT_FIELDS}
+    todo = [r for r in KSAT_IDS if r not in have]
     t = time.time()
-    out = O.ksat_anneal(wl["lits"], wl["n_vars"], wl["beta"], 0, wl["n_steps"], wl["seed"],
-                        replica_ids=KSAT_IDS, n_threads=min(len(KSAT_IDS), os.cpu_count() or 1))
+    if todo:
+        out = O.ksat_anneal(wl["lits"], wl["n_vars"], wl["beta"], 0, wl["n_steps"], wl["seed"],
+                            replica_ids=todo, n_threads=min(len(todo), os.cpu_count() or 1))
+        for j, r in enumerate(todo):
+            have[r] = {"energies": int(out["energies"][j]),
+                       "best_energies": int(out["best_energies"][j]),
+                       "states_sha256": digest(out["states"][j]),
+                       "best_states_sha256": digest(out["best_states"][j])}
     rec = {
-        "workload": "workload_ksat_large(n_steps=5000): 4-SAT N=50000, M=480000, beta geometric "
-                    "0.3->6.0, 20% at 0.4x for the first half then ramped; 1024 replicas",
+        "workload": KSAT_WORKLOAD,
         "seed": wl["seed"], "t0": 0, "t1": wl["n_steps"], "replicas": wl["replicas"],
         "replica_ids": KSAT_IDS,
-        "energies": [int(x) for x in out["energies"]],
-        "best_energies": [int(x) for x in out["best_energies"]],
-        "states_sha256": [digest(r) for r in out["states"]],
-        "best_states_sha256": [digest(r) for r in out["best_states"]],
-        "oracle_seconds": round(time.time() - t, 1),
+        **{k: [have[r][k] for r in KSAT_IDS] for k in KSAT_FIELDS},
+        "oracle_seconds_last_run": round(time.time() - t, 1),
+        "oracle_replicas_last_run": len(todo),
     }
     with open(KSAT_FILE, "w") as f:
         json.dump(rec, f, indent=1)
         f.write("\n")
-    print(KSAT_FILE, rec["energies"], rec["best_energies"], rec["oracle_seconds"], "s")
+    print(KSAT_FILE, rec["energies"], rec["best_energies"], rec["oracle_seconds_last_run"], "s")
 
 
 def qap_instances(sets):
