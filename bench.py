@@ -434,26 +434,6 @@ def run_ksat_small(args):
                                        f"sweeps, rate from the difference ({wall:.1f} s wall)"}}
 
 
-def _ksat_mix(n_inst, T, mix, seed):
-    """The uneven batch of the batched workload: instance i is kind mix[j] (k, alpha) with j
-    drawn uniformly, N uniform in [1000, 20000], replicas uniform in [32, 256]; beta linear 0.5
-    -> 4.0 with a seeded 30% at 0.5x (factored form)."""
-    s = W.Stream(seed)
-    kind = s.below(len(mix), n_inst)
-    ns = 1000 + s.below(19001, n_inst)
-    rs_n = 32 + s.below(225, n_inst)
-    base = W.linear_profile(0.5, 4.0, T).astype(np.float32)
-    out = []
-    for i in range(n_inst):
-        k, alpha = mix[int(kind[i])]
-        n = int(ns[i])
-        lits = W.random_ksat(n, alpha, k, seed * 1000 + i)
-        factor = np.where(W.seeded_subset(n, 0.3, seed * 2000 + i), 0.5, 1.0).astype(np.float32)
-        out.append(dict(lits=lits, n=n, k=k, factor=factor, base=base, R=int(rs_n[i]),
-                        seed=10_000 + i))
-    return out
-
-
 def run_ksat_batch(args, wide=False):
     """Uneven batch in one persistent launch per step: 256 instances of random 3-SAT (alpha 4.2)
     or 4-SAT (alpha 9.6), N in [1000, 20000], 32..256 replicas, 2000 sweeps, factored schedules.
@@ -466,7 +446,7 @@ def run_ksat_batch(args, wide=False):
         n_inst, T, mix, seed = 64, 1000, [(3, 4.2), (6, 12.0)], 1006
     else:
         n_inst, T, mix, seed = args.batch_instances, 2000, [(3, 4.2), (4, 9.6)], 1003
-    specs = _ksat_mix(n_inst, T, mix, seed)
+    specs = W.workload_ksat_mix(n_inst, T, mix, seed)
     sets, attempts, per, bytes_step = [], 0, [], 0
     for sp in specs:
         inst = ctx.load_ksat(sp["lits"], sp["n"])

@@ -211,6 +211,28 @@ def workload_ksat_batch(n_instances: int = 256, n_steps: int = 2000, n_min=1000,
     return out
 
 
+def workload_ksat_mix(n_instances: int = 256, n_steps: int = 2000, mix=((3, 4.2), (4, 9.6)),
+                      seed: int = 1003):
+    """The uneven batch of the batched benchmark: instance i is kind mix[j] (k, alpha) with j
+    drawn uniformly, N uniform in [1000, 20000], replicas uniform in [32, 256], Philox seed
+    10,000 + i; a factored schedule: base[t] linear 0.5 -> 4.0 over n_steps, factor[u] 0.5 on a
+    seeded 30% of the variables and 1 elsewhere (beta[u][t] = float32(factor[u] * base[t]))."""
+    s = Stream(seed)
+    kind = s.below(len(mix), n_instances)
+    ns = 1000 + s.below(19001, n_instances)
+    rs_n = 32 + s.below(225, n_instances)
+    base = linear_profile(0.5, 4.0, n_steps).astype(np.float32)
+    out = []
+    for i in range(n_instances):
+        k, alpha = mix[int(kind[i])]
+        n = int(ns[i])
+        lits = random_ksat(n, alpha, k, seed * 1000 + i)
+        factor = np.where(seeded_subset(n, 0.3, seed * 2000 + i), 0.5, 1.0).astype(np.float32)
+        out.append(dict(lits=lits, n=n, k=k, factor=factor, base=base, R=int(rs_n[i]),
+                        seed=10_000 + i))
+    return out
+
+
 def workload_qap_batch(n_instances: int = 64, n_steps: int = 10_000, n_min=32, n_max=256,
                        replicas=4096, seed=1004):
     """QAP batch: n uniform in [n_min, n_max], F,D symmetric uniform [0,99] (F half zeros),

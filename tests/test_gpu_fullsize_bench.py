@@ -69,6 +69,40 @@ def test_ksat_bench_workload_full_length(ctx):
                           got["best_energies"][rows])
 
 
+def test_ksat_batch_workload_full_length(ctx):
+    """The batched benchmark's launch: 256 uneven sets, launch shapes tuned on 8 sweeps (states
+    restored), then all 2,000 sweeps of every set in one batched launch."""
+    g = _golden("fullsize_ksat_batch_256x_t2000.json")
+    specs = W.workload_ksat_mix(256, 2000, ((3, 4.2), (4, 9.6)), 1003)
+    insts, sets = [], []
+    for s in specs:
+        inst = ctx.load_ksat(s["lits"], s["n"])
+        ctx.set_schedule_factored(inst, s["base"], s["factor"])
+        insts.append(inst)
+        sets.append(ctx.replicas_create(inst, s["R"], seed=s["seed"]))
+    ctx.batch_autotune(sets, 0, 8)
+    ctx.batch_run(sets, g["t0"], g["t1"])
+    checked = {rec["instance"]: rec for rec in g["instances"]}
+    for i, (s, rs) in enumerate(zip(specs, sets)):
+        if i in checked or i % 32 == 0:
+            got = ctx.replicas_read(rs)
+            assert np.all(got["best_energies"] <= got["energies"])
+            rows = np.arange(0, s["R"], 37)
+            assert np.array_equal(O.ksat_energies(s["lits"], s["n"], got["states"][rows]),
+                                  got["energies"][rows])
+            rec = checked.get(i)
+            if rec is not None:
+                assert rec["n"] == s["n"] and rec["seed"] == s["seed"] and rec["replicas"] == s["R"]
+                for j, r in enumerate(rec["replica_ids"]):
+                    assert int(got["energies"][r]) == rec["energies"][j], (i, r)
+                    assert int(got["best_energies"][r]) == rec["best_energies"][j], (i, r)
+                    assert _digest(got["states"][r]) == rec["states_sha256"][j], (i, r)
+                    assert _digest(got["best_states"][r]) == rec["best_states_sha256"][j], (i, r)
+        ctx.replicas_destroy(rs)
+    for inst in insts:
+        ctx.unload(inst)
+
+
 def test_qap_bench_workload_full_length(ctx):
     g = _golden("fullsize_qap_64x_r4096_t10000.json")
     specs = W.workload_qap_batch()
