@@ -9,13 +9,15 @@ Sec. "Quadratic Assignment Problems". Every value is computed by `oracle/` on th
 
   python tests/golden/make_fullsize.py ksat    # ~20 min per replica per core (64 replicas)
   python tests/golden/make_fullsize.py qap     # ~1 min on 8 cores
-  python tests/golden/make_fullsize.py batch   # ~20 min of one core per largest-instance replica
+  python tests/golden/make_fullsize.py batch   # ~8 min on 3 cores
+  python tests/golden/make_fullsize.py wide    # ~10 min on 3 cores
 
 Outputs (JSON, next to this script):
   fullsize_ksat_n50000_r1024_t5000.json   4-SAT N=50,000, M=480,000, 1,024 replicas, 5,000 sweeps
   fullsize_qap_64x_r4096_t10000.json      64 QAP instances, n in [32, 256], 4,096 replicas, 10^4 steps
   fullsize_ksat_batch_256x_t2000.json     256 uneven 3-/4-SAT instances, N in [1000, 20000],
                                           32..256 replicas, 2,000 sweeps, factored schedules
+  fullsize_ksat_wide_64x_t1000.json       64 uneven 3-SAT / 6-SAT instances, 1,000 sweeps
 Per sampled replica: final and best energies and SHA-256 digests of the final and best states
 (uint8 [N] assignments in the original variable order; int16 [n] little-endian permutations).
 """
@@ -40,6 +42,7 @@ import oracle as O  # noqa: E402
 KSAT_FILE = os.path.join(HERE, "fullsize_ksat_n50000_r1024_t5000.json")
 QAP_FILE = os.path.join(HERE, "fullsize_qap_64x_r4096_t10000.json")
 BATCH_FILE = os.path.join(HERE, "fullsize_ksat_batch_256x_t2000.json")
+WIDE_FILE = os.path.join(HERE, "fullsize_ksat_wide_64x_t1000.json")
 
 # 64 replicas, two in each of the 32 words of 32 replicas: the first and last lanes of the first
 # and last words, the rest drawn once with numpy's default_rng(64)
@@ -131,20 +134,25 @@ def qap():
     print(QAP_FILE, rec["oracle_seconds"], "s")
 
 
-# instances of the 256-instance batch: the first two (4-SAT, 3-SAT), the smallest N, the
-# largest N (also the most replicas), the fewest replicas, the last
-BATCH_INSTANCES = [0, 1, 6, 35, 121, 255]
+# Batched workloads: (instances, sweeps, mix of (k, alpha), seed, output file, checked instances).
+# "batch": the first two (4-SAT, 3-SAT), the smallest N, the largest N (also the most replicas),
+# the fewest replicas, the last. "wide": the first 3-SAT and 6-SAT, the largest 6-SAT, the
+# smallest and largest N, the fewest (a 6-SAT) and most replicas, the last.
+BATCHES = {
+    "batch": (256, 2000, ((3, 4.2), (4, 9.6)), 1003, BATCH_FILE, [0, 1, 6, 35, 121, 255]),
+    "wide": (64, 1000, ((3, 4.2), (6, 12.0)), 1006, WIDE_FILE, [0, 4, 17, 47, 19, 52, 12, 63]),
+}
 
 
-def batch():
-    """The batched benchmark's instances as the batch launch runs them once from their initial
-    states: sweeps 0..1999 of each set, beta[u][t] = float32(factor[u] * base[t])."""
-    specs = W.workload_ksat_mix(256, 2000, ((3, 4.2), (4, 9.6)), 1003)
+def batch(which="batch"):
+    """A batched benchmark's instances as the batch launch runs them once from their initial
+    states: sweeps 0..T-1 of each set, beta[u][t] = float32(factor[u] * base[t])."""
+    n_inst, T, mix, seed, path, pick = BATCHES[which]
+    specs = W.workload_ksat_mix(n_inst, T, mix, seed)
     t = time.time()
     recs = []
-    for i in BATCH_INSTANCES:
+    for i in pick:
         s = specs[i]
-        T = len(s["base"])
         beta = (s["factor"][:, None] * s["base"][None, :]).astype(np.float32)
         ids = [0, s["R"] // 2, s["R"] - 1]
         out = O.ksat_anneal(s["lits"], s["n"], beta, 0, T, s["seed"], replica_ids=ids,
@@ -155,22 +163,24 @@ def batch():
                      "best_energies": [int(x) for x in out["best_energies"]],
                      "states_sha256": [digest(r) for r in out["states"]],
                      "best_states_sha256": [digest(r) for r in out["best_states"]]})
-        print("batch instance", i, "n", s["n"], recs[-1]["energies"], flush=True)
-    rec = {"workload": "workload_ksat_mix(256, 2000, ((3, 4.2), (4, 9.6)), 1003): 3-SAT alpha "
-                       "4.2 or 4-SAT alpha 9.6, N uniform in [1000, 20000], 32..256 replicas, "
-                       "beta = factor x base (linear 0.5->4.0, 30% at 0.5x), 2000 sweeps",
-           "t0": 0, "t1": 2000, "instances": recs, "oracle_seconds": round(time.time() - t, 1)}
-    with open(BATCH_FILE, "w") as f:
+        print(which, "instance", i, "n", s["n"], "k", s["k"], recs[-1]["energies"], flush=True)
+    kinds = " or ".join(f"{k}-SAT alpha {a}" for k, a in mix)
+    rec = {"workload": f"workload_ksat_mix({n_inst}, {T}, {mix}, {seed}): {kinds}, N uniform in "
+                       "[1000, 20000], 32..256 replicas, beta = factor x base (linear 0.5->4.0, "
+                       f"30% at 0.5x), {T} sweeps",
+           "t0": 0, "t1": T, "instances": recs, "oracle_seconds": round(time.time() - t, 1)}
+    with open(path, "w") as f:
         json.dump(rec, f, indent=1)
         f.write("\n")
-    print(BATCH_FILE, rec["oracle_seconds"], "s")
+    print(path, rec["oracle_seconds"], "s")
 
 
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["ksat", "qap", "batch"]
+    which = sys.argv[1:] or ["ksat", "qap", "batch", "wide"]
     if "qap" in which:
         qap()
-    if "batch" in which:
-        batch()
+    for b in ("batch", "wide"):
+        if b in which:
+            batch(b)
     if "ksat" in which:
         ksat()

@@ -2,11 +2,13 @@
 
 `bench.py` times a 5,000-sweep anneal of 1,024 replicas of a 50,000-variable 4-SAT formula (the
 sampling stage of Algorithm 1 with a per-variable inverse temperature, Sec. "Nonequilibrium
-inhomogeneous sampling over subgraphs") and a 10^4-step swap anneal of 64 QAP instances with 4,096
-replicas each (Sec. "Quadratic Assignment Problems"). These tests run exactly those launches and
-compare sampled replicas with `tests/golden/fullsize_*.json`, which `tests/golden/make_fullsize.py`
-wrote from the oracle alone (the oracle needs about ten minutes per k-SAT replica, so the expected
-values are stored rather than recomputed here). Final and best energies must be equal and the final
+inhomogeneous sampling over subgraphs"), the same sweep over batches of uneven formulas (256
+3-/4-SAT sets for 2,000 sweeps, 64 3-/6-SAT sets for 1,000) in one launch, and a 10^4-step swap
+anneal of 64 QAP instances with 4,096 replicas each (Sec. "Quadratic Assignment Problems"). These
+tests run exactly those launches and compare sampled replicas with `tests/golden/fullsize_*.json`,
+which `tests/golden/make_fullsize.py` wrote from the oracle alone (the oracle needs about twenty
+minutes per replica of the 50,000-variable run, so the expected values are stored rather than
+recomputed here). Final and best energies must be equal and the final
 and best states equal byte for byte (SHA-256 of each row): tolerance zero, all outputs are integers.
 Every replica is also checked for the invariants best <= final, and a spread of them for energies
 that match a recount of their states.
@@ -69,11 +71,17 @@ def test_ksat_bench_workload_full_length(ctx):
                           got["best_energies"][rows])
 
 
-def test_ksat_batch_workload_full_length(ctx):
-    """The batched benchmark's launch: 256 uneven sets, launch shapes tuned on 8 sweeps (states
-    restored), then all 2,000 sweeps of every set in one batched launch."""
-    g = _golden("fullsize_ksat_batch_256x_t2000.json")
-    specs = W.workload_ksat_mix(256, 2000, ((3, 4.2), (4, 9.6)), 1003)
+@pytest.mark.parametrize("name,n_inst,T,mix,seed", [
+    ("fullsize_ksat_batch_256x_t2000.json", 256, 2000, ((3, 4.2), (4, 9.6)), 1003),
+    ("fullsize_ksat_wide_64x_t1000.json", 64, 1000, ((3, 4.2), (6, 12.0)), 1006),
+])
+def test_ksat_batch_workload_full_length(ctx, name, n_inst, T, mix, seed):
+    """The batched benchmarks' launch: 256 uneven 3-/4-SAT sets (or 64 3-/6-SAT sets, two list
+    entries per occurrence for k = 6), launch shapes tuned on 8 sweeps (states restored), then
+    every sweep of every set in one batched launch."""
+    g = _golden(name)
+    assert g["t1"] == T
+    specs = W.workload_ksat_mix(n_inst, T, mix, seed)
     insts, sets = [], []
     for s in specs:
         inst = ctx.load_ksat(s["lits"], s["n"])
@@ -84,7 +92,7 @@ def test_ksat_batch_workload_full_length(ctx):
     ctx.batch_run(sets, g["t0"], g["t1"])
     checked = {rec["instance"]: rec for rec in g["instances"]}
     for i, (s, rs) in enumerate(zip(specs, sets)):
-        if i in checked or i % 32 == 0:
+        if i in checked or i % 16 == 0:
             got = ctx.replicas_read(rs)
             assert np.all(got["best_energies"] <= got["energies"])
             rows = np.arange(0, s["R"], 37)
