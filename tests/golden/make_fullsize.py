@@ -11,6 +11,8 @@ Sec. "Quadratic Assignment Problems". Every value is computed by `oracle/` on th
   python tests/golden/make_fullsize.py qap     # ~1 min on 8 cores
   python tests/golden/make_fullsize.py batch   # ~8 min on 3 cores
   python tests/golden/make_fullsize.py wide    # ~10 min on 3 cores
+  python tests/golden/make_fullsize.py pt      # ~30 min on one core (the rounds couple a ladder)
+  python tests/golden/make_fullsize.py moves   # ~5 min on 3 cores
 
 Outputs (JSON, next to this script):
   fullsize_ksat_n50000_r1024_t5000.json   4-SAT N=50,000, M=480,000, 1,024 replicas, 5,000 sweeps
@@ -18,6 +20,9 @@ Outputs (JSON, next to this script):
   fullsize_ksat_batch_256x_t2000.json     256 uneven 3-/4-SAT instances, N in [1000, 20000],
                                           32..256 replicas, 2,000 sweeps, factored schedules
   fullsize_ksat_wide_64x_t1000.json       64 uneven 3-SAT / 6-SAT instances, 1,000 sweeps
+  fullsize_pt_4sat_n5000_32x32_t2000.json replica exchange, 32 ladders x 32 temperatures, 2,000 sweeps
+  fullsize_moves_4sat_n50000_r1024_t500.json  two-chain held sampling (500 sweeps), collective
+                                          flip of the backbone, whitening
 Per sampled replica: final and best energies and SHA-256 digests of the final and best states
 (uint8 [N] assignments in the original variable order; int16 [n] little-endian permutations).
 """
@@ -43,6 +48,8 @@ KSAT_FILE = os.path.join(HERE, "fullsize_ksat_n50000_r1024_t5000.json")
 QAP_FILE = os.path.join(HERE, "fullsize_qap_64x_r4096_t10000.json")
 BATCH_FILE = os.path.join(HERE, "fullsize_ksat_batch_256x_t2000.json")
 WIDE_FILE = os.path.join(HERE, "fullsize_ksat_wide_64x_t1000.json")
+PT_FILE = os.path.join(HERE, "fullsize_pt_4sat_n5000_32x32_t2000.json")
+MOVES_FILE = os.path.join(HERE, "fullsize_moves_4sat_n50000_r1024_t500.json")
 
 # 64 replicas, two in each of the 32 words of 32 replicas: the first and last lanes of the first
 # and last words, the rest drawn once with numpy's default_rng(64)
@@ -175,10 +182,85 @@ def batch(which="batch"):
     print(path, rec["oracle_seconds"], "s")
 
 
+def pt():
+    """Replica exchange as the benchmark runs it (Sec. "Nonequilibrium inhomogeneous sampling
+    over subgraphs"; App. "Adaptive Parallel Tempering"): 4-SAT N=5,000, alpha 9.884, 32 ladders
+    of 32 temperatures (geometric 0.5 -> 5.0) over a homogeneous schedule, an exchange round every
+    10 sweeps, 2,000 sweeps, Philox seed 1. Ladder 0 (replicas 0..31) evolves independently of the
+    other ladders, so the oracle runs it alone (single-threaded: the rounds couple its replicas)."""
+    n, alpha, T, L, per = 5000, 9.884, 2000, 32, 10
+    lits = W.random_ksat(n, alpha, 4, 2111)
+    ladder = W.geometric_profile(0.5, 5.0, L).astype(np.float32)
+    t = time.time()
+    out = O.ksat_pt_anneal(lits, n, np.ones((n, T), np.float32), ladder, 0, T, per, 1,
+                           replicas=L)
+    rec = {"workload": "4-SAT N=5000 alpha 9.884 (random_ksat seed 2111), ladder geometric "
+                       "0.5->5.0 x 32, 32 ladders (1024 replicas), beta 1, 2000 sweeps, "
+                       "exchange every 10, Philox seed 1; ladder 0",
+           "t0": 0, "t1": T, "per": per, "replica_ids": list(range(L)),
+           "energies": [int(x) for x in out["energies"]],
+           "best_energies": [int(x) for x in out["best_energies"]],
+           "states_sha256": [digest(r) for r in out["states"]],
+           "best_states_sha256": [digest(r) for r in out["best_states"]],
+           "slots": [int(x) for x in out["slots"]],
+           "oracle_seconds": round(time.time() - t, 1)}
+    with open(PT_FILE, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(PT_FILE, rec["energies"][:4], rec["oracle_seconds"], "s")
+
+
+MOVES_IDS = [0, 517, 1023]
+
+
+def moves():
+    """Two-chain held sampling, then the collective move and whitening, as the benchmark runs
+    them on the 50,000-variable instance (Algorithm 1's cycle; Sec. "Nonequilibrium inhomogeneous
+    sampling over subgraphs"): a seeded 20% backbone, 10 cycles of 20 hot (base 3.0, heat 4) + 20
+    cold + 10 unlearning sweeps, Philox seed 1, then one flip of the backbone at beta 0.75 (move
+    1000) and generalized whitening of the best states."""
+    wl = W.workload_ksat_large(n_steps=2)
+    lits, n = wl["lits"], wl["n_vars"]
+    labels = np.where(W.seeded_subset(n, 0.2, 77), 0, -1).astype(np.int32)
+    cycles, th, tc, tu = 10, 20, 20, 10
+    T = cycles * (th + tc + tu)
+    beta = O.backbone_schedule(labels, 3.0, 4.0, cycles, th, tc, tu)
+    t = time.time()
+    ids = np.array(MOVES_IDS)
+    ch = O.ksat_anneal(lits, n, beta, 0, T, 1, replica_ids=ids, n_threads=len(ids))
+    mask = (labels >= 0).astype(np.uint8)
+    mv = O.ksat_cluster_flip(lits, n, ch, mask, np.full(len(ids), 0.75, np.float32), 1000, 1,
+                             replica_ids=ids)
+    frozen = [int(O.ksat_whitening(lits, n, mv["best_states"][j])[1]) for j in range(len(ids))]
+    rec = {"workload": "workload_ksat_large (4-SAT N=50000, M=480000), 1024 replicas, backbone "
+                       "seeded_subset(n, 0.2, 77), 10 x (20 hot + 20 cold + 10 unlearning), base "
+                       "3.0, heat 4.0, Philox seed 1; flip of the backbone at beta 0.75, move "
+                       "1000; whitening of the best states",
+           "t0": 0, "t1": T, "replica_ids": MOVES_IDS,
+           "chain": {"energies": [int(x) for x in ch["energies"]],
+                     "best_energies": [int(x) for x in ch["best_energies"]],
+                     "states_sha256": [digest(r) for r in ch["states"]],
+                     "best_states_sha256": [digest(r) for r in ch["best_states"]]},
+           "accepted": [int(x) for x in mv["accepted"]],
+           "energies": [int(x) for x in mv["energies"]],
+           "best_energies": [int(x) for x in mv["best_energies"]],
+           "states_sha256": [digest(r) for r in mv["states"]],
+           "best_states_sha256": [digest(r) for r in mv["best_states"]],
+           "frozen": frozen, "oracle_seconds": round(time.time() - t, 1)}
+    with open(MOVES_FILE, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(MOVES_FILE, rec["energies"], rec["accepted"], rec["frozen"], rec["oracle_seconds"], "s")
+
+
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["ksat", "qap", "batch", "wide"]
+    which = sys.argv[1:] or ["ksat", "qap", "batch", "wide", "pt", "moves"]
     if "qap" in which:
         qap()
+    if "moves" in which:
+        moves()
+    if "pt" in which:
+        pt()
     for b in ("batch", "wide"):
         if b in which:
             batch(b)
