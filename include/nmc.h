@@ -171,7 +171,10 @@ int nmc_replicas_read_device(nmc_ctx *ctx, int32_t rs, const nmc_result *out_dev
 
 /*
  * Batched sweeps: runs sweeps t0[i]..t1[i]-1 of k-SAT replica sets rs[i] (i < n_sets), all in
- * one persistent launch, asynchronously on the context's stream. Each set's result is bit for
+ * one persistent launch per occurrence width (formulas with k <= 4 and with 4 < k <= 8),
+ * asynchronously on the context's stream; when both widths are present the k > 4 launch runs
+ * beside the other on an auxiliary stream of the context, forked from and joined back to the
+ * context's stream, so work enqueued later on that stream still follows. Each set's result is bit for
  * bit what nmc_replicas_run gives for it alone. Work is split into items of one word (32
  * replicas) of one set; a CTA runs an item with the word vector in shared memory, so each
  * instance needs n_vars <= the limit of nmc_batch_max_vars() and every variable in at most 127

@@ -91,6 +91,11 @@ struct nmc_ctx {
   cudaStream_t qaux[kQapShapes] = {};
   cudaEvent_t qfork = nullptr;
   cudaEvent_t qjoin[kQapShapes] = {};
+  // auxiliary stream of the batched k-SAT launch of the second occurrence width (created on first
+  // use): forked after the work-list upload and joined back, so that the two widths' persistent
+  // launches share the SMs (the second fills those the first's tail leaves idle)
+  cudaStream_t kaux = nullptr;
+  cudaEvent_t kfork = nullptr, kjoin = nullptr;
   // tuned batched-sweep shapes: (occurrence width, largest n, work items) -> (cs, lanes)
   std::map<std::tuple<int, int, int>, std::pair<int, int>> tune;
 };
@@ -408,12 +413,35 @@ int launch_items(nmc_ctx *ctx, const std::vector<BatchItem> &items, const size_t
   NMC_CUDA(cudaMemcpyAsync(ctx->items, items.data(), sizeof(BatchItem) * items.size(),
                            cudaMemcpyHostToDevice, ctx->stream),
            "upload batch work list");
-  for (int q = 0; q < 2; ++q) {
-    if (!cnt[q]) continue;
+  if (!cnt[0] || !cnt[1]) {
+    const int q = cnt[0] ? 0 : 1;
     NMC_CUDA(ksat_batch(ctx->items + off[q], cnt[q], q + 1, cs[q], max_n[q], ctx->next_item + q,
                         ctx->tab, ctx->tab_len, ctx->device, ctx->stream, pt, lanes[q]),
              "launch batched sweep");
+    return NMC_OK;
   }
+  // both widths: the two-entry items (k > 4) on the auxiliary stream, launched first, the
+  // one-entry items on the context's stream, which then waits for the auxiliary one
+  if (!ctx->kaux) {
+    NMC_CUDA(cudaStreamCreateWithFlags(&ctx->kaux, cudaStreamNonBlocking), "create batch stream");
+    NMC_CUDA(cudaEventCreateWithFlags(&ctx->kfork, cudaEventDisableTiming), "create batch event");
+    NMC_CUDA(cudaEventCreateWithFlags(&ctx->kjoin, cudaEventDisableTiming), "create batch event");
+  }
+  NMC_CUDA(cudaEventRecord(ctx->kfork, ctx->stream), "fork batch stream");
+  NMC_CUDA(cudaStreamWaitEvent(ctx->kaux, ctx->kfork, 0), "fork batch stream");
+  const cudaError_t e1 = ksat_batch(ctx->items + off[1], cnt[1], 2, cs[1], max_n[1],
+                                    ctx->next_item + 1, ctx->tab, ctx->tab_len, ctx->device,
+                                    ctx->kaux, pt, lanes[1]);
+  // joined whether or not the launch succeeded, so that nothing is left unjoined
+  const cudaError_t ej = cudaEventRecord(ctx->kjoin, ctx->kaux);
+  const cudaError_t e0 = ksat_batch(ctx->items + off[0], cnt[0], 1, cs[0], max_n[0],
+                                    ctx->next_item, ctx->tab, ctx->tab_len, ctx->device,
+                                    ctx->stream, pt, lanes[0]);
+  cudaError_t ew = ej == cudaSuccess ? cudaStreamWaitEvent(ctx->stream, ctx->kjoin, 0) : ej;
+  if (ew != cudaSuccess) cudaStreamSynchronize(ctx->kaux);  // no join: wait on the host instead
+  if (e1 != cudaSuccess) return cuda_fail(ctx, e1, "launch batched sweep");
+  if (e0 != cudaSuccess) return cuda_fail(ctx, e0, "launch batched sweep");
+  if (ew != cudaSuccess) return cuda_fail(ctx, ew, "join batch stream");
   return NMC_OK;
 }
 
@@ -522,6 +550,12 @@ void nmc_destroy(nmc_ctx *ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->kaux) {
+    cudaStreamSynchronize(ctx->kaux);
+    cudaStreamDestroy(ctx->kaux);
+  }
+  if (ctx->kfork) cudaEventDestroy(ctx->kfork);
+  if (ctx->kjoin) cudaEventDestroy(ctx->kjoin);
   for (auto &kv : ctx->sets) free_set(kv.second);
   for (auto &kv : ctx->insts) free_instance(kv.second);
   dev_free(ctx->tab);
