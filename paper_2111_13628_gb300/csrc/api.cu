@@ -1062,7 +1062,9 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
   //    an entry is {sign bytes, 4u1, 4u2, 4u3}: the other literals as byte offsets of their
   //    variable's word in the shared-memory word vector, and bit 7 of byte 0 / 1 / 2 / 3 of the
   //    first field set when the own literal / literal 1 / 2 / 3 is negated. For k > 4 the two
-  //    int4 hold the literal ids as in the per-variable lists.
+  //    int4 are {sign bits, 4u1, 4u2, 4u3} and {4u4, 4u5, 4u6, 4u7}: the same byte offsets, the
+  //    signs of the own literal and literals 1..3 in bit 7 and those of literals 4..7 in bit 6
+  //    of bytes 0..3 of the first field (unused literals: word n, which is always 0, positive).
   std::vector<int32_t> cgrp(n_colours + 1, 0), grp_base(1, 0), grp_v0;
   for (int32_t c = 0; c < n_colours; ++c) {
     const int32_t size = col_ptr[c + 1] - col_ptr[c];
@@ -1107,32 +1109,23 @@ int prepare_ksat(int32_t n_vars, int32_t n_clauses, int32_t k_max, const int32_t
                  &occ_t[static_cast<size_t>(grp_base[g]) * 4]);
         continue;
       }
+      // k > 4: two int4 per occurrence (src: {own sign mask, lit1..lit7} in literal ids; inert:
+      // own sign 0, literal 1 always true (word n negated), the rest always false (word n))
       for (int32_t l = 0; l < 32; ++l) {
         const int32_t v = g0 + l;
-        for (int32_t j = 0; j < len; ++j)
-          for (int q = 0; q < kq; ++q) {
-            int32_t *dst = &occ_t[(static_cast<size_t>(grp_base[g]) + (j * kq + q) * 32 + l) * 4];
-            const bool real = v < cend && j < occ_ptr[v + 1] - occ_ptr[v];
-            const int32_t *src = real ? &occ[(static_cast<size_t>(occ_ptr[v] + j) * slots) + 4 * q] : nullptr;
-            if (kq == 1) {
-              // src: {own sign mask, lit1, lit2, lit3} in literal ids (2u + neg)
-              const int32_t own_neg = real ? (src[0] != 0) : 0;
-              uint32_t signs = static_cast<uint32_t>(own_neg) << 7;
-              for (int z = 1; z < 4; ++z) {
-                const int32_t lit = real ? src[z] : (z == 1 ? lit_true : lit_false);
-                signs |= static_cast<uint32_t>(lit & 1) << (8 * z + 7);
-                dst[z] = (lit >> 1) * 4;
-              }
-              dst[0] = static_cast<int32_t>(signs);
-            } else if (real) {
-              for (int z = 0; z < 4; ++z) dst[z] = src[z];
-            } else {  // inert: own sign 0, one always-true literal
-              dst[0] = q == 0 ? 0 : lit_false;
-              dst[1] = q == 0 ? lit_true : lit_false;
-              dst[2] = lit_false;
-              dst[3] = lit_false;
-            }
-          }
+        for (int32_t j = 0; j < len; ++j) {
+          int32_t *dst = &occ_t[(static_cast<size_t>(grp_base[g]) + j * kq * 32 + l) * 4];
+          int32_t *dst2 = dst + 32 * 4;  // the occurrence's second int4, one warp row further
+          const bool real = v < cend && j < occ_ptr[v + 1] - occ_ptr[v];
+          const int32_t *src = real ? &occ[static_cast<size_t>(occ_ptr[v] + j) * slots] : nullptr;
+          auto lit = [&](int z) { return real ? src[z] : (z == 1 ? lit_true : lit_false); };
+          uint32_t signs = static_cast<uint32_t>(real && src[0] != 0) << 7;
+          for (int z = 1; z < 4; ++z) signs |= static_cast<uint32_t>(lit(z) & 1) << (8 * z + 7);
+          for (int z = 4; z < 8; ++z) signs |= static_cast<uint32_t>(lit(z) & 1) << (8 * (z - 4) + 6);
+          dst[0] = static_cast<int32_t>(signs);
+          for (int z = 1; z < 4; ++z) dst[z] = (lit(z) >> 1) * 4;
+          for (int z = 0; z < 4; ++z) dst2[z] = (lit(4 + z) >> 1) * 4;
+        }
       }
     }
   }, 32);  // a group is 32 variables' lists

@@ -137,9 +137,20 @@ __device__ __forceinline__ int sext_byte(uint32_t x, int b) {
   return (int)r;
 }
 
-// Truth value (32 replicas) of literal id l = 2u + neg from the word vector in shared memory.
-__device__ __forceinline__ uint32_t lit_word(const uint32_t *xs, int l) {
-  return xs[l >> 1] ^ (0u - (uint32_t)(l & 1));
+// OR over the clause's other literals of their truth values (32 replicas), from an occurrence's
+// entry: q = {sign bits, byte offsets of literals 1..3}; for k > 4 also q2 = {byte offsets of
+// literals 4..7}, whose signs sit in bit 6 of bytes 0..3 of q.x (shifted up to bit 7 here).
+template <int KQ>
+__device__ __forceinline__ uint32_t others_or(const uint32_t *xs, const int4 &q, const int4 &q2) {
+  const uint32_t sg = (uint32_t)q.x;
+  uint32_t o = (xs_at(xs, q.y) ^ sign_mask<1>(sg)) | (xs_at(xs, q.z) ^ sign_mask<2>(sg)) |
+               (xs_at(xs, q.w) ^ sign_mask<3>(sg));
+  if (KQ == 2) {
+    const uint32_t s6 = sg << 1;
+    o |= (xs_at(xs, q2.x) ^ sign_mask<0>(s6)) | (xs_at(xs, q2.y) ^ sign_mask<1>(s6)) |
+         (xs_at(xs, q2.z) ^ sign_mask<2>(s6)) | (xs_at(xs, q2.w) ^ sign_mask<3>(s6));
+  }
+  return o;
 }
 
 // Adds the bit-sliced counter p into c (ripple carry).
@@ -213,19 +224,8 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int4 q = qc[j * KQ];
-      uint32_t o, own;
-      if (KQ == 1) {
-        const uint32_t sg = (uint32_t)q.x;
-        o = (xs_at(xs, q.y) ^ sign_mask<1>(sg)) |
-            (xs_at(xs, q.z) ^ sign_mask<2>(sg)) |
-            (xs_at(xs, q.w) ^ sign_mask<3>(sg));
-        own = x ^ sign_mask<0>(sg);
-      } else {
-        o = lit_word(xs, q.y) | lit_word(xs, q.z) | lit_word(xs, q.w);
-        const int4 q2 = qc[j * KQ + 1];
-        o |= lit_word(xs, q2.x) | lit_word(xs, q2.y) | lit_word(xs, q2.z) | lit_word(xs, q2.w);
-        own = x ^ (uint32_t)q.x;
-      }
+      const uint32_t o = others_or<KQ>(xs, q, qc[j * KQ + KQ - 1]);
+      const uint32_t own = x ^ sign_mask<0>((uint32_t)q.x);
       bb[j] = own & ~o;
       mm[j] = ~(own | o);
     }
@@ -429,19 +429,8 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
       mm[i] = 0u;
       if (j < len) {
         const int4 q = qc[i * KQ];
-        uint32_t o, own;
-        if (KQ == 1) {
-          const uint32_t sg = (uint32_t)q.x;
-          o = (xs_at(xs, q.y) ^ sign_mask<1>(sg)) |
-              (xs_at(xs, q.z) ^ sign_mask<2>(sg)) |
-              (xs_at(xs, q.w) ^ sign_mask<3>(sg));
-          own = x ^ sign_mask<0>(sg);
-        } else {
-          const int4 q2 = qc[i * KQ + 1];
-          o = lit_word(xs, q.y) | lit_word(xs, q.z) | lit_word(xs, q.w) | lit_word(xs, q2.x) |
-              lit_word(xs, q2.y) | lit_word(xs, q2.z) | lit_word(xs, q2.w);
-          own = x ^ (uint32_t)q.x;
-        }
+        const uint32_t o = others_or<KQ>(xs, q, qc[i * KQ + KQ - 1]);
+        const uint32_t own = x ^ sign_mask<0>((uint32_t)q.x);
         bb[i] = own & ~o;
         mm[i] = ~(own | o);
       }
@@ -480,19 +469,9 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
         mm[i] = 0u;
         if (j < len) {
           const int4 q = __ldg(ent + (size_t)(j * KQ) * 32);
-          uint32_t o, own;
-          if (KQ == 1) {
-            const uint32_t sg = (uint32_t)q.x;
-            o = (xs_at(xs, q.y) ^ sign_mask<1>(sg)) |
-                (xs_at(xs, q.z) ^ sign_mask<2>(sg)) |
-                (xs_at(xs, q.w) ^ sign_mask<3>(sg));
-            own = x ^ sign_mask<0>(sg);
-          } else {
-            o = lit_word(xs, q.y) | lit_word(xs, q.z) | lit_word(xs, q.w);
-            const int4 q2 = __ldg(ent + (size_t)(j * KQ + 1) * 32);
-            o |= lit_word(xs, q2.x) | lit_word(xs, q2.y) | lit_word(xs, q2.z) | lit_word(xs, q2.w);
-            own = x ^ (uint32_t)q.x;
-          }
+          const int4 q2 = KQ == 2 ? __ldg(ent + (size_t)(j * KQ + 1) * 32) : q;
+          const uint32_t o = others_or<KQ>(xs, q, q2);
+          const uint32_t own = x ^ sign_mask<0>((uint32_t)q.x);
           bb[i] = own & ~o;
           mm[i] = ~(own | o);
         }
