@@ -333,7 +333,8 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
   // (bq * dE) >> 8 in 32-bit pieces: bq = 256 hi + lo, so the index is hi dE + (lo dE) >> 8
   // exactly (dE <= 127 keeps both terms below 2^31).
   const uint32_t bq_hi = bqv >> 8, bq_lo = bqv & 255u;
-  uint32_t flip = 0u;
+  // replicas whose dE <= 0 (sign plane set, or every plane zero) accept without a draw
+  uint32_t flip = s8[7] | ~(s8[0] | s8[1] | s8[2] | s8[3] | s8[4] | s8[5] | s8[6]);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     // replicas 8q .. 8q+7: Philox groups 2q and 2q+1, drawn together and always (a draw that
@@ -347,18 +348,17 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       de[j] = sext_byte(j < 4 ? xlo : xhi, j & 3);
-      th[j] = 0u;
-      if (de[j] > 0) {
-        uint32_t hi = bq_hi, lo = bq_lo;
-        if (PT) {
-          const unsigned long long be = ((unsigned long long)mult_s[8 * q + j] * bqv) >> 16;
-          const uint32_t b = be > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)be;
-          hi = b >> 8;  // below 2^24, so hi dE stays below 2^31
-          lo = b & 255u;
-        }
-        const uint32_t idx = hi * (uint32_t)de[j] + ((lo * (uint32_t)de[j]) >> 8);
-        th[j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
+      uint32_t hi = bq_hi, lo = bq_lo;
+      if (PT) {
+        const unsigned long long be = ((unsigned long long)mult_s[8 * q + j] * bqv) >> 16;
+        const uint32_t b = be > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)be;
+        hi = b >> 8;  // below 2^24, so hi dE stays below 2^31
+        lo = b & 255u;
       }
+      // for dE <= 0 the index is meaningless but clamped into the table; those replicas
+      // accept whatever the comparison gives
+      const uint32_t idx = hi * (uint32_t)de[j] + ((lo * (uint32_t)de[j]) >> 8);
+      th[j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
     }
     uint4 u0, u1;
     philox4x32_10_x2(make_uint4(vo, (uint32_t)t, (uint32_t)(8 * B.w + 2 * q), kTagKsatSweep),
@@ -367,7 +367,7 @@ __device__ __forceinline__ uint32_t attempt_batch(const BatchItem &B, const uint
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const uint32_t u = j < 4 ? uint4_word(u0, j) : uint4_word(u1, j - 4);
-      if (de[j] <= 0 || u < th[j]) flip |= 1u << (8 * q + j);
+      flip |= (uint32_t)(u < th[j]) << (8 * q + j);
     }
   }
   // energy bookkeeping: acc += D on the flipped replicas (bit-sliced, sign-extended add)
