@@ -521,18 +521,16 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
       const int r = 4 * g + j;
       const int val = (int)(signed char)(unsigned char)(xmb[gi >> 1] >> (8 * (r & 7)));
       de[4 * gi + j] = val;
-      th[4 * gi + j] = 0u;
-      if (val > 0) {
-        uint32_t hi = bq_hi, lo = bq_lo;
-        if (PT) {
-          const unsigned long long be = ((unsigned long long)mult_s[r] * bqv) >> 16;
-          const uint32_t b = be > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)be;
-          hi = b >> 8;
-          lo = b & 255u;
-        }
-        const uint32_t idx = hi * (uint32_t)val + ((lo * (uint32_t)val) >> 8);
-        th[4 * gi + j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
+      uint32_t hi = bq_hi, lo = bq_lo;
+      if (PT) {
+        const unsigned long long be = ((unsigned long long)mult_s[r] * bqv) >> 16;
+        const uint32_t b = be > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)be;
+        hi = b >> 8;
+        lo = b & 255u;
       }
+      // for dE <= 0 the index is meaningless but clamped into the table; those replicas accept
+      const uint32_t idx = hi * (uint32_t)val + ((lo * (uint32_t)val) >> 8);
+      th[4 * gi + j] = tab_s[min(idx, (uint32_t)tab_len)];  // entry tab_len is 0
     }
   }
 #pragma unroll
@@ -553,10 +551,9 @@ __device__ __forceinline__ uint32_t attempt_team(const BatchItem &B, const uint3
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int i = 4 * (gi + k) + j;
-        if (de[i] <= 0 || uint4_word(u[k], j) < th[i]) {
-          flip |= 1u << (4 * (g + k) + j);
-          if (active) acc[i] += de[i];
-        }
+        const bool ok = de[i] <= 0 || uint4_word(u[k], j) < th[i];
+        flip |= (uint32_t)ok << (4 * (g + k) + j);
+        if (active) acc[i] += ok ? de[i] : 0;
       }
     }
   }
